@@ -1,0 +1,443 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than its own formulas:
+the error bound (Sec. IV-A1), the partial-sum identity of the reconstruction
+(Sec. IV-B2 proof), closed forms of the Lorenzo residual on polynomial fields,
+the paper's run-length example (Sec. III-B), brute-force optimal Huffman costs,
+Kraft's equality, the redundancy bounds quoted in Sec. III-B1, and a textbook
+Huffman instance.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from tests import _layout as LY
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _fields(rng):
+    yield rng.standard_normal(5000).astype(np.float32).cumsum()
+    yield rng.standard_normal((70, 131)).astype(np.float32).cumsum(0).cumsum(1)
+    yield rng.standard_normal((19, 23, 37)).astype(np.float32).cumsum(2)
+    yield (rng.standard_normal((33, 65)) * 1e3).astype(np.float32)
+    yield np.exp(rng.standard_normal((17, 17, 40))).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------------
+# error bound: |x - x'| <= eb on every element (Sec. IV-A1 prequantization)
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
+@pytest.mark.parametrize("sel", [0, 1, 2, 3, 4])
+def test_error_bound_every_element(orc, eb, sel):
+    rng = np.random.default_rng(11)
+    for x in _fields(rng):
+        st, ar = orc.compress(x, orc.EB_REL, eb, select=sel)
+        assert st == 0
+        h = orc.parse_header(ar)
+        st, y = orc.decompress(ar, x.size)
+        assert st == 0
+        err = np.abs(x.ravel().astype(np.float64) - y.astype(np.float64))
+        assert err.max() <= h["eb_f"], (err.max(), h["eb_f"])
+        # eb_f is the largest float not above eb * range
+        rng_d = float(x.max()) - float(x.min())
+        assert h["eb_f"] <= eb * rng_d
+        assert float(np.nextafter(np.float32(h["eb_f"]), np.float32(np.inf))) > eb * rng_d
+
+
+def test_error_bound_absolute_and_small_radius(orc):
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal((40, 50)) * 10).astype(np.float32)
+    for r in (1, 2, 7, 512):
+        st, ar = orc.compress(x, orc.EB_ABS, 0.01, radius=r)
+        st, y = orc.decompress(ar, x.size)
+        h = orc.parse_header(ar)
+        assert np.abs(x.ravel().astype(np.float64) - y).max() <= h["eb_f"]
+        if r <= 2:
+            assert h["n_out"] > 0  # rough data at tiny radius must produce outliers
+
+
+def test_prequant_near_half_points_and_patches(orc):
+    """Values placed on the rounding boundary at large |k| stress the FP32 fix-up;
+    every reconstruction still meets the bound, through a verbatim patch if needed."""
+    eb = np.float32(0.0123456789)
+    st, ebd, ebf, x2, xr = orc.eb_params(orc.EB_ABS, float(eb))
+    assert st == 0
+    ks = np.array([1, 2, 3, 1000, 12345, 654321, 3000000, 7000000], dtype=np.float64)
+    vals = []
+    for k in ks:
+        mid = (k + 0.5) * float(x2)
+        m32 = np.float32(mid)
+        for d in range(-4, 5):
+            v = m32
+            for _ in range(abs(d)):
+                v = np.nextafter(v, np.float32(np.inf if d > 0 else -np.inf))
+            vals.extend([v, -v])
+    x = np.array(vals, dtype=np.float32)
+    patches = 0
+    for v in x:
+        st, k, p = orc.prequant(float(v), ebf, x2, xr)
+        assert st == 0
+        rec = np.float32(np.float32(k) * np.float32(x2))
+        if p:
+            patches += 1
+        else:
+            assert abs(float(v) - float(rec)) <= ebf
+    st, ar = orc.compress(x, orc.EB_ABS, float(eb))
+    st, y = orc.decompress(ar, x.size)
+    assert np.abs(x.astype(np.float64) - y).max() <= orc.parse_header(ar)["eb_f"]
+    assert orc.parse_header(ar)["n_patch"] == patches
+    assert patches > 0  # the large-k half points cannot all be met by rounding alone
+
+
+# ---------------------------------------------------------------------------------
+# reconstruction = N-D partial sum of q' per chunk (Sec. IV-B2), equal to the
+# oracle's sequential recurrence
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(9000,), (70, 131), (19, 23, 37), (1, 1), (5,), (3, 2, 1)])
+def test_recurrence_equals_partial_sum(orc, shape):
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(shape).astype(np.float32)
+    x = np.cumsum(x, axis=-1).astype(np.float32)
+    st, ar = orc.compress(x, orc.EB_ABS, 2e-3, radius=16)  # small radius: outliers
+    sec = orc.sections(ar)
+    h = sec["header"]
+    codes = orc.decode_codes(ar, shape)
+    slots = LY.slot_index(shape)
+    qp = codes.astype(np.int64)[slots] - h["radius"]
+    rec = sec["records"]
+    kinds = rec[:, 0] & 1
+    out_slots = (rec[:, 0] >> 1)[kinds == 0]
+    out_vals = rec[:, 1][kinds == 0].view(np.int32)
+    inv = np.full(codes.size, -1, dtype=np.int64)
+    inv[slots.ravel()] = np.arange(x.size)
+    qp.ravel()[inv[out_slots]] = out_vals
+    k = LY.chunk_cumsum(qp, shape)
+    y_ref = (k.astype(np.float32) * np.float32(2 * np.float32(h["eb_f"]))).astype(np.float32).ravel()
+    p_slots = (rec[:, 0] >> 1)[kinds == 1]
+    y_ref[inv[p_slots]] = rec[:, 1][kinds == 1].view(np.float32)
+    st, y = orc.decompress(ar, x.size)
+    assert np.array_equal(y.view(np.uint32), y_ref.view(np.uint32))
+
+
+# ---------------------------------------------------------------------------------
+# Lorenzo residuals on polynomial fields (Sec. IV-B2 predictors): with eb = 0.5
+# (2eb = 1) integer-valued fields prequantize exactly, and the residual is the
+# mixed difference of the field inside each chunk.
+# ---------------------------------------------------------------------------------
+def _codes_field(orc, x, radius=512):
+    st, ebd, ebf, x2, xr = orc.eb_params(orc.EB_ABS, 0.5)
+    assert (ebf, x2, xr) == (0.5, 1.0, 1.0)
+    c = orc.construct(x, ebf, x2, xr, radius)
+    slots = LY.slot_index(x.shape)
+    q = c["codes"].astype(np.int64) - radius
+    out = (c["keys"] & 1) == 0
+    q[c["keys"][out] >> 1] = c["vals"][out].view(np.int32)  # outliers carry delta itself
+    assert np.all(c["codes"][c["keys"][out] >> 1] == 0)
+    return q[slots], c
+
+
+def test_lorenzo_1d_constant_and_linear(orc):
+    n = 1000
+    i = np.arange(n)
+    start = LY.chunk_start_mask((n,))[2]
+    d, _ = _codes_field(orc, np.full(n, 7.0, np.float32))
+    assert np.all(d[~start] == 0) and np.all(d[start] == 7)
+    d, _ = _codes_field(orc, (5 + 3 * i).astype(np.float32))
+    # 1-D linear: the residual is the slope, not zero
+    assert np.all(d[~start] == 3)
+    assert np.array_equal(d[start], (5 + 3 * i)[start])
+
+
+def test_lorenzo_2d_planar_and_separable(orc):
+    ny, nx = 70, 90
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    _, sy, sx = LY.chunk_start_mask((ny, nx))
+    inner = ~sy & ~sx
+    f = (3 + 2 * x - 5 * y).astype(np.float32)
+    d, _ = _codes_field(orc, f)
+    assert np.all(d[inner] == 0)
+    assert np.all(d[sy & ~sx] == 2)      # first row of a chunk: x-difference
+    assert np.all(d[sx & ~sy] == -5)     # first column: y-difference
+    assert np.array_equal(d[sx & sy], f[sx & sy].astype(np.int64))
+    g = ((x % 7) * 3 + (y * y) % 11).astype(np.float32)  # g(x) + h(y)
+    d, _ = _codes_field(orc, g)
+    assert np.all(d[inner] == 0)
+    h = (x * y).astype(np.float32)  # mixed term: residual is its mixed difference, 1
+    d, _ = _codes_field(orc, h)
+    assert np.all(d[inner] == 1)
+
+
+def test_lorenzo_3d_trilinear(orc):
+    nz, ny, nx = 20, 19, 21
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    sz, sy, sx = LY.chunk_start_mask((nz, ny, nx))
+    inner = ~sz & ~sy & ~sx
+    f = (1 + 2 * x - 3 * y + 4 * z + x * y - 2 * y * z + 3 * x * z).astype(np.float32)
+    d, _ = _codes_field(orc, f, radius=512)
+    assert np.all(d[inner] == 0)
+    d, _ = _codes_field(orc, (x * y * z).astype(np.float32))
+    assert np.all(d[inner] == 1)
+
+
+def test_outlier_keeps_delta(orc):
+    """Modified quantization (Sec. IV-B1): an out-of-range delta is stored as the
+    outlier itself and its code is 0."""
+    x = np.zeros(300, np.float32)
+    x[10] = 2000.0
+    st, ebd, ebf, x2, xr = orc.eb_params(orc.EB_ABS, 0.5)
+    c = orc.construct(x, ebf, x2, xr, 512)
+    assert list(c["keys"]) == [20, 22]  # slots 10 and 11, kind 0
+    assert list(c["vals"].view(np.int32)) == [2000, -2000]
+    assert c["codes"][10] == 0 and c["codes"][11] == 0 and c["codes"][12] == 512
+
+
+# ---------------------------------------------------------------------------------
+# run-length encoding: the paper's worked example (Sec. III-B)
+# ---------------------------------------------------------------------------------
+def test_rle_worked_example(orc):
+    g = json.load(open(os.path.join(GOLDEN, "rle_worked_example.json")))
+    letters = {"a": 513, "b": 510, "c": 512}  # codes r+1, r-2, r (radius 512)
+    seq = [letters[ch] for ch in g["sequence"]]
+    delta = np.array(seq) - 512
+    x = np.cumsum(delta).astype(np.float32)  # 1-D Lorenzo residuals equal delta
+    st, ar = orc.compress(x, orc.EB_ABS, 0.5, select=orc.SEL_RLE)
+    sec = orc.sections(ar)
+    p = sec["payload"].view(np.uint16)
+    nr = len(g["runs"])
+    assert sec["blk_bytes"][0] == 4 * nr
+    assert list(p[:nr]) == [letters[v] for v, _ in g["runs"]]
+    assert list(p[nr:2 * nr]) == [n for _, n in g["runs"]]
+    st, y = orc.decompress(ar, x.size)
+    assert np.array_equal(y, x)
+
+
+# ---------------------------------------------------------------------------------
+# Huffman code lengths: optimality by brute force, Kraft, textbook instance,
+# redundancy bounds of Sec. III-B1
+# ---------------------------------------------------------------------------------
+def _brute_min_cost(freq):
+    k = len(freq)
+    best = None
+    for lens in itertools.product(range(1, k), repeat=k):
+        if sum(2.0 ** -l for l in lens) <= 1.0 + 1e-12:
+            c = sum(f * l for f, l in zip(freq, lens))
+            best = c if best is None or c < best else best
+    return best
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_huffman_brute_force_optimal(orc, seed):
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(2, 7 if seed < 10 else 8))
+    freq = rng.integers(1, 50, size=k).astype(np.uint32)
+    if seed % 3 == 0:
+        freq[: k // 2] = freq[0]  # ties
+    full = np.zeros(1024, np.uint32)
+    pos = rng.choice(1024, size=k, replace=False)
+    full[pos] = freq
+    ln = orc.huffman_lengths(full)
+    assert np.count_nonzero(ln) == k
+    cost = int((ln[pos].astype(np.int64) * freq).sum())
+    assert cost == _brute_min_cost(list(map(int, freq)))
+    assert sum(2.0 ** -int(l) for l in ln[pos]) == 1.0  # Kraft equality (full tree)
+
+
+def test_huffman_textbook(orc):
+    g = json.load(open(os.path.join(GOLDEN, "huffman_textbook.json")))
+    syms = sorted(g["freq"])
+    full = np.zeros(16, np.uint32)
+    for i, s in enumerate(syms):
+        full[i] = g["freq"][s]
+    ln = orc.huffman_lengths(full)
+    for i, s in enumerate(syms):
+        assert ln[i] == g["lengths"][s]
+    assert int((ln[: len(syms)].astype(int) * full[: len(syms)]).sum()) == g["cost"]
+
+
+def test_huffman_single_and_empty(orc):
+    f = np.zeros(1024, np.uint32)
+    assert not orc.huffman_lengths(f).any()
+    f[77] = 5
+    ln = orc.huffman_lengths(f)
+    assert ln[77] == 1 and ln.sum() == 1
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_huffman_redundancy_bounds(orc, seed):
+    """R = <b> - H: R <= p1 + 0.086 (Gallager), and R >= 1 - H(p1,1-p1) when
+    p1 > 0.4 (Sec. III-B1)."""
+    rng = np.random.default_rng(100 + seed)
+    k = int(rng.integers(2, 300))
+    f = rng.geometric(rng.uniform(0.05, 0.9), size=k).astype(np.float64) ** rng.uniform(0.5, 3)
+    if seed % 2:
+        f[0] *= rng.uniform(2, 200)
+    f = np.maximum(1, np.round(f * 50)).astype(np.uint32)
+    full = np.zeros(1024, np.uint32)
+    full[:k] = f
+    ln = orc.huffman_lengths(full)[:k].astype(np.float64)
+    p = f / f.sum()
+    H = -(p * np.log2(p)).sum()
+    avg = (p * ln).sum()
+    R = avg - H
+    p1 = p.max()
+    assert R >= -1e-12
+    assert R <= p1 + 0.086 + 1e-9
+    if p1 > 0.4:
+        Hb = -(p1 * math.log2(p1) + (1 - p1) * math.log2(1 - p1)) if p1 < 1 else 0.0
+        assert R >= 1 - Hb - 1e-9
+
+
+def test_canonical_codes_prefix_free(orc):
+    rng = np.random.default_rng(9)
+    f = np.zeros(4096, np.uint32)
+    idx = rng.choice(4096, 400, replace=False)
+    f[idx] = rng.integers(1, 10000, 400)
+    ln = orc.huffman_lengths(f)
+    code = orc.canonical_codes(ln)
+    words = sorted((int(ln[s]), int(s)) for s in np.nonzero(ln)[0])
+    strs = [format(int(code[s]), "0%db" % l) for l, s in words]
+    # canonical: ordered by (length, symbol) means codes increase as integers
+    # left-aligned at the max length
+    L = max(l for l, _ in words)
+    vals = [int(code[s]) << (L - l) for l, s in words]
+    assert vals == sorted(vals) and len(set(vals)) == len(vals)
+    for a, b in zip(strs, strs[1:]):
+        assert not b.startswith(a)
+    # all codes distinct and prefix-free overall
+    ss = sorted(strs)
+    for a, b in zip(ss, ss[1:]):
+        assert not b.startswith(a)
+
+
+def test_huffman_only_cr_at_most_32(orc):
+    """At least one bit per symbol, so Huffman-only CR <= 32 for FP32 (Sec. II-B1)."""
+    x = np.zeros((128, 128), np.float32)
+    st, ar = orc.compress(x, orc.EB_ABS, 1.0, select=orc.SEL_HUFF)
+    sec = orc.sections(ar)
+    assert sec["header"]["payload"] * 8 >= x.size
+    st, ar2 = orc.compress(x, orc.EB_ABS, 1.0, select=orc.SEL_EXHAUSTIVE)
+    assert ar2.size < ar.size  # runs beat the 1-bit floor on a constant field
+
+
+# ---------------------------------------------------------------------------------
+# lossless coding round trips: every codec reproduces the quant-codes exactly
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("sel", [0, 1, 2, 3, 4])
+def test_codec_round_trip_codes(orc, sel):
+    rng = np.random.default_rng(21)
+    for x in _fields(rng):
+        st, ar = orc.compress(x, orc.EB_REL, 1e-3, select=sel)
+        h = orc.parse_header(ar)
+        st, ebd, ebf, x2, xr = orc.eb_params(orc.EB_REL, 1e-3, float(x.min()), float(x.max()))
+        c = orc.construct(x, ebf, x2, xr)
+        dec = orc.decode_codes(ar, x.shape)
+        assert np.array_equal(dec, c["codes"])
+        sec = orc.sections(ar)
+        assert np.array_equal(sec["records"][:, 0], c["keys"])
+        if sel <= 2:
+            assert h["n_codec"][sel] == h["nblk"]
+
+
+def test_exhaustive_is_minimal(orc):
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((200, 300)).astype(np.float32).cumsum(1)
+    x[50:120, :] = 0.0
+    sizes = []
+    for sel in range(5):
+        st, ar = orc.compress(x, orc.EB_REL, 1e-2, select=sel)
+        sizes.append(orc.parse_header(ar)["payload"])
+    assert sizes[4] <= min(sizes[:3])
+    st, ar = orc.compress(x, orc.EB_REL, 1e-2, select=4)
+    h = orc.parse_header(ar)
+    assert h["n_codec"][0] > 0 and (h["n_codec"][1] + h["n_codec"][2]) > 0
+
+
+# ---------------------------------------------------------------------------------
+# selector pieces: fixed-point log2, heuristic on clear-cut histograms, features
+# ---------------------------------------------------------------------------------
+def test_log2_q16(orc):
+    for v in [1, 2, 3, 5, 7, 10, 100, 1000, 4095, 4096, 65535, 1 << 20, 123456789, (1 << 32) - 1]:
+        got = orc.log2_q16(v) / 65536.0
+        assert abs(got - math.log2(v)) <= 2.0 / 65536.0
+
+
+def test_heuristic_clear_cases(orc):
+    h = np.zeros(1024, np.uint32)
+    h[512] = 4096
+    assert orc.heuristic_pick(h, 4096) == orc.CODEC_RLE_HUFF  # H=0, R-=1 -> 1.0
+    h[:] = 0
+    h[500:516] = 256
+    assert orc.heuristic_pick(h, 4096) == orc.CODEC_HUFF  # H = 4 bits
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        h = np.zeros(1024, np.uint32)
+        k = int(rng.integers(1, 40))
+        h[rng.choice(1024, k, replace=False)] = rng.integers(1, 400, k)
+        m = int(h.sum())
+        p = h[h > 0] / m
+        H = -(p * np.log2(p)).sum()
+        p1 = p.max()
+        R = 1 + p1 * math.log2(p1) + ((1 - p1) * math.log2(1 - p1) if p1 < 1 else 0) if p1 > 0.4 else 0.0
+        est = H + max(R, 0)
+        if abs(est - 1.09) > 1e-3:
+            want = orc.CODEC_RLE_HUFF if est <= 1.09 else orc.CODEC_HUFF
+            assert orc.heuristic_pick(h, m) == want
+
+
+def test_features_special_cases(orc):
+    x = np.zeros(4096, np.float32)
+    st, ebd, ebf, x2, xr = orc.eb_params(orc.EB_ABS, 0.5)
+    c = orc.construct(x, ebf, x2, xr)
+    f = orc.block_features(c["codes"], (4096,))
+    assert np.allclose(f[0], [1, 0, 1, 1, 1 / 4096, 0, 0, 0])
+    rng = np.random.default_rng(2)
+    x = rng.integers(-300, 300, 4096).astype(np.float32)
+    c = orc.construct(x, ebf, x2, xr)
+    f = orc.block_features(c["codes"], (4096,))[0]
+    codes = c["codes"][:4096].astype(np.int64)
+    assert f[5] == np.float32(np.count_nonzero(codes == 0)) / np.float32(4096)
+    assert f[4] == np.float32(1 + np.count_nonzero(codes[1:] != codes[:-1])) / np.float32(4096)
+    hst = np.bincount(codes, minlength=1024)
+    p = hst[hst > 0] / 4096
+    assert abs(f[1] - (-(p * np.log2(p)).sum())) < 1e-3
+
+
+# ---------------------------------------------------------------------------------
+# MLP: FP32 forward close to a float64 forward; analytic gradient = finite differences
+# ---------------------------------------------------------------------------------
+def test_mlp_forward_and_gradient(orc):
+    rng = np.random.default_rng(1)
+    w = (rng.standard_normal(orc.MLP_PARAMS) * 0.3).astype(np.float32)
+    feat = rng.random((64, 8)).astype(np.float32)
+    tgt = rng.random((64, 3)).astype(np.float32) * 10
+    y = orc.mlp_forward(w, feat)
+    W1 = w[:256].reshape(32, 8).astype(np.float64)
+    b1 = w[256:288]
+    W2 = w[288:1312].reshape(32, 32).astype(np.float64)
+    b2 = w[1312:1344]
+    W3 = w[1344:1440].reshape(3, 32).astype(np.float64)
+    b3 = w[1440:1443]
+    h1 = np.maximum(0, feat.astype(np.float64) @ W1.T + b1)
+    h2 = np.maximum(0, h1 @ W2.T + b2)
+    y64 = h2 @ W3.T + b3
+    assert np.allclose(y, y64, rtol=1e-5, atol=1e-5)
+    loss, g = orc.mlp_loss_grad(w, feat, tgt)
+    assert abs(loss - ((y64 - tgt) ** 2).mean()) < 1e-6 * max(1, loss)
+    for i in rng.choice(orc.MLP_PARAMS, 40, replace=False):
+        w64 = w.astype(np.float64)
+        eps = 1e-7
+        wp, wm = w64.copy(), w64.copy()
+        wp[i] += eps
+        wm[i] -= eps
+
+        def L(ww):
+            a = np.maximum(0, feat @ ww[:256].reshape(32, 8).T + ww[256:288])
+            a = np.maximum(0, a @ ww[288:1312].reshape(32, 32).T + ww[1312:1344])
+            return ((a @ ww[1344:1440].reshape(3, 32).T + ww[1440:1443] - tgt) ** 2).mean()
+        fd = (L(wp) - L(wm)) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(fd))
