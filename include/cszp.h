@@ -1,0 +1,117 @@
+/*
+ * cszp -- GB300 (sm_103a) error-bounded lossy compressor: the data-parallel path of
+ * cuSZ+ (Tian et al., "Optimizing Error-Bounded Lossy Compression for Scientific
+ * Data on GPUs", arXiv 2105.12912).
+ *
+ * C ABI: plain pointers and sizes, no CUDA or PyTorch types.  A `stream` argument is
+ * a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *
+ * Ownership: the caller owns every buffer.  Device buffers (field, archive, output,
+ * workspace) are caller-allocated device memory; the library allocates nothing
+ * during a call.  Host pointers are marked h_.
+ *
+ * Errors: every call returns a csz_status; nothing throws across the ABI.  On error
+ * the contents of output buffers are unspecified, but no write ever leaves the
+ * capacity the caller passed.  Device-side failures (non-finite input, range,
+ * corrupt archive, capacity, a bounded wait that expired) are reported through the
+ * single synchronisation each call performs.
+ *
+ * Layout: fields are row-major FP32 with dims given slowest-first (dims[ndim-1] is
+ * the contiguous axis).  ndim is 1, 2 or 3; every extent is >= 1 and < 2^31, and
+ * the shape may hold at most 524287 codec blocks (1-D: 4096 elements, 2-D: 64x64,
+ * 3-D: 16^3 per block).
+ */
+#ifndef CSZP_H
+#define CSZP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CSZ_OK = 0,
+  CSZ_E_ARG = 1,       /* bad argument, empty shape, zero/negative/non-finite bound */
+  CSZ_E_NONFINITE = 2, /* the field holds NaN or Inf */
+  CSZ_E_RANGE = 3,     /* |x| / (2 eb) reaches 2^23: eb too small for the data */
+  CSZ_E_CORRUPT = 4,   /* archive failed validation */
+  CSZ_E_CAPACITY = 5,  /* output or workspace buffer too small */
+  CSZ_E_CUDA = 6,      /* a CUDA runtime call failed */
+  CSZ_E_TIMEOUT = 7    /* a bounded device-side wait expired */
+} csz_status;
+
+/* Error-bound mode (Sec. VI-A): absolute, or relative to the field's value range
+   (eb_abs = eb * (max - min), computed in double). */
+typedef enum { CSZ_EB_ABS = 0, CSZ_EB_REL = 1 } csz_eb_mode;
+
+/* Per-block codec selection.  The first three force one codec on every block;
+   HEURISTIC is the paper's histogram estimate with the 1.09-bit rule (Sec. III-B);
+   EXHAUSTIVE computes all three exact sizes and keeps the smallest; LEARNED runs
+   the 8-32-32-3 MLP selector on per-block statistics.  The choice only changes
+   the encoding: reconstructions are identical. */
+typedef enum {
+  CSZ_SEL_HUFF = 0,
+  CSZ_SEL_RLE = 1,
+  CSZ_SEL_RLE_HUFF = 2,
+  CSZ_SEL_HEURISTIC = 3,
+  CSZ_SEL_EXHAUSTIVE = 4,
+  CSZ_SEL_LEARNED = 5
+} csz_select;
+
+typedef struct {
+  uint32_t radius;               /* quantization radius r (Alg. 1), 1..512; 0 = 512 */
+  uint32_t select;               /* csz_select; default EXHAUSTIVE */
+  const float* selector_weights; /* device pointer, CSZ_MLP_PARAMS floats; LEARNED only */
+  uint32_t reserved[4];          /* must be zero */
+} csz_options;
+
+#define CSZ_MLP_PARAMS 1443 /* W1[32][8] b1[32] W2[32][32] b2[32] W3[3][32] b3[3] */
+
+/* Worst-case archive size for a shape (0 if the shape is invalid). */
+size_t csz_max_archive_bytes(int ndim, const uint64_t* dims);
+
+/* Device workspace both csz_compress and csz_decompress need for a shape
+   (0 if the shape is invalid).  The workspace may be reused across calls on one
+   stream; calls that run concurrently need separate workspaces. */
+size_t csz_workspace_bytes(int ndim, const uint64_t* dims);
+
+/*
+ * Compress a device-resident FP32 field (Sec. IV-A; Alg. 1 compression part):
+ * value range (REL), dual-quantization Lorenzo construction with outliers that keep
+ * delta, histograms, canonical Huffman books, per-block codec selection and
+ * encoding.  Writes the archive to d_archive (capacity archive_cap bytes) and its
+ * size to *h_archive_bytes.  Synchronises `stream` once, to read the size and the
+ * device status.
+ * Guarantee: every reconstructed element x' satisfies |x - x'| <= eb_f, where eb_f
+ * is the largest float not above the absolute bound.
+ */
+csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, int eb_mode,
+                        double eb, const csz_options* opt, void* d_workspace,
+                        size_t workspace_bytes, uint8_t* d_archive, size_t archive_cap,
+                        size_t* h_archive_bytes, void* stream);
+
+/* Read shape and bound from an archive header held in host memory (first 128
+   bytes suffice). */
+csz_status csz_archive_info(const uint8_t* h_archive, size_t bytes, int* ndim, uint64_t* dims,
+                            double* eb_abs, uint64_t* total_bytes);
+
+/*
+ * Decompress a device-resident archive into d_out (out_cap_elems floats): decode
+ * each block's codes, fuse outliers, rebuild the prequantized integers as an N-D
+ * partial sum per chunk and scale by 2 eb (Alg. 1 decompression part, Sec. IV-B).
+ * Copies the 128-byte header to the host, then synchronises `stream` once at the
+ * end to read the device status.
+ */
+csz_status csz_decompress(const uint8_t* d_archive, size_t bytes, float* d_out,
+                          uint64_t out_cap_elems, void* d_workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* Human-readable name of a status. */
+const char* csz_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSZP_H */

@@ -958,11 +958,11 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
   if (radius < 1 || radius > 512) return ORC_E_ARG;
   if (select < ORC_SEL_HUFF || select > ORC_SEL_LEARNED) return ORC_E_ARG;
   if (select == ORC_SEL_LEARNED && !mlp_w) return ORC_E_ARG;
+  if (!(eb > 0.0) || !isfinite(eb) || (eb_mode != ORC_EB_ABS && eb_mode != ORC_EB_REL)) return ORC_E_ARG;
+  /* a non-finite value is reported before any range error, in either mode */
   float vmin = 0.0f, vmax = 0.0f;
-  if (eb_mode == ORC_EB_REL) {
-    st = orc_value_range(x, g.nelem, &vmin, &vmax);
-    if (st) return st;
-  }
+  st = orc_value_range(x, g.nelem, &vmin, &vmax);
+  if (st) return st;
   double eb_d;
   float eb_f, ebx2_f, ebx2_r;
   st = orc_eb_params(eb_mode, eb, vmin, vmax, &eb_d, &eb_f, &ebx2_f, &ebx2_r);

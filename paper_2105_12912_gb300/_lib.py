@@ -1,0 +1,63 @@
+"""ctypes loader of libcszp.so (the CUDA library).  No fallback: if the library is
+missing the import of the binding fails with a message saying how to build it."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libcszp.so")
+
+OK, E_ARG, E_NONFINITE, E_RANGE, E_CORRUPT, E_CAPACITY, E_CUDA, E_TIMEOUT = range(8)
+STATUS_NAMES = ["ok", "E_ARG", "E_NONFINITE", "E_RANGE", "E_CORRUPT", "E_CAPACITY", "E_CUDA", "E_TIMEOUT"]
+
+
+class csz_options(C.Structure):
+    _fields_ = [("radius", C.c_uint32), ("select", C.c_uint32), ("selector_weights", C.c_void_p),
+                ("reserved", C.c_uint32 * 4)]
+
+
+class CszError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{what}: {name}")
+        self.status = status
+
+
+_lib = None
+
+# name -> (restype, argtypes); the exported C ABI of include/cszp.h
+SIGNATURES = {
+    "csz_max_archive_bytes": (C.c_size_t, [C.c_int, C.POINTER(C.c_uint64)]),
+    "csz_workspace_bytes": (C.c_size_t, [C.c_int, C.POINTER(C.c_uint64)]),
+    "csz_compress": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint64), C.c_int, C.c_double,
+                               C.POINTER(csz_options), C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t,
+                               C.POINTER(C.c_size_t), C.c_void_p]),
+    "csz_archive_info": (C.c_int, [C.c_void_p, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_uint64),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+    "csz_decompress": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t,
+                                 C.c_void_p]),
+    "csz_status_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcszp.so not found at {LIB_PATH}; build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def dims_array(dims):
+    d = (C.c_uint64 * 3)()
+    for i, v in enumerate(dims):
+        d[i] = int(v)
+    return d

@@ -1,0 +1,128 @@
+"""Python binding of the cszp C ABI (argument marshalling only).
+
+PyTorch provides device memory and streams; every step of compression and
+decompression runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+EB_MODES = {"abs": 0, "rel": 1}
+SELECT = {"huff": 0, "rle": 1, "rle_huff": 2, "heuristic": 3, "exhaustive": 4, "learned": 5}
+CODECS = ("huff", "rle", "rle_huff")
+MLP_PARAMS = 1443
+
+
+def _check(st: int, what: str):
+    if st != L.OK:
+        raise L.CszError(st, what)
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def max_archive_bytes(dims) -> int:
+    return int(L.lib().csz_max_archive_bytes(len(dims), L.dims_array(dims)))
+
+
+def workspace_bytes(dims) -> int:
+    return int(L.lib().csz_workspace_bytes(len(dims), L.dims_array(dims)))
+
+
+class Workspace:
+    """Device scratch for one stream, grown on demand and reused across calls."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device or "cuda")
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+_default_ws = {}
+
+
+def _ws(device, ws):
+    if ws is not None:
+        return ws
+    key = torch.device(device).index
+    if key not in _default_ws:
+        _default_ws[key] = Workspace(device)
+    return _default_ws[key]
+
+
+def compress(field: torch.Tensor, eb: float, eb_mode: str = "rel", radius: int = 512,
+             select: str = "exhaustive", weights: torch.Tensor | None = None, out: torch.Tensor | None = None,
+             workspace: Workspace | None = None, stream=None, raise_on_error: bool = True):
+    """Compress a contiguous FP32 CUDA tensor (1-3 dims).  Returns (archive, nbytes, status):
+    archive is a uint8 CUDA tensor whose first nbytes bytes hold the archive."""
+    if not (field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()):
+        raise ValueError("field must be a contiguous float32 CUDA tensor")
+    dims = tuple(field.shape)
+    if out is None:
+        out = torch.empty(max_archive_bytes(dims) or 1, dtype=torch.uint8, device=field.device)
+    ws = _ws(field.device, workspace).get(workspace_bytes(dims) or 256)
+    opt = L.csz_options()
+    opt.radius = int(radius)
+    opt.select = SELECT[select] if isinstance(select, str) else int(select)
+    if weights is not None:
+        if not (weights.is_cuda and weights.dtype == torch.float32 and weights.numel() == MLP_PARAMS):
+            raise ValueError("weights must be a float32 CUDA tensor of 1443 parameters")
+        opt.selector_weights = C.c_void_p(weights.data_ptr())
+    nbytes = C.c_size_t(0)
+    st = L.lib().csz_compress(C.c_void_p(field.data_ptr()), len(dims), L.dims_array(dims),
+                              EB_MODES[eb_mode] if isinstance(eb_mode, str) else int(eb_mode), float(eb),
+                              C.byref(opt), C.c_void_p(ws.data_ptr()), ws.numel(), C.c_void_p(out.data_ptr()),
+                              out.numel(), C.byref(nbytes), _stream_ptr(stream))
+    if raise_on_error:
+        _check(st, "csz_compress")
+    return out, int(nbytes.value), st
+
+
+def archive_info(archive_host_head: bytes):
+    """(dims, eb_abs, total_bytes) from the first 128 bytes of an archive."""
+    buf = (C.c_uint8 * len(archive_host_head)).from_buffer_copy(archive_host_head)
+    nd = C.c_int()
+    dims = (C.c_uint64 * 3)()
+    eb = C.c_double()
+    tot = C.c_uint64()
+    st = L.lib().csz_archive_info(C.cast(buf, C.c_void_p), len(archive_host_head), C.byref(nd), dims,
+                                  C.byref(eb), C.byref(tot))
+    _check(st, "csz_archive_info")
+    return tuple(int(dims[i]) for i in range(nd.value)), float(eb.value), int(tot.value)
+
+
+def decompress(archive: torch.Tensor, nbytes: int | None = None, out: torch.Tensor | None = None,
+               dims=None, workspace: Workspace | None = None, stream=None, raise_on_error: bool = True):
+    """Decompress a uint8 CUDA archive.  Returns (field, status)."""
+    if not (archive.is_cuda and archive.dtype == torch.uint8):
+        raise ValueError("archive must be a uint8 CUDA tensor")
+    if nbytes is None:
+        nbytes = archive.numel()
+    if dims is None:
+        head = bytes(archive[:128].cpu().numpy().tobytes())
+        dims, _, _ = archive_info(head)
+    n = 1
+    for d in dims:
+        n *= int(d)
+    if out is None:
+        out = torch.empty(tuple(dims), dtype=torch.float32, device=archive.device)
+    ws = _ws(archive.device, workspace).get(workspace_bytes(dims) or 256)
+    st = L.lib().csz_decompress(C.c_void_p(archive.data_ptr()), int(nbytes), C.c_void_p(out.data_ptr()),
+                                out.numel(), C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream))
+    if raise_on_error:
+        _check(st, "csz_decompress")
+    return out, st
+
+
+def status_string(st: int) -> str:
+    return L.lib().csz_status_string(int(st)).decode()

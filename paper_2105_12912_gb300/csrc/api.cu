@@ -1,0 +1,339 @@
+// Host side of the cszp C ABI: argument and archive-header validation, workspace
+// layout, kernel sequencing on the caller's stream, one synchronisation per call.
+#include <cmath>
+#include <cstring>
+
+#include "cszp.h"
+#include "kernels.h"
+
+using namespace cszp;
+
+namespace {
+
+constexpr uint64_t kMaxBlocks = (1ull << 31) / kSlots;  // slots*2 must fit in 32 bits
+
+uint64_t a8(uint64_t v) { return (v + 7) & ~7ull; }
+uint64_t a256(uint64_t v) { return (v + 255) & ~255ull; }
+
+// Codec blocks: 1-D 4096, 2-D 64x64, 3-D 16^3 (x fastest).
+bool make_geom(int ndim, const uint64_t* dims, Geom& g) {
+  static const uint32_t B[4][3] = {{0, 0, 0}, {1, 1, 4096}, {1, 64, 64}, {16, 16, 16}};
+  if (ndim < 1 || ndim > 3 || !dims) return false;
+  memset(&g, 0, sizeof(g));
+  g.ndim = ndim;
+  uint64_t n[3] = {1, 1, 1};
+  for (int i = 0; i < ndim; i++) {
+    if (dims[i] == 0 || dims[i] >= (1ull << 31)) return false;
+    n[3 - ndim + i] = dims[i];
+  }
+  uint64_t nblk = 1, nelem = 1;
+  for (int d = 0; d < 3; d++) {
+    g.n[d] = (uint32_t)n[d];
+    g.blk[d] = B[ndim][d];
+    g.g[d] = (uint32_t)((n[d] + B[ndim][d] - 1) / B[ndim][d]);
+    nblk *= g.g[d];
+    nelem *= n[d];
+  }
+  if (nblk >= kMaxBlocks) return false;
+  g.nblk = (uint32_t)nblk;
+  g.nelem = nelem;
+  return true;
+}
+
+// Workspace: [DevState | histograms | look-back states] (zeroed per compression),
+// books, decode tables and offsets, block-major code stream.
+struct Layout {
+  uint64_t st, hist_code, hist_val, hist_len, lb_c, lb_e, zero_end;
+  uint64_t lens, bcodes, feat, blk_off, rec_start, tabs, codes, total;
+};
+
+Layout layout(const Geom& g) {
+  Layout L;
+  uint64_t o = 0;
+  L.st = o;
+  o += a256(sizeof(DevState));
+  L.hist_code = o;
+  o += kNsymCode * 4;
+  L.hist_val = o;
+  o += kNsymCode * 4;
+  L.hist_len = o;
+  o += kNsymLen * 4;
+  L.lb_c = o;
+  o += 8ull * g.nblk;
+  L.lb_e = o;
+  o += 8ull * g.nblk;
+  L.zero_end = o;
+  o = a256(o);
+  L.lens = o;
+  o += a256(2 * kNsymCode + kNsymLen);
+  L.bcodes = o;
+  o += 8ull * (2 * kNsymCode + kNsymLen);
+  L.feat = o;
+  o += a256(32ull * g.nblk);
+  L.blk_off = o;
+  o += a256(8ull * (g.nblk + 1));
+  L.rec_start = o;
+  o += a256(4ull * (g.nblk + 1));
+  L.tabs = o;
+  o += a256(3 * sizeof(DecTab));
+  L.codes = o;
+  o += a256(2ull * kSlots * g.nblk);
+  L.total = o;
+  return L;
+}
+
+template <typename T>
+T* at(void* base, uint64_t off) {
+  return reinterpret_cast<T*>(static_cast<unsigned char*>(base) + off);
+}
+
+csz_status fold(uint32_t bits) {
+  if (bits & ERR_NONFINITE) return CSZ_E_NONFINITE;
+  if (bits & ERR_ARG) return CSZ_E_ARG;
+  if (bits & ERR_RANGE) return CSZ_E_RANGE;
+  if (bits & ERR_CORRUPT) return CSZ_E_CORRUPT;
+  if (bits & ERR_CAPACITY) return CSZ_E_CAPACITY;
+  if (bits & ERR_TIMEOUT) return CSZ_E_TIMEOUT;
+  return CSZ_OK;
+}
+
+uint32_t g_spin_limit = kSpinLimit;
+
+struct Header {
+  uint32_t magic;
+  uint16_t version;
+  uint8_t ndim, eb_mode;
+  uint64_t dims[3];
+  double eb_user, eb_d;
+  float eb_f;
+  uint32_t radius, huff_seg, flags;
+  uint64_t nblk, n_rec, n_out, n_patch, payload, total;
+};
+
+// Header checks that need no device data (magic, shape, bound, section sizes).  With
+// whole = false only the header itself is present, so section ends are not compared
+// with `bytes`.
+csz_status parse_header(const uint8_t* h, size_t bytes, Header& H, Geom& g, bool whole = true) {
+  if (bytes < (size_t)kHdr) return CSZ_E_CORRUPT;
+  memcpy(&H.magic, h, 4);
+  memcpy(&H.version, h + 4, 2);
+  H.ndim = h[6];
+  H.eb_mode = h[7];
+  memcpy(H.dims, h + 8, 24);
+  memcpy(&H.eb_user, h + 32, 8);
+  memcpy(&H.eb_d, h + 40, 8);
+  memcpy(&H.eb_f, h + 48, 4);
+  memcpy(&H.radius, h + 52, 4);
+  memcpy(&H.huff_seg, h + 56, 4);
+  memcpy(&H.flags, h + 60, 4);
+  memcpy(&H.nblk, h + 64, 8);
+  memcpy(&H.n_rec, h + 72, 8);
+  memcpy(&H.n_out, h + 80, 8);
+  memcpy(&H.n_patch, h + 88, 8);
+  memcpy(&H.payload, h + 96, 8);
+  memcpy(&H.total, h + 104, 8);
+  if (H.magic != kMagic || H.version != kVersion) return CSZ_E_CORRUPT;
+  if (H.ndim < 1 || H.ndim > 3 || H.eb_mode > 1) return CSZ_E_CORRUPT;
+  if (!make_geom(H.ndim, H.dims, g)) return CSZ_E_CORRUPT;
+  for (int i = H.ndim; i < 3; i++)
+    if (H.dims[i]) return CSZ_E_CORRUPT;
+  if (H.radius < 1 || H.radius > 512 || H.huff_seg != (uint32_t)kHuffSeg || H.flags > 3) return CSZ_E_CORRUPT;
+  if (H.nblk != g.nblk || H.n_rec != H.n_out + H.n_patch) return CSZ_E_CORRUPT;
+  if (!(H.eb_f > 0.0f) || !std::isfinite(2.0f * H.eb_f)) return CSZ_E_CORRUPT;
+  if (H.n_rec > 2 * g.nelem || (whole && H.payload > bytes) || (H.payload & 3)) return CSZ_E_CORRUPT;
+  const uint64_t off_bb = kHdr + a8(H.nblk);
+  const uint64_t off_rec = off_bb + a8(4 * H.nblk);
+  const uint64_t off_books = off_rec + 8 * H.n_rec + a8(H.payload);
+  const uint64_t total =
+      off_books + ((H.flags & 1) ? kNsymCode : 0) + ((H.flags & 2) ? kNsymCode + kNsymLen : 0);
+  if (H.total != total || (whole && total > bytes)) return CSZ_E_CORRUPT;
+  return CSZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* csz_status_string(int s) {
+  switch (s) {
+    case CSZ_OK: return "ok";
+    case CSZ_E_ARG: return "invalid argument";
+    case CSZ_E_NONFINITE: return "non-finite input value";
+    case CSZ_E_RANGE: return "value too large for the error bound";
+    case CSZ_E_CORRUPT: return "corrupt archive";
+    case CSZ_E_CAPACITY: return "buffer too small";
+    case CSZ_E_CUDA: return "CUDA runtime error";
+    case CSZ_E_TIMEOUT: return "bounded device wait expired";
+    default: return "unknown status";
+  }
+}
+
+size_t csz_max_archive_bytes(int ndim, const uint64_t* dims) {
+  Geom g;
+  if (!make_geom(ndim, dims, g)) return 0;
+  const uint64_t slots = (uint64_t)g.nblk * kSlots;
+  return (size_t)(kHdr + a8(g.nblk) + a8(4ull * g.nblk) + 16 * g.nelem + 16 * slots + 64ull * g.nblk +
+                  2 * kNsymCode + kNsymLen);
+}
+
+size_t csz_workspace_bytes(int ndim, const uint64_t* dims) {
+  Geom g;
+  if (!make_geom(ndim, dims, g)) return 0;
+  return (size_t)layout(g).total;
+}
+
+csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
+                        const csz_options* opt, void* d_ws, size_t ws_bytes, uint8_t* d_ar, size_t cap,
+                        size_t* h_bytes, void* stream) {
+  Geom g;
+  if (!d_field || !d_ar || !h_bytes || !d_ws) return CSZ_E_ARG;
+  if (!make_geom(ndim, dims, g)) return CSZ_E_ARG;
+  const uint32_t radius = (opt && opt->radius) ? opt->radius : 512u;
+  const int select = opt ? (int)opt->select : SEL_EXHAUSTIVE;
+  if (radius > 512 || select < 0 || select > SEL_LEARNED) return CSZ_E_ARG;
+  if (select == SEL_LEARNED && !(opt && opt->selector_weights)) return CSZ_E_ARG;
+  if (opt)
+    for (int i = 0; i < 4; i++)
+      if (opt->reserved[i]) return CSZ_E_ARG;
+  if (!(eb > 0.0) || !std::isfinite(eb) || (eb_mode != CSZ_EB_ABS && eb_mode != CSZ_EB_REL)) return CSZ_E_ARG;
+  const Layout L = layout(g);
+  if (ws_bytes < L.total) return CSZ_E_CAPACITY;
+  const uint64_t off_bb = kHdr + a8(g.nblk);
+  const uint64_t off_rec = off_bb + a8(4ull * g.nblk);
+  if (cap < off_rec) return CSZ_E_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevState* st = at<DevState>(d_ws, L.st);
+
+  if (cudaMemsetAsync(d_ws, 0, L.zero_end, s) != cudaSuccess) return CSZ_E_CUDA;
+  cudaError_t e = eb_mode == CSZ_EB_REL ? launch_range(d_field, g.nelem, st, 1, eb, s)
+                                        : launch_abs_params(st, eb, s);
+  if (e != cudaSuccess) return CSZ_E_CUDA;
+
+  ConstructArgs ca;
+  ca.x = d_field;
+  ca.g = g;
+  ca.st = st;
+  ca.radius = radius;
+  ca.codes = at<uint16_t>(d_ws, L.codes);
+  ca.rec = reinterpret_cast<uint32_t*>(d_ar + off_rec);
+  ca.rec_cap = (cap - off_rec) / 8;
+  ca.hist_code = at<uint32_t>(d_ws, L.hist_code);
+  ca.hist_val = at<uint32_t>(d_ws, L.hist_val);
+  ca.hist_len = at<uint32_t>(d_ws, L.hist_len);
+  ca.lb = at<uint64_t>(d_ws, L.lb_c);
+  ca.spin_limit = g_spin_limit;
+  if (launch_construct(ndim, ca, s) != cudaSuccess) return CSZ_E_CUDA;
+
+  BookArgs ba;
+  ba.hist_code = ca.hist_code;
+  ba.hist_val = ca.hist_val;
+  ba.hist_len = ca.hist_len;
+  ba.lens = at<uint8_t>(d_ws, L.lens);
+  ba.codes = at<uint64_t>(d_ws, L.bcodes);
+  ba.st = st;
+  if (launch_codebook(ba, s) != cudaSuccess) return CSZ_E_CUDA;
+
+  EncodeArgs ea;
+  ea.g = g;
+  ea.st = st;
+  ea.radius = radius;
+  ea.select = select;
+  ea.codes = ca.codes;
+  ea.lens = ba.lens;
+  ea.bcodes = ba.codes;
+  ea.mlp_w = opt ? opt->selector_weights : nullptr;
+  ea.feat_out = nullptr;
+  ea.ar = d_ar;
+  ea.cap = cap;
+  ea.off_codec = kHdr;
+  ea.off_bb = off_bb;
+  ea.off_rec = off_rec;
+  ea.lb = at<uint64_t>(d_ws, L.lb_e);
+  ea.spin_limit = g_spin_limit;
+  if (launch_encode(ea, s) != cudaSuccess) return CSZ_E_CUDA;
+
+  FinalizeArgs fa;
+  fa.st = st;
+  fa.ar = d_ar;
+  fa.cap = cap;
+  fa.ndim = ndim;
+  fa.eb_mode = eb_mode;
+  for (int i = 0; i < 3; i++) fa.dims[i] = i < ndim ? dims[i] : 0;
+  fa.eb_user = eb;
+  fa.radius = radius;
+  fa.select = select;
+  fa.nblk = g.nblk;
+  fa.off_bb = off_bb;
+  fa.off_rec = off_rec;
+  fa.lens = ba.lens;
+  if (launch_finalize(fa, s) != cudaSuccess) return CSZ_E_CUDA;
+
+  DevState hs;
+  if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  const csz_status r = fold(hs.status);
+  if (r != CSZ_OK) return r;
+  *h_bytes = (size_t)hs.total;
+  return CSZ_OK;
+}
+
+csz_status csz_archive_info(const uint8_t* h, size_t bytes, int* ndim, uint64_t* dims, double* eb_abs,
+                            uint64_t* total_bytes) {
+  if (!h) return CSZ_E_ARG;
+  Header H;
+  Geom g;
+  csz_status r = parse_header(h, bytes, H, g, false);
+  if (r != CSZ_OK) return r;
+  if (ndim) *ndim = H.ndim;
+  if (dims)
+    for (int i = 0; i < 3; i++) dims[i] = H.dims[i];
+  if (eb_abs) *eb_abs = H.eb_d;
+  if (total_bytes) *total_bytes = H.total;
+  return CSZ_OK;
+}
+
+csz_status csz_decompress(const uint8_t* d_ar, size_t bytes, float* d_out, uint64_t out_cap, void* d_ws,
+                          size_t ws_bytes, void* stream) {
+  if (!d_ar || !d_out || !d_ws) return CSZ_E_ARG;
+  if (bytes < (size_t)kHdr) return CSZ_E_CORRUPT;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t h[kHdr];
+  if (cudaMemcpyAsync(h, d_ar, kHdr, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  Header H;
+  Geom g;
+  csz_status r = parse_header(h, bytes, H, g);
+  if (r != CSZ_OK) return r;
+  if (out_cap < g.nelem) return CSZ_E_CAPACITY;
+  const Layout L = layout(g);
+  if (ws_bytes < L.total) return CSZ_E_CAPACITY;
+  DevState* st = at<DevState>(d_ws, L.st);
+  if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return CSZ_E_CUDA;
+  DecodeArgs da;
+  da.g = g;
+  da.st = st;
+  da.ar = d_ar;
+  da.bytes = bytes;
+  da.off_codec = kHdr;
+  da.off_bb = kHdr + a8(g.nblk);
+  da.off_rec = da.off_bb + a8(4ull * g.nblk);
+  da.off_pay = da.off_rec + 8 * H.n_rec;
+  da.off_books = da.off_pay + a8(H.payload);
+  da.n_rec = H.n_rec;
+  da.payload = H.payload;
+  da.flags = H.flags;
+  da.radius = H.radius;
+  da.ebx2_f = 2.0f * H.eb_f;
+  da.blk_off = at<uint64_t>(d_ws, L.blk_off);
+  da.rec_start = at<uint32_t>(d_ws, L.rec_start);
+  da.tabs = at<DecTab>(d_ws, L.tabs);
+  da.codes = at<uint16_t>(d_ws, L.codes);
+  da.out = d_out;
+  if (launch_decode(da, s) != cudaSuccess) return CSZ_E_CUDA;
+  DevState hs;
+  if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  return fold(hs.status);
+}
+
+}  // extern "C"

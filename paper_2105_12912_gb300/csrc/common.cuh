@@ -1,0 +1,351 @@
+// Shared device-side definitions of the cszp CUDA library (sm_103a).
+//
+// Archive layout (little-endian, sections 8-byte aligned):
+//   [0,128)          header
+//   codec[nblk]      u8 per codec block (0 HUFF, 1 RLE, 2 RLE_HUFF)
+//   blk_bytes[nblk]  u32 payload bytes of each block (multiples of 4)
+//   records[n_rec]   (u32 key, u32 val), key = slot*2 + kind; kind 0 outlier (val =
+//                    delta as int32), kind 1 verbatim patch (val = float bits);
+//                    sorted by key
+//   payload          per-block payloads in block order
+//   books            u8 code lengths: quant-code book [1024] if any HUFF block, then
+//                    run-value book [1024] + run-length book [4096] if any RLE_HUFF
+//                    block
+// A slot is 4096*block + the element's row-major index among the block's in-field
+// elements.  Codec blocks: 1-D 4096, 2-D 64x64, 3-D 16^3.  Lorenzo chunks (where
+// prediction restarts from zero, Sec. II-A "Step-1" and Sec. IV-B3): 1-D 256,
+// 2-D 16x16, 3-D 8^3 (the paper gives no 3-D size).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cszp {
+
+constexpr int kSlots = 4096;
+constexpr int kNsymCode = 1024;
+constexpr int kNsymLen = 4096;
+constexpr int kHdr = 128;
+constexpr uint32_t kMagic = 0x2B5A5343u;  // "CSZ+"
+constexpr uint32_t kVersion = 1;
+constexpr int kHuffSeg = 1024;
+constexpr int kMaxLen = 64;
+constexpr int kLutBits = 12;
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+enum : int { CODEC_HUFF = 0, CODEC_RLE = 1, CODEC_RLE_HUFF = 2 };
+enum : int { SEL_HUFF = 0, SEL_RLE = 1, SEL_RLE_HUFF = 2, SEL_HEURISTIC = 3, SEL_EXHAUSTIVE = 4, SEL_LEARNED = 5 };
+
+// device status bits, folded into a csz_status by the host
+enum : uint32_t {
+  ERR_ARG = 1u,
+  ERR_NONFINITE = 2u,
+  ERR_RANGE = 4u,
+  ERR_CORRUPT = 8u,
+  ERR_CAPACITY = 16u,
+  ERR_TIMEOUT = 32u
+};
+
+struct Geom {
+  int ndim;
+  uint32_t n[3];    // extents z, y, x (x contiguous)
+  uint32_t blk[3];  // codec block extents
+  uint32_t g[3];    // blocks per axis
+  uint32_t nblk;
+  uint64_t nelem;
+};
+
+__host__ __device__ inline uint32_t imin(uint32_t a, uint32_t b) { return a < b ? a : b; }
+
+// origin and in-field extents of codec block b (row-major over the block grid)
+__host__ __device__ inline void block_box(const Geom& g, uint32_t b, uint32_t org[3], uint32_t w[3]) {
+  uint32_t bi[3];
+  bi[0] = b / (g.g[1] * g.g[2]);
+  bi[1] = (b / g.g[2]) % g.g[1];
+  bi[2] = b % g.g[2];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    org[d] = bi[d] * g.blk[d];
+    w[d] = imin(g.blk[d], g.n[d] - org[d]);
+  }
+}
+
+// Values the device derives once per compression (error bound, range, counters).
+struct DevState {
+  double eb_d;
+  float eb_f, ebx2_f, ebx2_r;
+  uint32_t status;        // ERR_* bits
+  uint32_t range_lo_inv;  // max of ~orderkey(x): gives the minimum
+  uint32_t range_hi;      // max of orderkey(x)
+  uint32_t range_done;    // CTAs finished in the range pass
+  uint32_t ticket_construct;
+  uint32_t ticket_encode;
+  uint32_t ncodec[3];
+  unsigned long long n_rec;
+  unsigned long long n_patch;
+  unsigned long long payload;
+  unsigned long long total;
+  float vmin, vmax;
+};
+
+// ---------------------------------------------------------------------------------
+// memory-model helpers for the decoupled look-back
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+constexpr uint64_t LB_AGG = 1ull << 62;
+constexpr uint64_t LB_INC = 1ull << 63;
+constexpr uint64_t LB_VAL = LB_AGG - 1;
+
+// Publish a tile's own aggregate (any thread).
+__device__ __forceinline__ void lookback_publish(uint64_t* state, uint32_t tile, uint64_t agg) {
+  st_relaxed(&state[tile], (tile == 0 ? LB_INC : LB_AGG) | agg);
+}
+
+// Decoupled look-back (single-pass prefix scan over tiles taken in ticket order):
+// called by one full warp after lookback_publish; returns the exclusive prefix and
+// publishes the inclusive one.  The wait is bounded; on expiry the status gets
+// ERR_TIMEOUT and the tile publishes what it has so successors finish too.
+__device__ inline uint64_t lookback_warp(uint64_t* state, uint32_t tile, uint64_t agg,
+                                         uint32_t* status, uint32_t spin_limit) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) return 0;
+  uint64_t excl = 0;
+  int64_t base = (int64_t)tile - 1;
+  uint32_t spins = 0;
+  while (true) {
+    int64_t idx = base - lane;
+    uint64_t v = idx >= 0 ? ld_relaxed(&state[idx]) : LB_INC;
+    uint32_t inc = __ballot_sync(~0u, (v & LB_INC) != 0);
+    uint32_t bad = __ballot_sync(~0u, (v & (LB_INC | LB_AGG)) == 0);
+    int first = inc ? __ffs(inc) : 32;  // 1-based lane of the nearest inclusive value
+    uint32_t upto = first >= 32 ? ~0u : ((1u << first) - 1u);
+    if (bad & upto) {
+      if (++spins > spin_limit) {
+        if (lane == 0) atomicOr(status, ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    uint64_t add = ((1u << lane) & upto) ? (v & LB_VAL) : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) add += __shfl_xor_sync(~0u, add, o);
+    excl += add;
+    if (inc) break;
+    base -= 32;
+  }
+  if (lane == 0) st_relaxed(&state[tile], LB_INC | (excl + agg));
+  return excl;
+}
+
+// ---------------------------------------------------------------------------------
+// block-wide scans and reductions (blockDim.x a multiple of 32, <= 1024)
+// ---------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(~0u, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(~0u, v, o);
+  return v;
+}
+
+// exclusive scan; *total receives the block sum; scratch holds >= 33 T.
+// Contains __syncthreads; all threads must call.
+template <typename T>
+__device__ T block_excl_scan(T v, T* scratch, T* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) scratch[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T s = lane < nw ? scratch[lane] : T(0);
+    T si = warp_incl_scan(s);
+    if (lane < nw) scratch[lane] = si - s;
+    if (lane == nw - 1) scratch[32] = si;
+  }
+  __syncthreads();
+  T r = scratch[wid] + inc - v;
+  if (total) *total = scratch[32];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__device__ T block_sum(T v, T* scratch) {
+  T t;
+  block_excl_scan(v, scratch, &t);
+  return t;
+}
+
+__device__ inline uint32_t block_max_u32(uint32_t v, uint32_t* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(~0u, v, o));
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t s = lane < nw ? scratch[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s = max(s, __shfl_xor_sync(~0u, s, o));
+    if (lane == 0) scratch[32] = s;
+  }
+  __syncthreads();
+  uint32_t r = scratch[32];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------------
+// prequantization arithmetic (Sec. IV-A1), bit-identical to a plain C reading
+// ---------------------------------------------------------------------------------
+
+// |x - y| > eb, decided exactly: Knuth's TwoSum gives x - y = s + e exactly, then
+// the comparison against the float eb follows from s = RN(x - y).
+__device__ __forceinline__ bool exceeds_exact(float x, float y, float eb) {
+  float s = __fsub_rn(x, y);
+  float ny = -y;
+  float bb = __fsub_rn(s, x);
+  float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(ny, bb));
+  if (s > eb || s < -eb) return true;
+  if (s == eb) return e > 0.0f;
+  if (s == -eb) return e < 0.0f;
+  return false;
+}
+
+// k0 = round-half-away(fl32(x/2eb)); if fl32(k0*2eb) misses x by more than eb, try the
+// neighbour integer on x's side, else keep k0 and ask for a verbatim patch.
+// Returns ERR_* bits (0 on success).
+__device__ __forceinline__ uint32_t prequant(float x, float eb_f, float ebx2_f, float ebx2_r,
+                                             int32_t& k, bool& patch) {
+  patch = false;
+  k = 0;
+  if (!isfinite(x)) return ERR_NONFINITE;
+  float v = __fmul_rn(x, ebx2_r);
+  if (!(fabsf(v) < 8388608.0f)) return ERR_RANGE;
+  int32_t k0 = (int32_t)roundf(v);
+  float x0 = __fmul_rn(__int2float_rn(k0), ebx2_f);
+  if (!exceeds_exact(x, x0, eb_f)) {
+    k = k0;
+    return 0;
+  }
+  int32_t k1 = k0 + (x > x0 ? 1 : -1);
+  float x1 = __fmul_rn(__int2float_rn(k1), ebx2_f);
+  if (!exceeds_exact(x, x1, eb_f)) {
+    k = k1;
+    return 0;
+  }
+  k = k0;
+  patch = true;
+  return 0;
+}
+
+// Binary logarithm in Q16 by bit-by-bit squaring of the mantissa (integer only).
+__device__ __forceinline__ uint32_t log2_q16(uint64_t v) {
+  if (v == 0) return 0;
+  uint32_t e = 63 - __clzll((long long)v);
+  uint64_t m = e >= 31 ? (v >> (e - 31)) : (v << (31 - e));
+  uint32_t frac = 0;
+#pragma unroll 1
+  for (int i = 0; i < 16; i++) {
+    m = (m * m) >> 31;
+    frac <<= 1;
+    if (m >= (2ull << 31)) {
+      m >>= 1;
+      frac |= 1u;
+    }
+  }
+  return e * 65536u + frac;
+}
+
+// ---------------------------------------------------------------------------------
+// canonical Huffman codes from lengths (block-wide).  Codes are ordered by
+// (length, symbol); the first code of length l is (first(l-1) + count(l-1)) << 1.
+// Outputs per symbol its code and its rank in (length, symbol) order; per length
+// the first code, the count and the offset of its first symbol in that order.
+// smem: cnt[kMaxLen+1] u32, first[kMaxLen+1] u64, off[kMaxLen+1] u32,
+//       wcnt[(nsym/32)*(kMaxLen+1)] u16
+// Contains __syncthreads; all threads call.
+// ---------------------------------------------------------------------------------
+struct CanonSmem {
+  uint32_t cnt[kMaxLen + 1];
+  uint32_t off[kMaxLen + 1];
+  unsigned long long first[kMaxLen + 1];
+  uint32_t bad;
+};
+
+__device__ inline void canonical_build(const uint8_t* len, int nsym, CanonSmem* cs, uint16_t* wcnt,
+                                       uint64_t* code_out, uint16_t* sorted_out) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int l = tid; l <= kMaxLen; l += nt) cs->cnt[l] = 0;
+  if (tid == 0) cs->bad = 0;
+  const int nchunk = nsym / 32;
+  for (int i = tid; i < nchunk * (kMaxLen + 1); i += nt) wcnt[i] = 0;
+  __syncthreads();
+  // per-warp-chunk counts and ranks by length
+  for (int base = (tid & ~31); base < nsym; base += nt) {
+    const int s = base + (tid & 31);
+    const int l = len[s];
+    const uint32_t peers = __match_any_sync(~0u, l);
+    if (l > kMaxLen) cs->bad = 1;
+    if (l && l <= kMaxLen && (peers & ((1u << (tid & 31)) - 1u)) == 0) {
+      wcnt[(s >> 5) * (kMaxLen + 1) + l] = (uint16_t)__popc(peers);
+      atomicAdd(&cs->cnt[l], (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long c = 0;
+    uint32_t o = 0;
+    cs->first[0] = 0;
+    cs->off[0] = 0;
+    for (int l = 1; l <= kMaxLen; l++) {
+      c = (c + (l > 1 ? cs->cnt[l - 1] : 0u)) << 1;
+      cs->first[l] = c;
+      cs->off[l] = o;
+      o += cs->cnt[l];
+    }
+  }
+  // prefix of per-chunk counts over chunks, per length (in place)
+  for (int l = 1 + tid; l <= kMaxLen; l += nt) {
+    uint32_t run = 0;
+    for (int ch = 0; ch < nchunk; ch++) {
+      uint16_t c = wcnt[ch * (kMaxLen + 1) + l];
+      wcnt[ch * (kMaxLen + 1) + l] = (uint16_t)run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int base = (tid & ~31); base < nsym; base += nt) {
+    const int s = base + (tid & 31);
+    const int l = len[s];
+    const uint32_t peers = __match_any_sync(~0u, l);
+    if (l && l <= kMaxLen) {
+      uint32_t rank = wcnt[(s >> 5) * (kMaxLen + 1) + l] + __popc(peers & ((1u << (tid & 31)) - 1u));
+      if (code_out) code_out[s] = cs->first[l] + rank;
+      if (sorted_out) sorted_out[cs->off[l] + rank] = (uint16_t)s;
+    } else if (code_out) {
+      code_out[s] = 0;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace cszp

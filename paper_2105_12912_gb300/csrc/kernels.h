@@ -1,0 +1,102 @@
+// Kernel argument blocks and host-side launchers of the cszp CUDA library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace cszp {
+
+struct ConstructArgs {
+  const float* x;
+  Geom g;
+  DevState* st;
+  uint32_t radius;
+  uint16_t* codes;     // nblk * 4096, block-major
+  uint32_t* rec;       // archive record section (u32 key, u32 val pairs)
+  uint64_t rec_cap;    // records that fit before the archive capacity ends
+  uint32_t* hist_code; // [1024]
+  uint32_t* hist_val;  // [1024]
+  uint32_t* hist_len;  // [4096]
+  uint64_t* lb;        // look-back state [nblk], zeroed
+  uint32_t spin_limit;
+};
+
+struct BookArgs {
+  const uint32_t* hist_code;
+  const uint32_t* hist_val;
+  const uint32_t* hist_len;
+  uint8_t* lens;    // 1024 + 1024 + 4096
+  uint64_t* codes;  // 1024 + 1024 + 4096
+  DevState* st;
+};
+
+struct EncodeArgs {
+  Geom g;
+  DevState* st;
+  uint32_t radius;
+  int select;
+  const uint16_t* codes;
+  const uint8_t* lens;
+  const uint64_t* bcodes;
+  const float* mlp_w;
+  float* feat_out;  // optional [nblk][8] features (LEARNED mode)
+  uint8_t* ar;
+  uint64_t cap;
+  uint64_t off_codec, off_bb, off_rec;
+  uint64_t* lb;
+  uint32_t spin_limit;
+};
+
+struct FinalizeArgs {
+  DevState* st;
+  uint8_t* ar;
+  uint64_t cap;
+  int ndim, eb_mode;
+  uint64_t dims[3];
+  double eb_user;
+  uint32_t radius;
+  int select;
+  uint64_t nblk, off_bb, off_rec;
+  const uint8_t* lens;
+};
+
+// decode tables of one canonical book
+struct DecTab {
+  unsigned long long first[kMaxLen + 1];
+  uint32_t count[kMaxLen + 1];
+  uint32_t off[kMaxLen + 1];
+  uint32_t present;
+  uint16_t sorted[kNsymLen];
+  uint32_t lut[1 << kLutBits];  // (symbol << 8) | length, 0 = longer than kLutBits
+};
+
+struct DecodeArgs {
+  Geom g;
+  DevState* st;
+  const uint8_t* ar;
+  uint64_t bytes;
+  uint64_t off_codec, off_bb, off_rec, off_pay, off_books;
+  uint64_t n_rec, payload;
+  uint32_t flags, radius;
+  float ebx2_f;
+  uint64_t* blk_off;   // [nblk+1]
+  uint32_t* rec_start; // [nblk+1]
+  DecTab* tabs;        // [3]
+  uint16_t* codes;     // nblk * 4096
+  float* out;
+};
+
+// ---- launchers (return cudaGetLastError of the launch) ---------------------------
+cudaError_t launch_abs_params(DevState* st, double eb, cudaStream_t s);
+cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, double eb, cudaStream_t s);
+cudaError_t launch_construct(int ndim, const ConstructArgs& a, cudaStream_t s);
+cudaError_t launch_codebook(const BookArgs& a, cudaStream_t s);
+cudaError_t launch_encode(const EncodeArgs& a, cudaStream_t s);
+cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+
+cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);
+
+}  // namespace cszp
