@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark: compress + decompress throughput of the cuSZ+ data-parallel path on GB300.
+
+One step = compress one synthetic field (device-resident FP32) to an archive and
+decompress it back, through the library's C ABI.  Default workload: the 2-D
+1800x3600 GRF (power spectrum k^-3) with 20% exact zeros, value-range-relative
+eb 1e-4, exhaustive per-block choice between Huffman, RLE and RLE+Huffman.
+
+Prints one JSON line (rank 0).  `--impl reference` times the scalar CPU oracle on
+the host cores instead (bounded samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+FLUSH_BYTES = 256 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["2d", "1d", "3d"], default="2d")
+    p.add_argument("--select", default="exhaustive")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload_spec(name, rank=0):
+    from paper_2105_12912_gb300 import synth
+    if name == "2d":
+        return synth.workload_2d(seed=2 + 1000 * rank)
+    if name == "1d":
+        return synth.workload_1d(seed=1 + 1000 * rank)
+    return synth.workload_3d(seed=3 + 1000 * rank, eb=1e-4)
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(kernel, n, nslots, nblk, hdr):
+    """Bytes a kernel must move per launch (measurement)."""
+    payload, n_rec = hdr["payload"], hdr["n_rec"]
+    nh, nr, nrh = hdr["n_codec"]
+    huff_frac = nh / max(1, nblk)
+    if kernel == "range":
+        return 4 * n
+    if kernel == "construct":
+        return 4 * n + 2 * nslots + 8 * n_rec
+    if kernel == "encode":
+        return 2 * nslots + payload + 5 * nblk
+    if kernel == "huff_decode":
+        return int(payload * huff_frac) + int(2 * n * huff_frac)
+    if kernel == "rle_decode":
+        return int(payload * (1 - huff_frac)) + int(2 * n * (1 - huff_frac))
+    if kernel == "reconstruct":
+        return 2 * nslots + 4 * n + 8 * n_rec
+    return 0
+
+
+def run_reference(args):
+    """Reference arm: the scalar C oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2105_12912_gb300 import synth
+    spec = workload_spec(args.workload)
+    x = synth.make_field(spec, "cpu").numpy()
+    # bounded sample: a slab of the field along the slowest axis (~1.3M elements)
+    rows = max(1, min(x.shape[0], int(math.ceil(1_300_000 / max(1, x.size // x.shape[0])))))
+    xs = np.ascontiguousarray(x[:rows])
+    mode = O.EB_REL if spec.eb_mode == "rel" else O.EB_ABS
+    sel = {"huff": 0, "rle": 1, "rle_huff": 2, "heuristic": 3, "exhaustive": 4}[args.select]
+    for _ in range(args.warmup):
+        st, ar = O.compress(xs, mode, spec.eb, select=sel)
+        O.decompress(ar, xs.size)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, ar = O.compress(xs, mode, spec.eb, select=sel)
+        O.decompress(ar, xs.size)
+    t = time.perf_counter() - t0
+    gbs = args.steps * 4 * xs.size / t / 1e9
+    line = {"impl": "reference", "metric": "compress+decompress GB/s (FP32 in)", "value": gbs, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": spec.name, "dims": list(spec.dims), "eb_mode": spec.eb_mode, "eb": spec.eb,
+                       "select": args.select},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {rows} rows of the field ({xs.size} floats) per step"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(spec, x_cpu, select):
+    """The oracle, single-threaded, on a bounded sample (~10-30 s of CPU work)."""
+    from oracle import oracle as O
+    mode = O.EB_REL if spec.eb_mode == "rel" else O.EB_ABS
+    sel = {"huff": 0, "rle": 1, "rle_huff": 2, "heuristic": 3, "exhaustive": 4}.get(select, 4)
+    x = x_cpu.numpy()
+    t0 = time.perf_counter()
+    st, ar = O.compress(x, mode, spec.eb, select=sel)
+    O.decompress(ar, x.size)
+    t = time.perf_counter() - t0
+    reps, sample = 1, "one full compress+decompress round trip of the field"
+    if t > 30:  # the full field is too slow: report the measured time anyway, it is bounded
+        sample += f" ({t:.0f} s)"
+    gbs = reps * 4 * x.size / t / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def run_ours(args):
+    from paper_2105_12912_gb300 import api, synth
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+
+    spec = workload_spec(args.workload, rank)
+    x = synth.make_field(spec, dev)
+    n = x.numel()
+    bytes_in = 4 * n
+    dims = tuple(x.shape)
+    ws = api.Workspace(dev)
+    arc = torch.empty(api.max_archive_bytes(dims), dtype=torch.uint8, device=dev)
+    rec = torch.empty_like(x)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(xin, out_rec):
+        ar, nb, _ = api.compress(xin, spec.eb, spec.eb_mode, select=args.select, out=arc, workspace=ws)
+        api.decompress(ar, nb, out=out_rec, dims=dims, workspace=ws)
+        return nb
+
+    for _ in range(args.warmup):
+        nb = step(x, rec)
+    torch.cuda.synchronize()
+    # correctness guard on the measured configuration
+    err = float((x.double() - rec.double()).abs().max())
+    hdr = api.header(arc)
+    assert err <= hdr["eb_f"], (err, hdr["eb_f"])
+
+    def timed(fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))  # evict the previous step's data from L2 (untimed)
+            evs[i][0].record(stream)
+            fn()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    api.trace_read(reset=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_round = timed(lambda: step(x, rec), args.steps)
+    launches = sum(c for _, c in api.trace_read(reset=True).values())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_step = float(np.mean(t_round))
+    total_ms = float(np.sum(t_round))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * bytes_in / (total_ms * 1e-3) / 1e9
+
+    # compress-only and decompress-only throughput
+    t_c = timed(lambda: api.compress(x, spec.eb, spec.eb_mode, select=args.select, out=arc, workspace=ws),
+                max(10, args.steps // 2))
+    t_d = timed(lambda: api.decompress(arc, nb, out=rec, dims=dims, workspace=ws), max(10, args.steps // 2))
+
+    # per-kernel durations (CUDA events around each launch on the launching stream)
+    api.trace_enable(True)
+    api.trace_read(reset=True)
+    ksteps = max(10, args.steps // 2)
+    timed(lambda: step(x, rec), ksteps)
+    tr = api.trace_read(reset=True)
+    api.trace_enable(False)
+    nslots = 4096 * hdr["nblk"]
+    peak, peak_kind = measured_peak_hbm()
+    kernels = {}
+    for name, (ms, cnt) in tr.items():
+        if cnt == 0:
+            continue
+        avg_ms = ms / cnt
+        ab = algorithmic_bytes(name, n, nslots, hdr["nblk"], hdr)
+        kernels[name] = {"launches": cnt, "avg_us": 1e3 * avg_ms, "share": None,
+                         "alg_bytes": ab, "gbs": (ab / (avg_ms * 1e-3) / 1e9) if ab and avg_ms > 0 else None}
+    tot = sum(v["avg_us"] * v["launches"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = v["avg_us"] * v["launches"] / tot if tot else None
+    dom = max(kernels, key=lambda k: kernels[k]["avg_us"] * kernels[k]["launches"])
+    dk = kernels[dom]
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            ent = tj.get(f"{args.workload}:{dom}")
+            if ent and ent.get("source_rev") == tj.get("kernel_rev"):
+                traffic = ent.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": (dk["gbs"] / peak) if dk["gbs"] else None, "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                "note": "achieved = algorithmic bytes per launch / mean launch time (CUDA events)"}
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        xh = x.cpu().pin_memory()
+        arh = torch.empty(arc.numel(), dtype=torch.uint8, pin_memory=True)
+        outh = torch.empty(dims, dtype=torch.float32, pin_memory=True)
+        xd = torch.empty_like(x)
+        ard = torch.empty_like(arc)
+        nb_box = [0]
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            ar, nbe, _ = api.compress(xd, spec.eb, spec.eb_mode, select=args.select, out=arc, workspace=ws)
+            arh[:nbe].copy_(ar[:nbe], non_blocking=True)
+            ard[:nbe].copy_(arh[:nbe], non_blocking=True)
+            api.decompress(ard, nbe, out=rec, dims=dims, workspace=ws)
+            outh.copy_(rec, non_blocking=True)
+            nb_box[0] = nbe
+
+        t_e = timed(e2e_step, max(10, args.steps // 2))
+        torch.cuda.synchronize()
+        assert torch.equal(outh, rec.cpu())
+        e2e = {"value": world * bytes_in / (np.mean(t_e) * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": bytes_in + nb_box[0], "d2h_bytes_per_step": nb_box[0] + bytes_in}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, x.cpu(), args.select)
+
+    line = {
+        "metric": "compress+decompress GB/s (FP32 in)",
+        "value": value,
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": spec.name, "dims": list(dims), "eb_mode": spec.eb_mode, "eb": spec.eb,
+                   "radius": 512, "select": args.select, "parallelism": f"replicas{world}",
+                   "l2": "flushed (256 MiB write) before every timed step, outside the step's events"},
+        "compress_gbs": world * bytes_in / (np.mean(t_c) * 1e-3) / 1e9,
+        "decompress_gbs": world * bytes_in / (np.mean(t_d) * 1e-3) / 1e9,
+        "cr": bytes_in / nb,
+        "archive_bytes": nb,
+        "codec_blocks": {"huff": hdr["n_codec"][0], "rle": hdr["n_codec"][1], "rle_huff": hdr["n_codec"][2]},
+        "max_abs_err": err,
+        "eb_abs": hdr["eb_f"],
+        "roofline": roofline,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -111,6 +111,19 @@ csz_status csz_decompress(const uint8_t* d_archive, size_t bytes, float* d_out,
 /* Human-readable name of a status. */
 const char* csz_status_string(int status);
 
+/*
+ * Kernel tracing (benchmarking aid; process-global, not thread-safe).
+ * csz_kernel_count() kernels are numbered 0..count-1 and named by csz_kernel_name().
+ * Launch counts are always kept.  While tracing is enabled every launch is bracketed
+ * by CUDA events on the caller's stream and the elapsed milliseconds are added to the
+ * kernel's total at the call's synchronisation.  csz_trace_read fills ms[count] and
+ * launches[count] (either may be NULL) and optionally resets both.
+ */
+int csz_kernel_count(void);
+const char* csz_kernel_name(int id);
+csz_status csz_trace_enable(int on);
+csz_status csz_trace_read(double* ms, uint64_t* launches, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,5 +124,42 @@ def decompress(archive: torch.Tensor, nbytes: int | None = None, out: torch.Tens
     return out, st
 
 
+def header(archive) -> dict:
+    """Parsed 128-byte archive header (from a CUDA/CPU uint8 tensor or bytes)."""
+    import struct
+    if isinstance(archive, torch.Tensor):
+        archive = bytes(archive[:128].cpu().numpy().tobytes())
+    b = bytes(archive[:128])
+    magic, ver, ndim, mode = struct.unpack_from("<IHBB", b, 0)
+    dims = struct.unpack_from("<3Q", b, 8)
+    eb_user, eb_d = struct.unpack_from("<2d", b, 32)
+    eb_f, = struct.unpack_from("<f", b, 48)
+    radius, seg, flags = struct.unpack_from("<3I", b, 52)
+    nblk, nrec, nout, npatch, payload, total = struct.unpack_from("<6Q", b, 64)
+    select, nh, nr, nrh = struct.unpack_from("<4I", b, 112)
+    return dict(magic=magic, version=ver, ndim=ndim, eb_mode=mode, dims=dims[:ndim], eb_user=eb_user, eb_d=eb_d,
+                eb_f=eb_f, radius=radius, huff_seg=seg, flags=flags, nblk=nblk, n_rec=nrec, n_out=nout,
+                n_patch=npatch, payload=payload, total=total, select=select, n_codec=(nh, nr, nrh))
+
+
 def status_string(st: int) -> str:
     return L.lib().csz_status_string(int(st)).decode()
+
+
+def kernel_names():
+    n = L.lib().csz_kernel_count()
+    return [L.lib().csz_kernel_name(i).decode() for i in range(n)]
+
+
+def trace_enable(on: bool = True):
+    L.lib().csz_trace_enable(1 if on else 0)
+
+
+def trace_read(reset: bool = True):
+    """{kernel name: (total ms while tracing, launches)}"""
+    n = L.lib().csz_kernel_count()
+    ms = (C.c_double * n)()
+    cnt = (C.c_uint64 * n)()
+    L.lib().csz_trace_read(ms, cnt, 1 if reset else 0)
+    names = kernel_names()
+    return {names[i]: (float(ms[i]), int(cnt[i])) for i in range(n)}

@@ -99,6 +99,26 @@ csz_status fold(uint32_t bits) {
 
 uint32_t g_spin_limit = kSpinLimit;
 
+// Tracing: CUDA events around every launch while enabled, folded into per-kernel
+// totals at the call's synchronisation; launch counts are always kept.
+struct TraceState {
+  bool on = false;
+  bool armed[K_COUNT] = {};
+  cudaEvent_t ev[K_COUNT][2] = {};
+  double ms[K_COUNT] = {};
+  unsigned long long launches[K_COUNT] = {};
+} g_trace;
+
+void trace_collect() {
+  if (!g_trace.on) return;
+  for (int k = 0; k < K_COUNT; k++) {
+    if (!g_trace.armed[k]) continue;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, g_trace.ev[k][0], g_trace.ev[k][1]) == cudaSuccess) g_trace.ms[k] += ms;
+    g_trace.armed[k] = false;
+  }
+}
+
 struct Header {
   uint32_t magic;
   uint16_t version;
@@ -152,7 +172,50 @@ csz_status parse_header(const uint8_t* h, size_t bytes, Header& H, Geom& g, bool
 
 }  // namespace
 
+namespace cszp {
+void trace_begin(int id, cudaStream_t s) {
+  g_trace.launches[id]++;
+  if (!g_trace.on) return;
+  if (!g_trace.ev[id][0]) {
+    cudaEventCreate(&g_trace.ev[id][0]);
+    cudaEventCreate(&g_trace.ev[id][1]);
+  }
+  cudaEventRecord(g_trace.ev[id][0], s);
+}
+void trace_end(int id, cudaStream_t s) {
+  if (!g_trace.on) return;
+  cudaEventRecord(g_trace.ev[id][1], s);
+  g_trace.armed[id] = true;
+}
+}  // namespace cszp
+
 extern "C" {
+
+static const char* const kKernelNames[K_COUNT] = {
+    "range", "abs_params", "construct", "codebook", "encode", "finalize", "dec_prep",
+    "dec_records", "dec_tables", "huff_decode", "rle_decode", "reconstruct"};
+
+int csz_kernel_count(void) { return K_COUNT; }
+
+const char* csz_kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kKernelNames[id] : ""; }
+
+csz_status csz_trace_enable(int on) {
+  g_trace.on = on != 0;
+  return CSZ_OK;
+}
+
+csz_status csz_trace_read(double* ms, uint64_t* launches, int reset) {
+  for (int k = 0; k < K_COUNT; k++) {
+    if (ms) ms[k] = g_trace.ms[k];
+    if (launches) launches[k] = g_trace.launches[k];
+    if (reset) {
+      g_trace.ms[k] = 0.0;
+      g_trace.launches[k] = 0;
+    }
+  }
+  return CSZ_OK;
+}
+
 
 const char* csz_status_string(int s) {
   switch (s) {
@@ -271,6 +334,7 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   DevState hs;
   if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  trace_collect();
   const csz_status r = fold(hs.status);
   if (r != CSZ_OK) return r;
   *h_bytes = (size_t)hs.total;
@@ -333,6 +397,7 @@ csz_status csz_decompress(const uint8_t* d_ar, size_t bytes, float* d_out, uint6
   DevState hs;
   if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  trace_collect();
   return fold(hs.status);
 }
 

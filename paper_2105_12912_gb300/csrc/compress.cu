@@ -1005,7 +1005,9 @@ __global__ void finalize_kernel(FinalizeArgs a) {
 // launchers
 // =================================================================================
 cudaError_t launch_abs_params(DevState* st, double eb, cudaStream_t s) {
+  trace_begin(K_PARAMS, s);
   abs_params_kernel<<<1, 32, 0, s>>>(st, eb);
+  trace_end(K_PARAMS, s);
   return cudaGetLastError();
 }
 
@@ -1016,12 +1018,15 @@ cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, dou
   uint64_t want = (n / 4 + 255) / 256;
   uint64_t grid = want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8;
   if (grid == 0) grid = 1;
+  trace_begin(K_RANGE, s);
   range_kernel<<<(unsigned)grid, 256, 0, s>>>(x, n, st, mode, eb);
+  trace_end(K_RANGE, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_construct(int ndim, const ConstructArgs& a, cudaStream_t s) {
   const size_t sm = construct_smem_bytes();
+  trace_begin(K_CONSTRUCT, s);
   if (ndim == 1) {
     construct_kernel<1><<<a.g.nblk, kConstructThreads, sm, s>>>(a);
   } else if (ndim == 2) {
@@ -1029,6 +1034,7 @@ cudaError_t launch_construct(int ndim, const ConstructArgs& a, cudaStream_t s) {
   } else {
     construct_kernel<3><<<a.g.nblk, kConstructThreads, sm, s>>>(a);
   }
+  trace_end(K_CONSTRUCT, s);
   return cudaGetLastError();
 }
 
@@ -1036,17 +1042,23 @@ cudaError_t launch_codebook(const BookArgs& a, cudaStream_t s) {
   const size_t sm = codebook_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  trace_begin(K_CODEBOOK, s);
   codebook_kernel<<<3, kBookThreads, sm, s>>>(a);
+  trace_end(K_CODEBOOK, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_encode(const EncodeArgs& a, cudaStream_t s) {
+  trace_begin(K_ENCODE, s);
   encode_kernel<<<a.g.nblk, kEncThreads, encode_smem_bytes(), s>>>(a);
+  trace_end(K_ENCODE, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
+  trace_begin(K_FINALIZE, s);
   finalize_kernel<<<1, 256, 0, s>>>(a);
+  trace_end(K_FINALIZE, s);
   return cudaGetLastError();
 }
 

@@ -501,21 +501,33 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) 
 }
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
+  trace_begin(K_DEC_PREP, s);
   dec_prep_kernel<<<1, 1024, 0, s>>>(a);
+  trace_end(K_DEC_PREP, s);
   const uint64_t n = (a.n_rec > (uint64_t)a.g.nblk + 1 ? a.n_rec : (uint64_t)a.g.nblk + 1);
   uint64_t grid = (n + 255) / 256;
   if (grid > 4096) grid = 4096;
+  trace_begin(K_DEC_RECORDS, s);
   dec_records_kernel<<<(unsigned)grid, 256, 0, s>>>(a);
+  trace_end(K_DEC_RECORDS, s);
+  trace_begin(K_DEC_TABLES, s);
   dec_tables_kernel<<<3, 1024, 0, s>>>(a);
+  trace_end(K_DEC_TABLES, s);
   const uint64_t nseg = (uint64_t)a.g.nblk * 4;
+  trace_begin(K_HUFF_DECODE, s);
   huff_decode_kernel<<<(unsigned)((nseg + kHuffDecThreads - 1) / kHuffDecThreads), kHuffDecThreads, 0, s>>>(a);
+  trace_end(K_HUFF_DECODE, s);
+  trace_begin(K_RLE_DECODE, s);
   rle_decode_kernel<<<a.g.nblk, kRleThreads, 0, s>>>(a);
+  trace_end(K_RLE_DECODE, s);
+  trace_begin(K_RECONSTRUCT, s);
   if (a.g.ndim == 1)
     reconstruct_kernel<1><<<a.g.nblk, kRecThreads, 0, s>>>(a);
   else if (a.g.ndim == 2)
     reconstruct_kernel<2><<<a.g.nblk, kRecThreads, 0, s>>>(a);
   else
     reconstruct_kernel<3><<<a.g.nblk, kRecThreads, 0, s>>>(a);
+  trace_end(K_RECONSTRUCT, s);
   return cudaGetLastError();
 }
 

@@ -89,6 +89,25 @@ struct DecodeArgs {
   float* out;
 };
 
+// ---- per-kernel tracing (CUDA events around each launch; defined in api.cu) -------
+enum KernelId : int {
+  K_RANGE = 0,
+  K_PARAMS,
+  K_CONSTRUCT,
+  K_CODEBOOK,
+  K_ENCODE,
+  K_FINALIZE,
+  K_DEC_PREP,
+  K_DEC_RECORDS,
+  K_DEC_TABLES,
+  K_HUFF_DECODE,
+  K_RLE_DECODE,
+  K_RECONSTRUCT,
+  K_COUNT
+};
+void trace_begin(int id, cudaStream_t s);
+void trace_end(int id, cudaStream_t s);
+
 // ---- launchers (return cudaGetLastError of the launch) ---------------------------
 cudaError_t launch_abs_params(DevState* st, double eb, cudaStream_t s);
 cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, double eb, cudaStream_t s);
