@@ -108,6 +108,27 @@ csz_status csz_decompress(const uint8_t* d_archive, size_t bytes, float* d_out,
                           uint64_t out_cap_elems, void* d_workspace, size_t workspace_bytes,
                           void* stream);
 
+/*
+ * Decompression that allocates nothing and takes no workspace.  Some callers cannot
+ * call cudaMalloc: a compression filter plug-in inside an I/O library is handed only
+ * the archive and the output buffer, and an application whose device memory is all
+ * reserved by its own pool allocator cannot let a library allocate beside it.  This
+ * entry point uses a scratch array the library holds on every GPU that loads it
+ * (768 KiB, kept until the process exits) instead of a workspace.  The paper has no
+ * counterpart; it is a convenience of this library.
+ *
+ * Limit: archives of at most 64 codec blocks (1-D: 262,144 elements; 2-D: 64 blocks
+ * of 64x64; 3-D: 64 blocks of 16^3).  Larger archives return CSZ_E_CAPACITY before
+ * any device work.  Other arguments, output and errors as for csz_decompress.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture starts.
+ * Every call shares the one array, which keeps the previous call's contents (each
+ * call clears the status word it needs zeroed): calls that overlap on the GPU, from
+ * two streams or two host threads, race and must be serialised by the caller.
+ */
+csz_status csz_decompress_static(const uint8_t* d_archive, size_t bytes, float* d_out,
+                                 uint64_t out_cap_elems, void* stream);
+
 /* Human-readable name of a status. */
 const char* csz_status_string(int status);
 

@@ -37,6 +37,7 @@ SIGNATURES = {
                                    C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     "csz_decompress": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t,
                                  C.c_void_p]),
+    "csz_decompress_static": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint64, C.c_void_p]),
     "csz_status_string": (C.c_char_p, [C.c_int]),
     "csz_kernel_count": (C.c_int, []),
     "csz_kernel_name": (C.c_char_p, [C.c_int]),
