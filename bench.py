@@ -125,10 +125,10 @@ def algorithmic_bytes(kernel, n, nslots, nblk, hdr):
         return 4 * n + 2 * nslots + 8 * n_rec
     if kernel == "encode":
         return 2 * nslots + payload + 5 * nblk
-    if kernel == "huff_decode":
-        return int(payload * huff_frac) + int(2 * n * huff_frac)
-    if kernel == "rle_decode":
-        return int(payload * (1 - huff_frac)) + int(2 * n * (1 - huff_frac))
+    if kernel == "stream_decode":
+        return payload + int(2 * n * huff_frac)
+    if kernel == "rle_expand":
+        return int(2 * n * (1 - huff_frac))
     if kernel == "reconstruct":
         return 2 * nslots + 4 * n + 8 * n_rec
     return 0

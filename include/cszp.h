@@ -114,7 +114,7 @@ csz_status csz_decompress(const uint8_t* d_archive, size_t bytes, float* d_out,
  * the archive and the output buffer, and an application whose device memory is all
  * reserved by its own pool allocator cannot let a library allocate beside it.  This
  * entry point uses a scratch array the library holds on every GPU that loads it
- * (768 KiB, kept until the process exits) instead of a workspace.  The paper has no
+ * (1.25 MiB, kept until the process exits) instead of a workspace.  The paper has no
  * counterpart; it is a convenience of this library.
  *
  * Limit: archives of at most 64 codec blocks (1-D: 262,144 elements; 2-D: 64 blocks

@@ -35,7 +35,6 @@
 #define HDR 128
 #define MAGIC 0x2B5A5343u /* "CSZ+" */
 #define VERSION 1
-#define HUFF_SEG 1024    /* symbols per Huffman segment */
 #define MAXLEN 64
 
 /* ------------------------------------------------------------------------------- */
@@ -521,89 +520,151 @@ static void build_dectab(const uint8_t* len, int nsym, dectab_t* t) {
     }
 }
 
-/* MSB-first bit writer into 32-bit words */
-typedef struct {
-  uint32_t* w;
-  uint64_t pos;
-} bitw_t;
-
-static void put_bits(bitw_t* b, uint64_t code, int len) {
-  for (int i = len - 1; i >= 0; i--) {
-    uint64_t bit = (code >> i) & 1u;
-    if (bit) b->w[b->pos >> 5] |= 1u << (31 - (b->pos & 31));
-    b->pos++;
-  }
-}
-
-static int get_bit(const uint32_t* w, uint64_t pos) { return (int)((w[pos >> 5] >> (31 - (pos & 31))) & 1u); }
-
-/* decode one symbol starting at *pos, bits available up to nbits */
-static int decode_sym(const dectab_t* t, const uint32_t* w, uint64_t* pos, uint64_t nbits) {
-  uint64_t c = 0;
-  for (int l = 1; l <= MAXLEN; l++) {
-    if (*pos >= nbits) return -1;
-    c = (c << 1) | (uint64_t)get_bit(w, *pos);
-    (*pos)++;
-    if (t->count[l] && c >= t->first[l] && c - t->first[l] < t->count[l])
-      return t->sorted[t->offset[l] + (c - t->first[l])];
-  }
-  return -1;
-}
-
 static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 static uint64_t align4(uint64_t a) { return (a + 3) & ~3ull; }
 static uint64_t align8(uint64_t a) { return (a + 7) & ~7ull; }
 
 /* ------------------------------------------------------------------------------- */
-/* per-block payloads                                                               */
-/*   HUFF      : u16 words[S] (padded to 4 B), then S word-aligned segments of at   */
-/*               most 1024 symbols, bits MSB-first                                   */
-/*   RLE       : u16 value[nr], u16 length[nr]                                       */
-/*   RLE_HUFF  : u32 nr, u32 value-words, value bits, length bits (length-1 coded)   */
+/* Interleaved Huffman stream (the concatenated codes of Sec. II-A Step-7/8, laid   */
+/* out for a 32-lane decoder).  Symbol i of a sequence belongs to lane i % 32.  A   */
+/* lane's bit string is its symbols' codes, MSB first, zero-padded to a multiple of */
+/* 16 and cut into 16-bit units (first bit = MSB of the unit).  Units are stored in */
+/* the order a 32-lane decoder reads them: at step t the lanes holding symbols      */
+/* 32t..32t+31 top up in rounds -- in each round every lane whose next code is      */
+/* longer than the bits it holds takes one unit, lanes in increasing order -- and   */
+/* then all of them consume their code.                                             */
 /* ------------------------------------------------------------------------------- */
+#define LANES 32
+#define UNIT 16
 
-static uint64_t huff_size(const uint16_t* c, uint64_t m, const uint8_t* len, int* missing) {
-  uint64_t S = ceil_div(m, HUFF_SEG), bytes = align4(2 * S);
-  for (uint64_t s = 0; s < S; s++) {
-    uint64_t bits = 0, e = (s + 1) * HUFF_SEG < m ? (s + 1) * HUFF_SEG : m;
-    for (uint64_t i = s * HUFF_SEG; i < e; i++) {
-      if (!len[c[i]]) *missing = 1;
-      bits += len[c[i]];
-    }
-    bytes += 4 * ceil_div(bits, 32);
+typedef struct {
+  uint16_t* u;
+  uint64_t bits;
+} lane_t;
+
+static void lane_put(lane_t* L, uint64_t code, int len) {
+  for (int i = len - 1; i >= 0; i--) {
+    if ((code >> i) & 1u) L->u[L->bits >> 4] |= (uint16_t)(1u << (15 - (L->bits & 15)));
+    L->bits++;
   }
-  return bytes;
 }
 
-static uint64_t rlehuff_size(const run_t* runs, uint64_t nr, const uint8_t* vlen,
-                             const uint8_t* llen, int* missing) {
-  uint64_t vb = 0, lb = 0;
-  for (uint64_t i = 0; i < nr; i++) {
-    if (!vlen[runs[i].v] || !llen[runs[i].len - 1]) *missing = 1;
-    vb += vlen[runs[i].v];
-    lb += llen[runs[i].len - 1];
+/* number of units of the stream; writes them to out unless out is NULL */
+static uint64_t ihs_encode(const uint16_t* sym, uint64_t N, int add, const uint8_t* len,
+                           const uint64_t* code, uint16_t* out, int* missing) {
+  lane_t L[LANES];
+  const uint64_t per = ceil_div(N, LANES);
+  for (int l = 0; l < LANES; l++) {
+    L[l].u = (uint16_t*)calloc(ceil_div(per * MAXLEN, UNIT) + 1, sizeof(uint16_t));
+    L[l].bits = 0;
   }
-  return 8 + 4 * ceil_div(vb, 32) + 4 * ceil_div(lb, 32);
+  for (uint64_t i = 0; i < N; i++) {
+    const int s = sym[i] + add;
+    if (!len[s]) *missing = 1;
+    lane_put(&L[i % LANES], code[s], len[s]);
+  }
+  int nb[LANES] = {0};
+  uint64_t next[LANES] = {0}, pos = 0;
+  for (uint64_t t = 0; t * LANES < N; t++) {
+    for (;;) {
+      int any = 0;
+      for (uint64_t l = 0; l < LANES && t * LANES + l < N; l++) {
+        if (len[sym[t * LANES + l] + add] > nb[l]) {
+          if (out) out[pos] = L[l].u[next[l]];
+          next[l]++;
+          pos++;
+          nb[l] += UNIT;
+          any = 1;
+        }
+      }
+      if (!any) break;
+    }
+    for (uint64_t l = 0; l < LANES && t * LANES + l < N; l++) nb[l] -= len[sym[t * LANES + l] + add];
+  }
+  for (int l = 0; l < LANES; l++) free(L[l].u);
+  return pos;
+}
+
+/* length of the codeword that is a prefix of the nb valid top bits of buf, 0 if none */
+static int match_len(const dectab_t* t, uint64_t buf, int nb) {
+  for (int l = 1; l <= nb && l <= MAXLEN; l++) {
+    uint64_t c = buf >> (64 - l);
+    if (t->count[l] && c >= t->first[l] && c - t->first[l] < t->count[l]) return l;
+  }
+  return 0;
+}
+
+/* decode N symbols from the units in[0..avail); returns the units read, -1 if the
+   stream is damaged (a lane needs bits it cannot hold, or the units run out) */
+static int64_t ihs_decode(const uint16_t* in, uint64_t avail, uint64_t N, const dectab_t* t,
+                          uint16_t* out) {
+  uint64_t buf[LANES] = {0}, pos = 0;
+  int nb[LANES] = {0};
+  for (uint64_t s = 0; s * LANES < N; s++) {
+    for (;;) {
+      int any = 0;
+      for (uint64_t l = 0; l < LANES && s * LANES + l < N; l++) {
+        if (match_len(t, buf[l], nb[l]) == 0) {
+          if (nb[l] > 64 - UNIT || pos >= avail) return -1;
+          buf[l] |= (uint64_t)in[pos++] << (64 - UNIT - nb[l]);
+          nb[l] += UNIT;
+          any = 1;
+        }
+      }
+      if (!any) break;
+    }
+    for (uint64_t l = 0; l < LANES && s * LANES + l < N; l++) {
+      const int ml = match_len(t, buf[l], nb[l]);
+      const uint64_t c = buf[l] >> (64 - ml);
+      out[s * LANES + l] = t->sorted[t->offset[ml] + (c - t->first[ml])];
+      buf[l] = ml == 64 ? 0 : buf[l] << ml;
+      nb[l] -= ml;
+    }
+  }
+  return (int64_t)pos;
+}
+
+/* ------------------------------------------------------------------------------- */
+/* per-block payloads                                                               */
+/*   HUFF      : interleaved stream of the block's codes (u16 units, padded to 4 B)  */
+/*   RLE       : u16 value[nr], u16 length[nr]                                       */
+/*   RLE_HUFF  : u32 nr, u32 value units, value stream, length stream (length-1      */
+/*               coded), padded to 4 B                                               */
+/* ------------------------------------------------------------------------------- */
+
+static uint64_t huff_size(const uint16_t* c, uint64_t m, const uint8_t* len, const uint64_t* code,
+                          int* missing) {
+  return align4(2 * ihs_encode(c, m, 0, len, code, NULL, missing));
+}
+
+static void run_streams(const run_t* runs, uint64_t nr, uint16_t* v, uint16_t* l) {
+  for (uint64_t i = 0; i < nr; i++) {
+    v[i] = runs[i].v;
+    l[i] = runs[i].len;
+  }
+}
+
+static uint64_t rlehuff_size(const run_t* runs, uint64_t nr, const uint8_t* vlen, const uint64_t* vcode,
+                             const uint8_t* llen, const uint64_t* lcode, int* missing) {
+  uint16_t* v = (uint16_t*)malloc((nr + 1) * 2);
+  uint16_t* l = (uint16_t*)malloc((nr + 1) * 2);
+  run_streams(runs, nr, v, l);
+  uint64_t vu = ihs_encode(v, nr, 0, vlen, vcode, NULL, missing);
+  uint64_t lu = ihs_encode(l, nr, -1, llen, lcode, NULL, missing);
+  free(v);
+  free(l);
+  return align4(8 + 2 * (vu + lu));
 }
 
 static void huff_write(const uint16_t* c, uint64_t m, const uint8_t* len, const uint64_t* code,
                        uint8_t* out) {
-  uint64_t S = ceil_div(m, HUFF_SEG), hdr = align4(2 * S);
-  memset(out, 0, hdr);
-  uint8_t* p = out + hdr;
-  for (uint64_t s = 0; s < S; s++) {
-    uint64_t bits = 0, e = (s + 1) * HUFF_SEG < m ? (s + 1) * HUFF_SEG : m;
-    for (uint64_t i = s * HUFF_SEG; i < e; i++) bits += len[c[i]];
-    uint64_t nw = ceil_div(bits, 32);
-    uint32_t* w = (uint32_t*)calloc(nw + 1, 4);
-    bitw_t bw = {w, 0};
-    for (uint64_t i = s * HUFF_SEG; i < e; i++) put_bits(&bw, code[c[i]], len[c[i]]);
-    memcpy(p, w, nw * 4);
-    p += nw * 4;
-    uint16_t nw16 = (uint16_t)nw;
-    memcpy(out + 2 * s, &nw16, 2);
-    free(w);
-  }
+  int missing = 0;
+  uint64_t nu = ihs_encode(c, m, 0, len, code, NULL, &missing);
+  uint16_t* u = (uint16_t*)calloc(nu + 2, sizeof(uint16_t));
+  ihs_encode(c, m, 0, len, code, u, &missing);
+  memset(out, 0, align4(2 * nu));
+  memcpy(out, u, 2 * nu);
+  free(u);
 }
 
 static void rle_write(const run_t* runs, uint64_t nr, uint8_t* out) {
@@ -616,31 +677,36 @@ static void rle_write(const run_t* runs, uint64_t nr, uint8_t* out) {
 static void rlehuff_write(const run_t* runs, uint64_t nr, const uint8_t* vlen,
                           const uint64_t* vcode, const uint8_t* llen, const uint64_t* lcode,
                           uint8_t* out) {
-  uint64_t vb = 0, lb = 0;
-  for (uint64_t i = 0; i < nr; i++) {
-    vb += vlen[runs[i].v];
-    lb += llen[runs[i].len - 1];
-  }
-  uint64_t vw = ceil_div(vb, 32), lw = ceil_div(lb, 32);
-  uint32_t h[2] = {(uint32_t)nr, (uint32_t)vw};
+  int missing = 0;
+  uint16_t* v = (uint16_t*)malloc((nr + 1) * 2);
+  uint16_t* l = (uint16_t*)malloc((nr + 1) * 2);
+  run_streams(runs, nr, v, l);
+  uint64_t vu = ihs_encode(v, nr, 0, vlen, vcode, NULL, &missing);
+  uint64_t lu = ihs_encode(l, nr, -1, llen, lcode, NULL, &missing);
+  uint16_t* u = (uint16_t*)calloc(vu + lu + 2, sizeof(uint16_t));
+  ihs_encode(v, nr, 0, vlen, vcode, u, &missing);
+  ihs_encode(l, nr, -1, llen, lcode, u + vu, &missing);
+  uint32_t h[2] = {(uint32_t)nr, (uint32_t)vu};
+  memset(out, 0, align4(8 + 2 * (vu + lu)));
   memcpy(out, h, 8);
-  uint32_t* w = (uint32_t*)calloc(vw + lw + 1, 4);
-  bitw_t bv = {w, 0};
-  for (uint64_t i = 0; i < nr; i++) put_bits(&bv, vcode[runs[i].v], vlen[runs[i].v]);
-  bitw_t bl = {w + vw, 0};
-  for (uint64_t i = 0; i < nr; i++) put_bits(&bl, lcode[runs[i].len - 1], llen[runs[i].len - 1]);
-  memcpy(out + 8, w, (vw + lw) * 4);
-  free(w);
+  memcpy(out + 8, u, 2 * (vu + lu));
+  free(u);
+  free(v);
+  free(l);
 }
 
 int orc_block_sizes(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_t radius,
                     const uint8_t* code_len, const uint8_t* val_len, const uint8_t* len_len,
-                    uint32_t huff_seg, uint64_t* sizes) {
+                    uint32_t lanes, uint64_t* sizes) {
   geom_t g;
   int st = make_geom(ndim, dims, &g);
   if (st) return st;
   (void)radius;
-  if (huff_seg != HUFF_SEG) return ORC_E_ARG;
+  if (lanes != LANES) return ORC_E_ARG;
+  uint64_t ccode[NSYM_CODE], vcode[NSYM_CODE], lcode[NSYM_LEN];
+  orc_canonical_codes(code_len, NSYM_CODE, ccode);
+  orc_canonical_codes(val_len, NSYM_CODE, vcode);
+  orc_canonical_codes(len_len, NSYM_LEN, lcode);
   run_t* runs = (run_t*)malloc(SLOTS * sizeof(run_t));
   int missing = 0;
   for (uint64_t b = 0; b < g.nblk; b++) {
@@ -648,9 +714,9 @@ int orc_block_sizes(const uint16_t* codes, int ndim, const uint64_t* dims, uint3
     const uint16_t* c = codes + b * SLOTS;
     uint64_t nr = make_runs(c, m, runs);
     int miss_h = 0, miss_r = 0;
-    sizes[3 * b + ORC_CODEC_HUFF] = huff_size(c, m, code_len, &miss_h);
+    sizes[3 * b + ORC_CODEC_HUFF] = huff_size(c, m, code_len, ccode, &miss_h);
     sizes[3 * b + ORC_CODEC_RLE] = 4 * nr;
-    sizes[3 * b + ORC_CODEC_RLE_HUFF] = rlehuff_size(runs, nr, val_len, len_len, &miss_r);
+    sizes[3 * b + ORC_CODEC_RLE_HUFF] = rlehuff_size(runs, nr, val_len, vcode, len_len, lcode, &miss_r);
     missing |= miss_h | miss_r;
   }
   free(runs);
@@ -877,7 +943,7 @@ typedef struct {
   uint64_t dims[3];
   double eb_user, eb_d;
   float eb_f;
-  uint32_t radius, huff_seg, flags;
+  uint32_t radius, lanes, flags;
   uint64_t nblk, n_rec, n_out, n_patch, payload, total;
   uint32_t select, n_codec[3];
 } hdr_t;
@@ -906,7 +972,7 @@ static void write_header(uint8_t* o, const hdr_t* h) {
   memcpy(o + 40, &h->eb_d, 8);
   memcpy(o + 48, &h->eb_f, 4);
   put32(o + 52, h->radius);
-  put32(o + 56, h->huff_seg);
+  put32(o + 56, h->lanes);
   put32(o + 60, h->flags);
   put64(o + 64, h->nblk);
   put64(o + 72, h->n_rec);
@@ -928,7 +994,7 @@ static void read_header(const uint8_t* o, hdr_t* h) {
   memcpy(&h->eb_d, o + 40, 8);
   memcpy(&h->eb_f, o + 48, 4);
   h->radius = get32(o + 52);
-  h->huff_seg = get32(o + 56);
+  h->lanes = get32(o + 56);
   h->flags = get32(o + 60);
   h->nblk = get64(o + 64);
   h->n_rec = get64(o + 72);
@@ -991,7 +1057,7 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
   orc_canonical_codes(clen, NSYM_CODE, ccode);
   orc_canonical_codes(vlen, NSYM_CODE, vcode);
   orc_canonical_codes(llen, NSYM_LEN, lcode);
-  st = orc_block_sizes(codes, ndim, dims, radius, clen, vlen, llen, HUFF_SEG, sizes);
+  st = orc_block_sizes(codes, ndim, dims, radius, clen, vlen, llen, LANES, sizes);
   if (st) goto done;
 
   /* codec per block */
@@ -1046,7 +1112,7 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
   h.eb_d = eb_d;
   h.eb_f = eb_f;
   h.radius = radius;
-  h.huff_seg = HUFF_SEG;
+  h.lanes = LANES;
   h.flags = flags;
   h.nblk = g.nblk;
   h.n_rec = nrec;
@@ -1120,7 +1186,7 @@ static int parse(const uint8_t* ar, size_t bytes, parsed_t* P) {
   if (make_geom(h->ndim, h->dims, &P->g)) return ORC_E_CORRUPT;
   for (int i = h->ndim; i < 3; i++)
     if (h->dims[i]) return ORC_E_CORRUPT;
-  if (h->radius < 1 || h->radius > 512 || h->huff_seg != HUFF_SEG || h->flags > 3) return ORC_E_CORRUPT;
+  if (h->radius < 1 || h->radius > 512 || h->lanes != LANES || h->flags > 3) return ORC_E_CORRUPT;
   if (h->nblk != P->g.nblk || h->n_rec != h->n_out + h->n_patch) return ORC_E_CORRUPT;
   if (!(h->eb_f > 0.0f) || !isfinite(2.0f * h->eb_f)) return ORC_E_CORRUPT;
   if (h->n_rec > 2 * P->g.nelem || h->payload > bytes || (h->payload & 3)) return ORC_E_CORRUPT;
@@ -1166,28 +1232,15 @@ static int decode_block(const parsed_t* P, const uint8_t* pay, uint64_t bytes, i
                         uint16_t* c) {
   const uint32_t nsym = 2 * P->h.radius;
   if (codec == ORC_CODEC_HUFF) {
-    uint64_t S = ceil_div(m, HUFF_SEG), hdr = align4(2 * S);
-    if (hdr > bytes) return ORC_E_CORRUPT;
-    uint64_t off = hdr;
-    for (uint64_t s = 0; s < S; s++) {
-      uint16_t nw;
-      memcpy(&nw, pay + 2 * s, 2);
-      if (off + 4ull * nw > bytes) return ORC_E_CORRUPT;
-      uint32_t* w = (uint32_t*)malloc(4ull * nw + 4);
-      memcpy(w, pay + off, 4ull * nw);
-      uint64_t pos = 0, e = (s + 1) * HUFF_SEG < m ? (s + 1) * HUFF_SEG : m;
-      for (uint64_t i = s * HUFF_SEG; i < e; i++) {
-        int sym = decode_sym(tc, w, &pos, 32ull * nw);
-        if (sym < 0 || (uint32_t)sym >= nsym) {
-          free(w);
-          return ORC_E_CORRUPT;
-        }
-        c[i] = (uint16_t)sym;
-      }
-      free(w);
-      off += 4ull * nw;
-    }
-    return off == bytes ? ORC_OK : ORC_E_CORRUPT;
+    uint64_t nu = bytes / 2;
+    uint16_t* u = (uint16_t*)malloc((nu + 1) * sizeof(uint16_t));
+    memcpy(u, pay, 2 * nu);
+    int64_t used = ihs_decode(u, nu, m, tc, c);
+    free(u);
+    if (used < 0 || align4(2 * (uint64_t)used) != bytes) return ORC_E_CORRUPT;
+    for (uint64_t i = 0; i < m; i++)
+      if (c[i] >= nsym) return ORC_E_CORRUPT;
+    return ORC_OK;
   }
   run_t* runs = (run_t*)malloc((SLOTS + 1) * sizeof(run_t));
   uint64_t nr;
@@ -1207,27 +1260,30 @@ static int decode_block(const parsed_t* P, const uint8_t* pay, uint64_t bytes, i
       return ORC_E_CORRUPT;
     }
     nr = get32(pay);
-    uint64_t vw = get32(pay + 4);
-    if (nr > m || 8 + 4 * vw > bytes) {
+    uint64_t vu = get32(pay + 4);
+    if (nr > m || 8 + 2 * vu > bytes) {
       free(runs);
       return ORC_E_CORRUPT;
     }
-    uint64_t lw = (bytes - 8 - 4 * vw) / 4;
-    uint32_t* w = (uint32_t*)malloc(4 * (vw + lw) + 4);
-    memcpy(w, pay + 8, 4 * (vw + lw));
-    uint64_t pv = 0, pl = 0;
-    for (uint64_t i = 0; i < nr; i++) {
-      int v = decode_sym(tv, w, &pv, 32 * vw);
-      int l = decode_sym(tl, w + vw, &pl, 32 * lw);
-      if (v < 0 || l < 0) {
-        free(w);
-        free(runs);
-        return ORC_E_CORRUPT;
-      }
-      runs[i].v = (uint16_t)v;
-      runs[i].len = (uint16_t)(l + 1);
+    uint64_t lavail = (bytes - 8) / 2 - vu;
+    uint16_t* u = (uint16_t*)malloc((vu + lavail + 1) * sizeof(uint16_t));
+    uint16_t* v = (uint16_t*)malloc((nr + 1) * sizeof(uint16_t));
+    uint16_t* l = (uint16_t*)malloc((nr + 1) * sizeof(uint16_t));
+    memcpy(u, pay + 8, 2 * (vu + lavail));
+    int64_t uv = ihs_decode(u, vu, nr, tv, v);
+    int64_t ul = ihs_decode(u + vu, lavail, nr, tl, l);
+    int ok = uv >= 0 && (uint64_t)uv == vu && ul >= 0 && align4(8 + 2 * (vu + (uint64_t)ul)) == bytes;
+    for (uint64_t i = 0; ok && i < nr; i++) {
+      runs[i].v = v[i];
+      runs[i].len = (uint16_t)(l[i] + 1);
     }
-    free(w);
+    free(u);
+    free(v);
+    free(l);
+    if (!ok) {
+      free(runs);
+      return ORC_E_CORRUPT;
+    }
   }
   uint64_t pos = 0;
   for (uint64_t i = 0; i < nr; i++) {

@@ -90,10 +90,11 @@ int orc_run_stats(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_
 int orc_huffman_lengths(const uint32_t* freq, int nsym, uint8_t* len);
 int orc_canonical_codes(const uint8_t* len, int nsym, uint64_t* code);
 
-/* per-block exact encoded sizes [nblk][3] (bytes) for the three codecs */
+/* per-block exact encoded sizes [nblk][3] (bytes) for the three codecs; lanes must
+   be 32 (the interleave width of Huffman streams) */
 int orc_block_sizes(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_t radius,
                     const uint8_t* code_len, const uint8_t* val_len, const uint8_t* len_len,
-                    uint32_t huff_seg, uint64_t* sizes);
+                    uint32_t lanes, uint64_t* sizes);
 
 /* per-block selector features [nblk][8] */
 int orc_block_features(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_t radius,

@@ -197,7 +197,7 @@ def block_sizes(codes, dims, radius, code_len, val_len, len_len):
     c = np.ascontiguousarray(codes, dtype=np.uint16)
     a, b, d = (np.ascontiguousarray(v, dtype=np.uint8) for v in (code_len, val_len, len_len))
     st = lib().orc_block_sizes(_p(c, _u16p), len(dims), _p(_dims(dims), _u64p), int(radius), _p(a, _u8p),
-                               _p(b, _u8p), _p(d, _u8p), 1024, _p(out, _u64p))
+                               _p(b, _u8p), _p(d, _u8p), 32, _p(out, _u64p))
     if st:
         raise OracleError(st, "block_sizes")
     return out
@@ -257,11 +257,11 @@ def parse_header(ar):
     dims = struct.unpack_from("<3Q", b, 8)
     eb_user, eb_d = struct.unpack_from("<2d", b, 32)
     eb_f, = struct.unpack_from("<f", b, 48)
-    radius, seg, flags = struct.unpack_from("<3I", b, 52)
+    radius, lanes, flags = struct.unpack_from("<3I", b, 52)
     nblk, nrec, nout, npatch, payload, total = struct.unpack_from("<6Q", b, 64)
     select, nh, nr, nrh = struct.unpack_from("<4I", b, 112)
     return dict(magic=magic, version=ver, ndim=ndim, eb_mode=mode, dims=dims[:ndim], eb_user=eb_user, eb_d=eb_d,
-                eb_f=eb_f, radius=radius, huff_seg=seg, flags=flags, nblk=nblk, n_rec=nrec, n_out=nout,
+                eb_f=eb_f, radius=radius, lanes=lanes, flags=flags, nblk=nblk, n_rec=nrec, n_out=nout,
                 n_patch=npatch, payload=payload, total=total, select=select, n_codec=(nh, nr, nrh))
 
 

@@ -134,11 +134,11 @@ def header(archive) -> dict:
     dims = struct.unpack_from("<3Q", b, 8)
     eb_user, eb_d = struct.unpack_from("<2d", b, 32)
     eb_f, = struct.unpack_from("<f", b, 48)
-    radius, seg, flags = struct.unpack_from("<3I", b, 52)
+    radius, lanes, flags = struct.unpack_from("<3I", b, 52)
     nblk, nrec, nout, npatch, payload, total = struct.unpack_from("<6Q", b, 64)
     select, nh, nr, nrh = struct.unpack_from("<4I", b, 112)
     return dict(magic=magic, version=ver, ndim=ndim, eb_mode=mode, dims=dims[:ndim], eb_user=eb_user, eb_d=eb_d,
-                eb_f=eb_f, radius=radius, huff_seg=seg, flags=flags, nblk=nblk, n_rec=nrec, n_out=nout,
+                eb_f=eb_f, radius=radius, lanes=lanes, flags=flags, nblk=nblk, n_rec=nrec, n_out=nout,
                 n_patch=npatch, payload=payload, total=total, select=select, n_codec=(nh, nr, nrh))
 
 

@@ -44,7 +44,7 @@ bool make_geom(int ndim, const uint64_t* dims, Geom& g) {
 // books, decode tables and offsets, block-major code stream.
 struct Layout {
   uint64_t st, hist_code, hist_val, hist_len, lb_c, lb_e, zero_end;
-  uint64_t lens, bcodes, feat, blk_off, rec_start, tabs, codes, total;
+  uint64_t lens, bcodes, feat, blk_off, rec_start, tabs, codes, runl, total;
 };
 
 Layout layout(const Geom& g) {
@@ -77,6 +77,8 @@ Layout layout(const Geom& g) {
   L.tabs = o;
   o += a256(3 * sizeof(DecTab));
   L.codes = o;
+  o += a256(2ull * kSlots * g.nblk);
+  L.runl = o;
   o += a256(2ull * kSlots * g.nblk);
   L.total = o;
   return L;
@@ -126,7 +128,7 @@ struct Header {
   uint64_t dims[3];
   double eb_user, eb_d;
   float eb_f;
-  uint32_t radius, huff_seg, flags;
+  uint32_t radius, lanes, flags;
   uint64_t nblk, n_rec, n_out, n_patch, payload, total;
 };
 
@@ -144,7 +146,7 @@ csz_status parse_header(const uint8_t* h, size_t bytes, Header& H, Geom& g, bool
   memcpy(&H.eb_d, h + 40, 8);
   memcpy(&H.eb_f, h + 48, 4);
   memcpy(&H.radius, h + 52, 4);
-  memcpy(&H.huff_seg, h + 56, 4);
+  memcpy(&H.lanes, h + 56, 4);
   memcpy(&H.flags, h + 60, 4);
   memcpy(&H.nblk, h + 64, 8);
   memcpy(&H.n_rec, h + 72, 8);
@@ -157,7 +159,7 @@ csz_status parse_header(const uint8_t* h, size_t bytes, Header& H, Geom& g, bool
   if (!make_geom(H.ndim, H.dims, g)) return CSZ_E_CORRUPT;
   for (int i = H.ndim; i < 3; i++)
     if (H.dims[i]) return CSZ_E_CORRUPT;
-  if (H.radius < 1 || H.radius > 512 || H.huff_seg != (uint32_t)kHuffSeg || H.flags > 3) return CSZ_E_CORRUPT;
+  if (H.radius < 1 || H.radius > 512 || H.lanes != (uint32_t)kLanes || H.flags > 3) return CSZ_E_CORRUPT;
   if (H.nblk != g.nblk || H.n_rec != H.n_out + H.n_patch) return CSZ_E_CORRUPT;
   if (!(H.eb_f > 0.0f) || !std::isfinite(2.0f * H.eb_f)) return CSZ_E_CORRUPT;
   if (H.n_rec > 2 * g.nelem || (whole && H.payload > bytes) || (H.payload & 3)) return CSZ_E_CORRUPT;
@@ -192,8 +194,8 @@ void trace_end(int id, cudaStream_t s) {
 extern "C" {
 
 static const char* const kKernelNames[K_COUNT] = {
-    "range", "abs_params", "construct", "codebook", "encode", "finalize", "dec_prep",
-    "dec_records", "dec_tables", "huff_decode", "rle_decode", "reconstruct"};
+    "range", "abs_params", "construct", "codebook", "encode", "dec_setup",
+    "stream_decode", "rle_expand", "reconstruct"};
 
 int csz_kernel_count(void) { return K_COUNT; }
 
@@ -313,9 +315,7 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   ea.off_rec = off_rec;
   ea.lb = at<uint64_t>(d_ws, L.lb_e);
   ea.spin_limit = g_spin_limit;
-  if (launch_encode(ea, s) != cudaSuccess) return CSZ_E_CUDA;
-
-  FinalizeArgs fa;
+  FinalizeArgs& fa = ea.fin;
   fa.st = st;
   fa.ar = d_ar;
   fa.cap = cap;
@@ -329,7 +329,7 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   fa.off_bb = off_bb;
   fa.off_rec = off_rec;
   fa.lens = ba.lens;
-  if (launch_finalize(fa, s) != cudaSuccess) return CSZ_E_CUDA;
+  if (launch_encode(ea, s) != cudaSuccess) return CSZ_E_CUDA;
 
   DevState hs;
   if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
@@ -392,6 +392,8 @@ csz_status csz_decompress(const uint8_t* d_ar, size_t bytes, float* d_out, uint6
   da.rec_start = at<uint32_t>(d_ws, L.rec_start);
   da.tabs = at<DecTab>(d_ws, L.tabs);
   da.codes = at<uint16_t>(d_ws, L.codes);
+  da.runv = da.codes;  // run values of an RLE+Huffman block wait in its own code slots
+  da.runl = at<uint16_t>(d_ws, L.runl);
   da.out = d_out;
   if (launch_decode(da, s) != cudaSuccess) return CSZ_E_CUDA;
   DevState hs;

@@ -28,7 +28,7 @@ constexpr int kNsymLen = 4096;
 constexpr int kHdr = 128;
 constexpr uint32_t kMagic = 0x2B5A5343u;  // "CSZ+"
 constexpr uint32_t kVersion = 1;
-constexpr int kHuffSeg = 1024;
+constexpr int kLanes = 32;  // interleave width of Huffman streams (header field)
 constexpr int kMaxLen = 64;
 constexpr int kLutBits = 12;
 constexpr uint32_t kSpinLimit = 1u << 20;
@@ -80,6 +80,7 @@ struct DevState {
   uint32_t range_done;    // CTAs finished in the range pass
   uint32_t ticket_construct;
   uint32_t ticket_encode;
+  uint32_t encode_done;
   uint32_t ncodec[3];
   unsigned long long n_rec;
   unsigned long long n_patch;
@@ -220,14 +221,14 @@ __device__ inline uint32_t block_max_u32(uint32_t v, uint32_t* scratch) {
 // |x - y| > eb, decided exactly: Knuth's TwoSum gives x - y = s + e exactly, then
 // the comparison against the float eb follows from s = RN(x - y).
 __device__ __forceinline__ bool exceeds_exact(float x, float y, float eb) {
-  float s = __fsub_rn(x, y);
-  float ny = -y;
-  float bb = __fsub_rn(s, x);
-  float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(ny, bb));
-  if (s > eb || s < -eb) return true;
-  if (s == eb) return e > 0.0f;
-  if (s == -eb) return e < 0.0f;
-  return false;
+  const float s = __fsub_rn(x, y);
+  // s = RN(x - y) and eb is a float, so |s| < eb implies |x - y| <= eb and |s| > eb
+  // implies |x - y| > eb; only |s| == eb needs the rounding error
+  if (fabsf(s) < eb) return false;
+  if (fabsf(s) > eb) return true;
+  const float bb = __fsub_rn(s, x);
+  const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(-y, bb));
+  return s > 0.0f ? e > 0.0f : e < 0.0f;
 }
 
 // k0 = round-half-away(fl32(x/2eb)); if fl32(k0*2eb) misses x by more than eb, try the
@@ -347,5 +348,203 @@ __device__ inline void canonical_build(const uint8_t* len, int nsym, CanonSmem* 
   }
   __syncthreads();
 }
+
+// ---------------------------------------------------------------------------------
+// runs of a block's dense codes c[0..m) (m <= 4096), blockDim.x == 256.
+// head[w] bit b: position 32w+b starts a run; woff[w]: runs before word w;
+// nexthead[w]: first run start at or after word w's first position (m if none).
+// ---------------------------------------------------------------------------------
+__device__ inline uint32_t block_run_heads(const uint16_t* c, uint32_t m, uint32_t* head, uint32_t* woff,
+                                           uint32_t* nexthead) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = 0; i < kSlots / 256; i++) {
+    const uint32_t j = tid + 256 * i;
+    const bool h = j < m && (j == 0 || c[j] != c[j - 1]);
+    const uint32_t hb = __ballot_sync(~0u, h);
+    if (lane == 0) head[j >> 5] = hb;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    // lane covers words 4*lane .. 4*lane+3
+    uint32_t cnt[4], first[4];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t w = 4 * lane + k, hm = head[w];
+      cnt[k] = __popc(hm);
+      first[k] = hm ? w * 32 + (__ffs(hm) - 1) : 0xffffffffu;
+      tot += cnt[k];
+    }
+    const uint32_t incl = warp_incl_scan(tot);
+    uint32_t run = incl - tot;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      woff[4 * lane + k] = run;
+      run += cnt[k];
+    }
+    // suffix minimum of first-head positions
+    uint32_t lf = min(min(first[0], first[1]), min(first[2], first[3]));
+    uint32_t suf = lf;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_down_sync(~0u, suf, o);
+      if (lane + o < 32) suf = min(suf, v);
+    }
+    uint32_t after = __shfl_down_sync(~0u, suf, 1);
+    if (lane == 31) after = 0xffffffffu;
+    uint32_t cur = after;
+#pragma unroll
+    for (int k = 3; k >= 0; k--) {
+      cur = min(cur, first[k]);
+      nexthead[4 * lane + k] = cur == 0xffffffffu ? m : cur;
+    }
+    if (lane == 31) woff[kSlots / 32] = incl;
+  }
+  __syncthreads();
+  return woff[kSlots / 32];
+}
+
+// position of the run start after position j (a run start), using the head words
+__device__ __forceinline__ uint32_t next_head(const uint32_t* head, const uint32_t* nexthead, uint32_t j,
+                                              uint32_t m) {
+  const uint32_t w = j >> 5, b = j & 31;
+  const uint32_t rest = b == 31 ? 0u : (head[w] >> (b + 1)) << (b + 1);
+  if (rest) return w * 32 + (__ffs(rest) - 1);
+  return w + 1 < (uint32_t)(kSlots / 32) ? nexthead[w + 1] : m;
+}
+
+// ---------------------------------------------------------------------------------
+// Interleaved Huffman stream (32 lanes, 16-bit units): symbol i belongs to lane i%32;
+// a lane's bit string (its codes, MSB first, zero-padded) is cut into 16-bit units
+// stored in the order a 32-lane decoder reads them: at step t the lanes holding
+// symbols 32t..32t+31 top up in rounds (each lane whose next code is longer than
+// the bits it holds takes one unit per round, lanes in increasing order), then all
+// consume their code.
+// ---------------------------------------------------------------------------------
+
+// One warp encodes sym[0..N) (+add) with a book into out[]; returns the unit count.
+__device__ inline uint32_t ihs_encode_warp(const uint16_t* sym, uint32_t N, int add,
+                                           const uint8_t* __restrict__ lens,
+                                           const uint64_t* __restrict__ codes, uint16_t* out) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t mine = N > lane ? (N - lane + 31) / 32 : 0;
+  uint64_t acc = 0;   // produced, not yet emitted bits (MSB-aligned)
+  int nacc = 0;
+  uint32_t enext = 0;  // next own symbol to produce
+  int nb = 0;          // bits the simulated decoder lane holds
+  uint32_t base = 0;
+  const uint32_t T = (N + 31) / 32;
+  for (uint32_t t = 0; t < T; t++) {
+    const bool active = t < mine;
+    const int len = active ? (int)__ldg(&lens[sym[32 * t + lane] + add]) : 0;
+    while (true) {
+      const bool need = active && len > nb;
+      const uint32_t ballot = __ballot_sync(~0u, need);
+      if (!ballot) break;
+      if (need) {
+        while (nacc < 16 && enext < mine) {
+          const int s = sym[32 * enext + lane] + add;
+          const int l = __ldg(&lens[s]);
+          acc |= (__ldg(&codes[s]) << (64 - l)) >> nacc;
+          nacc += l;
+          enext++;
+        }
+        out[base + __popc(ballot & ((1u << lane) - 1u))] = (uint16_t)(acc >> 48);
+        acc <<= 16;
+        nacc = nacc > 16 ? nacc - 16 : 0;
+        nb += 16;
+      }
+      base += __popc(ballot);
+    }
+    nb -= len;
+  }
+  return base;
+}
+
+// Block-wide encoder of the same stream (blockDim.x == 256): thread (lane l, warp w)
+// owns lane l's steps 16w..16w+15.  A lane holding cum(t) bits of codes after step t
+// has taken U(t) = ceil(cum(t)/16) units, so at step t it takes U(t) - U(t-1) units,
+// one per round; positions follow from per-step ballots (rounds, then lane order).
+// Every unit a lane takes at step t starts inside the code of its symbol t, so the
+// owner of step t gathers the unit's 16 bits from that code onwards.  Each unit is
+// written exactly once.  Returns the unit count.  scratch: >= 8*32 + 8 u32.
+__device__ inline uint32_t ihs_unit_gather(const uint16_t* sym, uint32_t N, int add,
+                                           const uint8_t* __restrict__ lens,
+                                           const uint64_t* __restrict__ codes, uint32_t lane,
+                                           uint32_t t, uint32_t skip) {
+  uint32_t unit = 0;
+  int have = 0;
+  for (uint32_t tt = t; have < 16 && 32 * tt + lane < N; tt++) {
+    const int s = sym[32 * tt + lane] + add;
+    const int L = __ldg(&lens[s]);
+    const uint64_t C = __ldg(&codes[s]);
+    const int avail = L - (int)skip;
+    const int take = min(avail, 16 - have);
+    const uint32_t bits = (uint32_t)((C >> (avail - take)) & ((1ull << take) - 1ull));
+    unit |= bits << (16 - have - take);
+    have += take;
+    skip = 0;
+  }
+  return unit;
+}
+
+__device__ inline uint32_t ihs_encode_block(const uint16_t* sym, uint32_t N, int add,
+                                            const uint8_t* __restrict__ lens,
+                                            const uint64_t* __restrict__ codes, uint16_t* out16,
+                                            uint32_t* scratch) {
+  const uint32_t tid = threadIdx.x, l = tid & 31, w = tid >> 5;
+  const uint32_t t0 = 16 * w;
+  auto len_at = [&](uint32_t t) -> uint32_t {
+    const uint32_t j = 32 * t + l;
+    return j < N ? (uint32_t)__ldg(&lens[sym[j] + add]) : 0u;
+  };
+  __syncthreads();
+  uint32_t cum = 0;
+  for (int i = 0; i < 16; i++) cum += len_at(t0 + i);
+  scratch[32 * w + l] = cum;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (uint32_t v = 0; v < w; v++) pre += scratch[32 * v + l];
+  // units per step summed over lanes, per warp
+  uint32_t c = pre, uprev = (pre + 15) >> 4, wtot = 0;
+  for (int i = 0; i < 16; i++) {
+    c += len_at(t0 + i);
+    const uint32_t u = (c + 15) >> 4;
+    wtot += warp_sum(u - uprev);
+    uprev = u;
+  }
+  if (l == 0) scratch[256 + w] = wtot;
+  __syncthreads();
+  uint32_t base = 0, total = 0;
+  for (uint32_t v = 0; v < 8; v++) {
+    if (v < w) base += scratch[256 + v];
+    total += scratch[256 + v];
+  }
+  const uint32_t lt = (1u << l) - 1u;
+  c = pre;
+  uprev = (pre + 15) >> 4;
+#pragma unroll 1
+  for (int i = 0; i < 16; i++) {
+    const uint32_t cn = c + len_at(t0 + i);
+    const uint32_t u = (cn + 15) >> 4;
+    const uint32_t D = u - uprev;
+#pragma unroll 1
+    for (uint32_t r = 1; r <= 4; r++) {
+      const uint32_t br = __ballot_sync(~0u, D >= r);
+      if (!br) break;
+      if (D >= r) {
+        const uint32_t k = uprev + r - 1;
+        out16[base + __popc(br & lt)] = (uint16_t)ihs_unit_gather(sym, N, add, lens, codes, l, t0 + i, 16 * k - c);
+      }
+      base += __popc(br);
+    }
+    c = cn;
+    uprev = u;
+  }
+  return total;
+}
+
+// Units lane `lane` of a stream needs: ceil(bits/16), given its bit total.
+__device__ __forceinline__ uint32_t ihs_lane_units(uint32_t bits) { return (bits + 15) / 16; }
 
 }  // namespace cszp

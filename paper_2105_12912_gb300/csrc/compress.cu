@@ -9,7 +9,7 @@
 //   codebook_kernel                   three canonical Huffman books
 //   encode_kernel                     per block: exact sizes or heuristic / MLP pick,
 //                                     payload placement by decoupled look-back, payload
-//   finalize_kernel                   header, padding, books
+//   (the last encode block)           header, padding, books
 #include "common.cuh"
 #include "kernels.h"
 
@@ -188,7 +188,9 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
   uint32_t* s_patch = s_hl + kNsymLen / 2;                     // 128 words
   uint32_t* s_outl = s_patch + kSlots / 32;                    // 128 words
   uint32_t* s_head = s_outl + kSlots / 32;                     // 128 words
-  uint64_t* s_scan = reinterpret_cast<uint64_t*>(s_head + kSlots / 32);  // 33
+  uint32_t* s_woff = s_head + kSlots / 32;                     // 129 (+3) words
+  uint32_t* s_next = s_woff + kSlots / 32 + 4;                 // 128 words
+  uint64_t* s_scan = reinterpret_cast<uint64_t*>(s_next + kSlots / 32);  // 33
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_prefix;
 
@@ -285,35 +287,45 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
 
   // ---- Lorenzo residual (Sec. IV-B2 predictors, chunk-local) and postquant -------
   int32_t dl[kPer];
-  const uint32_t sy = w[2], sz = w[1] * w[2];
+  const bool full = w[0] == g.blk[0] && w[1] == g.blk[1] && w[2] == g.blk[2];
+  auto residual = [&](uint32_t j, uint32_t zz, uint32_t yy, uint32_t xx, uint32_t sy, uint32_t sz) -> int32_t {
+    const bool hx = (xx % Chunk<ND>::x) != 0;
+    const bool hy = ND >= 2 && (yy % Chunk<ND>::y) != 0;
+    const bool hz = ND >= 3 && (zz % Chunk<ND>::z) != 0;
+    int32_t p;
+    if (ND == 1) {
+      p = hx ? s_k[j - 1] : 0;
+    } else if (ND == 2) {
+      p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) - ((hx && hy) ? s_k[j - sy - 1] : 0);
+    } else {
+      p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) + (hz ? s_k[j - sz] : 0) -
+          ((hx && hy) ? s_k[j - sy - 1] : 0) - ((hx && hz) ? s_k[j - sz - 1] : 0) -
+          ((hy && hz) ? s_k[j - sz - sy] : 0) + ((hx && hy && hz) ? s_k[j - sz - sy - 1] : 0);
+    }
+    return s_k[j] - p;
+  };
 #pragma unroll
   for (int i = 0; i < kPer; i++) {
     const uint32_t j = tid + kConstructThreads * i;
     int32_t delta = 0;
     uint16_t q = 0;
-    bool in = j < m;
+    const bool in = j < m;
     if (in) {
-      uint32_t zz, yy, xx;
-      dense_coords<ND>(j, w[1], w[2], zz, yy, xx);
-      const bool hx = (xx % Chunk<ND>::x) != 0;
-      const bool hy = ND >= 2 && (yy % Chunk<ND>::y) != 0;
-      const bool hz = ND >= 3 && (zz % Chunk<ND>::z) != 0;
-      int32_t p;
-      if (ND == 1) {
-        p = hx ? s_k[j - 1] : 0;
-      } else if (ND == 2) {
-        p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) - ((hx && hy) ? s_k[j - sy - 1] : 0);
+      if (full) {
+        // interior block: strides are the block extents (powers of two)
+        if (ND == 1) delta = residual(j, 0, 0, j, 0, 0);
+        else if (ND == 2) delta = residual(j, 0, j >> 6, j & 63, 64, 0);
+        else delta = residual(j, j >> 8, (j >> 4) & 15, j & 15, 16, 256);
       } else {
-        p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) + (hz ? s_k[j - sz] : 0) -
-            ((hx && hy) ? s_k[j - sy - 1] : 0) - ((hx && hz) ? s_k[j - sz - 1] : 0) -
-            ((hy && hz) ? s_k[j - sz - sy] : 0) + ((hx && hy && hz) ? s_k[j - sz - sy - 1] : 0);
+        uint32_t zz, yy, xx;
+        dense_coords<ND>(j, w[1], w[2], zz, yy, xx);
+        delta = residual(j, zz, yy, xx, w[2], w[1] * w[2]);
       }
-      delta = s_k[j] - p;
       q = (delta > -r && delta < r) ? (uint16_t)(delta + r) : (uint16_t)0;
     }
     dl[i] = delta;
     s_c[j] = q;  // zero beyond m
-    uint32_t ob = __ballot_sync(~0u, in && q == 0);
+    const uint32_t ob = __ballot_sync(~0u, in && q == 0);
     if ((tid & 31) == 0) s_outl[j >> 5] = ob;
   }
   __syncthreads();
@@ -337,6 +349,7 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
   }
 
   // ---- codes to the block-major stream (whole 4096-slot block, zero tail) --------
+  __syncthreads();
   {
     const uint4* src = reinterpret_cast<const uint4*>(s_c);
     uint4* dst = reinterpret_cast<uint4*>(a.codes + (uint64_t)b * kSlots);
@@ -344,39 +357,27 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
   }
 
   // ---- runs: heads, lengths, histograms (code hist = sum of run lengths) ---------
-#pragma unroll
-  for (int i = 0; i < kPer; i++) {
-    const uint32_t j = tid + kConstructThreads * i;
-    const bool head = j < m && (j == 0 || s_c[j] != s_c[j - 1]);
-    uint32_t hb = __ballot_sync(~0u, head);
-    if ((tid & 31) == 0) s_head[j >> 5] = hb;
-  }
-  __syncthreads();
-  if (tid < kSlots / 32) {
-    uint32_t mask = s_head[tid];
-    while (mask) {
-      const int bit = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const uint32_t j = tid * 32 + bit;
-      uint32_t nxt;
-      if (mask) {
-        nxt = tid * 32 + (__ffs(mask) - 1);
-      } else {
-        nxt = m;
-        for (int wd = tid + 1; wd < kSlots / 32; wd++) {
-          uint32_t hm = s_head[wd];
-          if (hm) {
-            nxt = wd * 32 + (__ffs(hm) - 1);
-            break;
-          }
-        }
+  block_run_heads(s_c, m, s_head, s_woff, s_next);
+  {
+    // single-element runs (the common case on rough data) are counted in a register
+    // and added once, so the shared run-length bin for length 1 is not contended
+    uint32_t ones = 0;
+#pragma unroll 4
+    for (int i = 0; i < kPer; i++) {
+      const uint32_t j = tid + kConstructThreads * i;
+      if (j < m && ((s_head[j >> 5] >> (j & 31)) & 1u)) {
+        const uint32_t v = s_c[j];
+        const uint32_t len = next_head(s_head, s_next, j, m) - j;
+        add16(s_hc, v, len);
+        add16(s_hv, v, 1u);
+        if (len == 1)
+          ones++;
+        else
+          add16(s_hl, len - 1, 1u);
       }
-      const uint32_t len = nxt - j;
-      const uint32_t v = s_c[j];
-      add16(s_hc, v, len);
-      add16(s_hv, v, 1u);
-      add16(s_hl, len - 1, 1u);
     }
+    ones = warp_sum(ones);
+    if ((tid & 31) == 0 && ones) add16(s_hl, 0, ones);
   }
 
   // ---- place records: exclusive prefix over tiles, then ordered writes -----------
@@ -416,7 +417,7 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
 }
 
 static size_t construct_smem_bytes() {
-  return kSlots * 4 + kSlots * 2 + (kNsymCode + kNsymCode + kNsymLen) / 2 * 4 + 3 * (kSlots / 32) * 4 +
+  return kSlots * 4 + kSlots * 2 + (kNsymCode + kNsymCode + kNsymLen) / 2 * 4 + 5 * (kSlots / 32) * 4 + 16 +
          33 * 8 + 16;
 }
 
@@ -426,25 +427,43 @@ static size_t construct_smem_bytes() {
 
 constexpr int kBookThreads = 1024;
 
-__device__ void bitonic_sort_u64(uint64_t* k, int P) {
-  for (int size = 2; size <= P; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
-        int i = 2 * t - (t & (stride - 1));
-        int j = i + stride;
-        bool up = (i & size) == 0;
-        uint64_t a = k[i], c = k[j];
-        if ((a > c) == up) {
-          k[i] = c;
-          k[j] = a;
-        }
+// Ascending sort of L distinct keys by merging runs: an element's place in the merged
+// run is its index in its own run plus the number of smaller keys in the partner run
+// (binary search).  a holds the keys on entry and on exit; b is scratch of L keys.
+__device__ void rank_merge_sort_u64(uint64_t* a, uint64_t* b, int L) {
+  uint64_t* src = a;
+  uint64_t* dst = b;
+  for (int run = 1; run < L; run <<= 1) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+      const uint64_t k = src[i];
+      const int r = i / run;
+      const int r0 = r * run;
+      const bool left = (r & 1) == 0;
+      const int p0 = left ? r0 + run : r0 - run;
+      const int pn = left ? max(0, min(run, L - p0)) : run;
+      int lo = 0, hi = pn;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (src[p0 + mid] < k) lo = mid + 1;
+        else hi = mid;
       }
-      __syncthreads();
+      dst[(left ? r0 : p0) + (i - r0) + lo] = k;
     }
+    __syncthreads();
+    uint64_t* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != a) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) a[i] = src[i];
+    __syncthreads();
   }
 }
 
 // One CTA per book: 0 quant codes [1024], 1 run values [1024], 2 run lengths [4096].
+// Shared memory (bytes): len 4K | sym 8K | weight by node 32K | parent by node 16K |
+// region A 32K (sort keys, live node list, canonical scratch) | region B 32K (sort
+// scratch, new nodes, depth pass).
 __global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int book = blockIdx.x;
@@ -453,13 +472,14 @@ __global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) {
   uint8_t* len_out = a.lens + (book == 0 ? 0 : (book == 1 ? kNsymCode : 2 * kNsymCode));
   uint64_t* code_out = a.codes + (book == 0 ? 0 : (book == 1 ? kNsymCode : 2 * kNsymCode));
 
-  uint8_t* s_len = smem;                                                // 4096
-  uint64_t* s_key = reinterpret_cast<uint64_t*>(smem + kNsymLen);       // 4096 u64
-  uint32_t* s_w = reinterpret_cast<uint32_t*>(s_key);                   // 8192 u32 (aliases)
-  uint16_t* s_sym = reinterpret_cast<uint16_t*>(s_key + kNsymLen);      // 4096
-  uint16_t* s_anc = s_sym + kNsymLen;                                   // 8192
-  uint16_t* s_dep = s_anc + 2 * kNsymLen;                               // 8192
+  uint8_t* s_len = smem;                                                       // 4096
+  uint16_t* s_sym = reinterpret_cast<uint16_t*>(smem + 4096);                  // 4096
+  uint32_t* s_wt = reinterpret_cast<uint32_t*>(smem + 12288);                  // 8192
+  uint16_t* s_par = reinterpret_cast<uint16_t*>(smem + 45056);                 // 8192
+  uint64_t* A = reinterpret_cast<uint64_t*>(smem + 61440);                     // 4096
+  uint64_t* B = reinterpret_cast<uint64_t*>(smem + 94208);                     // 4096
   __shared__ uint32_t s_L;
+  __shared__ int s_n, s_k, s_next;
   __shared__ CanonSmem cs;
   const int tid = threadIdx.x;
 
@@ -467,74 +487,146 @@ __global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) {
   for (int s = tid; s < nsym; s += blockDim.x) s_len[s] = 0;
   __syncthreads();
   for (int s = tid; s < nsym; s += blockDim.x) {
-    uint32_t f = hist[s];
-    if (f) {
-      uint32_t p = atomicAdd(&s_L, 1u);
-      s_key[p] = ((uint64_t)f << 12) | (uint64_t)s;
-    }
+    const uint32_t f = hist[s];
+    if (f) A[atomicAdd(&s_L, 1u)] = ((uint64_t)f << 12) | (uint64_t)s;
   }
   __syncthreads();
   const int L = (int)s_L;
   if (L == 1) {
-    if (tid == 0) s_len[s_key[0] & 0xfff] = 1;
+    if (tid == 0) s_len[A[0] & 0xfff] = 1;
   } else if (L > 1) {
-    int P = 1;
-    while (P < L) P <<= 1;
-    for (int i = L + tid; i < P; i += blockDim.x) s_key[i] = ~0ull;
-    __syncthreads();
-    bitonic_sort_u64(s_key, P);
-    // leaves: weights and symbols in (frequency, symbol) order
-    uint64_t kk[4];
-    int cntk = 0;
-    for (int i = tid; i < L; i += blockDim.x) kk[cntk++] = s_key[i];
-    __syncthreads();
-    cntk = 0;
+    // leaves in (frequency, symbol) order
+    rank_merge_sort_u64(A, B, L);
     for (int i = tid; i < L; i += blockDim.x) {
-      s_w[i] = (uint32_t)(kk[cntk] >> 12);
-      s_sym[i] = (uint16_t)(kk[cntk] & 0xfff);
-      cntk++;
+      s_wt[i] = (uint32_t)(A[i] >> 12);
+      s_sym[i] = (uint16_t)(A[i] & 0xfff);
     }
     __syncthreads();
     const int nn = 2 * L - 1;
+    // ---- pairing rounds ----------------------------------------------------------
+    // Keys order the live nodes as the sequential two-queue method picks them:
+    // (weight, leaves before internal nodes, creation order).  With t the sum of the
+    // two lightest, every consecutive pair whose second member weighs <= t precedes
+    // the new node of weight t in that order, so all such pairs merge in one round;
+    // the new nodes are rank-merged back.  When a round would merge few pairs the
+    // rest is finished by the sequential loop, from the same state.
+    constexpr uint64_t kClass = 1ull << 13, kIdx = kClass - 1;
+    for (int i = tid; i < L; i += blockDim.x) A[i] = ((uint64_t)s_wt[i] << 14) | (uint64_t)i;
     if (tid == 0) {
-      // two queues: leaves [qi, L), internal nodes [qj, nxt); a weight tie takes the leaf
-      int qi = 0, qj = L, nxt = L;
-      uint32_t wi = s_w[0], wj = 0;
+      s_n = L;
+      s_next = L;
+    }
+    __syncthreads();
+    while (true) {
+      const int n = s_n;
+      if (n <= 1) break;
+      if (tid == 0) {
+        const uint64_t t = (A[0] >> 14) + (A[1] >> 14);
+        int lo = 0, hi = n / 2;  // pairs i with weight(A[2i+1]) <= t
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if ((A[2 * mid + 1] >> 14) <= t) lo = mid + 1;
+          else hi = mid;
+        }
+        s_k = lo;
+      }
+      __syncthreads();
+      const int k = s_k;
+      if (k < 16) break;
+      const int next = s_next;
+      for (int i = tid; i < k; i += blockDim.x) {
+        const uint64_t x = A[2 * i], y = A[2 * i + 1];
+        const uint64_t wn = (x >> 14) + (y >> 14);
+        const uint32_t id = (uint32_t)next + i;
+        s_par[x & kIdx] = (uint16_t)id;
+        s_par[y & kIdx] = (uint16_t)id;
+        s_wt[id] = (uint32_t)wn;
+        B[i] = (wn << 14) | kClass | id;
+      }
+      __syncthreads();
+      const int nr = n - 2 * k;
+      uint64_t mine[4];
+      int dst[4], cnt = 0;
+      for (int i = tid; i < n - k; i += blockDim.x) {
+        const bool from_rest = i < nr;
+        const uint64_t x = from_rest ? A[2 * k + i] : B[i - nr];
+        const uint64_t* other = from_rest ? B : A + 2 * k;
+        int lo = 0, hi = from_rest ? k : nr;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (other[mid] < x) lo = mid + 1;
+          else hi = mid;
+        }
+        mine[cnt] = x;
+        dst[cnt] = (from_rest ? i : i - nr) + lo;
+        cnt++;
+      }
+      __syncthreads();
+      for (int c = 0; c < cnt; c++) A[dst[c]] = mine[c];
+      if (tid == 0) {
+        s_n = n - k;
+        s_next = next + k;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      // sequential finish; consumed leaves and internal nodes are prefixes of their
+      // queues, so the live list gives the queue fronts
+      const int n = s_n;
+      int live_leaves = 0;
+      for (int i = 0; i < n; i++) live_leaves += (A[i] & kClass) ? 0 : 1;
+      int qi = L - live_leaves, nxt = s_next, qj = nxt - (n - live_leaves);
+      constexpr uint32_t INF = 0xffffffffu;
+      uint32_t l0 = qi < L ? s_wt[qi] : INF, l1 = qi + 1 < L ? s_wt[qi + 1] : INF,
+               l2 = qi + 2 < L ? s_wt[qi + 2] : INF;
+      uint32_t i0 = qj < nxt ? s_wt[qj] : INF, i1 = qj + 1 < nxt ? s_wt[qj + 1] : INF;
       while (nxt < nn) {
         int pk[2];
         uint32_t pw[2];
 #pragma unroll
         for (int t = 0; t < 2; t++) {
-          if (qi < L && (qj >= nxt || wi <= wj)) {
+          if (l0 <= i0) {
             pk[t] = qi;
-            pw[t] = wi;
+            pw[t] = l0;
             qi++;
-            wi = qi < L ? s_w[qi] : 0u;
+            l0 = l1;
+            l1 = l2;
+            l2 = qi + 2 < L ? s_wt[qi + 2] : INF;
           } else {
             pk[t] = qj;
-            pw[t] = wj;
+            pw[t] = i0;
             qj++;
-            wj = qj < nxt ? s_w[qj] : 0u;
+            i0 = i1;
+            i1 = qj + 1 < nxt ? s_wt[qj + 1] : INF;
           }
         }
         const uint32_t sum = pw[0] + pw[1];
-        s_w[nxt] = sum;
-        if (qj == nxt) wj = sum;  // the internal queue was empty: new node is its front
-        s_anc[pk[0]] = (uint16_t)nxt;
-        s_anc[pk[1]] = (uint16_t)nxt;
+        s_wt[nxt] = sum;
+        s_par[pk[0]] = (uint16_t)nxt;
+        s_par[pk[1]] = (uint16_t)nxt;
+        if (qj == nxt) {
+          i0 = sum;
+        } else if (qj + 1 == nxt) {
+          i1 = sum;
+        }
         nxt++;
       }
-      s_anc[nn - 1] = (uint16_t)(nn - 1);
+      s_par[nn - 1] = (uint16_t)(nn - 1);
     }
     __syncthreads();
-    // depths by pointer jumping
-    for (int i = tid; i < nn; i += blockDim.x) s_dep[i] = (i == nn - 1) ? 0 : 1;
+    // depths by pointer jumping (region B)
+    uint16_t* s_anc = reinterpret_cast<uint16_t*>(B);
+    uint16_t* s_dep = s_anc + 2 * kNsymLen;
+    for (int i = tid; i < nn; i += blockDim.x) {
+      s_anc[i] = s_par[i];
+      s_dep[i] = (i == nn - 1) ? 0 : 1;
+    }
     __syncthreads();
     for (int step = 1; step < nn; step <<= 1) {
       uint16_t na[8], nd[8];
       int c = 0;
       for (int i = tid; i < nn; i += blockDim.x) {
-        uint16_t an = s_anc[i];
+        const uint16_t an = s_anc[i];
         nd[c] = s_dep[i] + s_dep[an];
         na[c] = s_anc[an];
         c++;
@@ -549,60 +641,90 @@ __global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) {
       __syncthreads();
     }
     for (int i = tid; i < L; i += blockDim.x) {
-      uint16_t d = s_dep[i];
+      const uint16_t d = s_dep[i];
       if (d > kMaxLen) atomicOr(&a.st->status, ERR_RANGE);
       s_len[s_sym[i]] = (uint8_t)d;
     }
   }
   __syncthreads();
   for (int s = tid; s < nsym; s += blockDim.x) len_out[s] = s_len[s];
-  uint16_t* wcnt = reinterpret_cast<uint16_t*>(s_key);  // tree storage is free now
-  canonical_build(s_len, nsym, &cs, wcnt, code_out, nullptr);
+  canonical_build(s_len, nsym, &cs, reinterpret_cast<uint16_t*>(A), code_out, nullptr);
 }
 
-static size_t codebook_smem_bytes() { return kNsymLen + kNsymLen * 8 + kNsymLen * 2 + 2 * kNsymLen * 2 * 2; }
+static size_t codebook_smem_bytes() { return 94208 + kNsymLen * 8; }
 
 // =================================================================================
 // per-block selection and encoding
 // =================================================================================
 
-constexpr int kEncThreads = 256;
-constexpr int kBufWords = 4096;  // 16 KB payload assembly buffer
-
-// MSB-first bits of `code` (len bits) at bit offset off of a u32 word buffer
-__device__ __forceinline__ void put_bits(uint32_t* buf, uint32_t off, uint64_t code, int len) {
-  uint32_t wd = off >> 5;
-  int sh = off & 31;
-  int rem = len;
-  while (rem > 0) {
-    int take = min(rem, 32 - sh);
-    uint32_t chunk = (uint32_t)((code >> (rem - take)) & ((1ull << take) - 1ull));
-    atomicOr(&buf[wd], chunk << (32 - sh - take));
-    rem -= take;
-    wd++;
-    sh = 0;
-  }
-}
-
-// Encode syms[0..cnt) (+sym_add) with a book into buf (zeroed) from bit 0; each thread
-// takes a contiguous share; returns total bits.
-__device__ uint32_t encode_seq(const uint16_t* syms, int cnt, int sym_add, const uint8_t* __restrict__ lens,
-                               const uint64_t* __restrict__ codes, uint32_t* buf, uint32_t* scan) {
-  const int per = (cnt + blockDim.x - 1) / blockDim.x;
-  const int lo = min(cnt, (int)threadIdx.x * per), hi = min(cnt, lo + per);
-  uint32_t bits = 0;
-  for (int i = lo; i < hi; i++) bits += __ldg(&lens[syms[i] + sym_add]);
-  uint32_t total;
-  uint32_t off = block_excl_scan<uint32_t>(bits, scan, &total);
-  for (int i = lo; i < hi; i++) {
-    const int s = syms[i] + sym_add;
-    const int l = __ldg(&lens[s]);
-    put_bits(buf, off, __ldg(&codes[s]), l);
-    off += l;
+// =================================================================================
+// header, section padding and books
+// =================================================================================
+__device__ void finalize_body(const FinalizeArgs& a) {
+  __shared__ uint32_t s_hdr[kHdr / 4];
+  __shared__ uint64_t s_total, s_off_books;
+  __shared__ uint32_t s_flags;
+  DevState* st = a.st;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const uint64_t n_rec = st->n_rec, payload = st->payload;
+    const uint32_t flags = (st->ncodec[CODEC_HUFF] ? 1u : 0u) | (st->ncodec[CODEC_RLE_HUFF] ? 2u : 0u);
+    const uint64_t off_pay = a.off_rec + 8 * n_rec;
+    const uint64_t off_books = off_pay + ((payload + 7) & ~7ull);
+    const uint64_t total = off_books + ((flags & 1) ? kNsymCode : 0) + ((flags & 2) ? kNsymCode + kNsymLen : 0);
+    s_total = total;
+    s_off_books = off_books;
+    s_flags = flags;
+    st->total = total;
+    if (total > a.cap) atomicOr(&st->status, ERR_CAPACITY);
+    for (int i = 0; i < kHdr / 4; i++) s_hdr[i] = 0;
+    unsigned char* h = reinterpret_cast<unsigned char*>(s_hdr);
+    auto put32 = [&](int off, uint32_t v) { memcpy(h + off, &v, 4); };
+    auto put64 = [&](int off, uint64_t v) { memcpy(h + off, &v, 8); };
+    put32(0, kMagic);
+    h[4] = (unsigned char)(kVersion & 0xff);
+    h[5] = (unsigned char)(kVersion >> 8);
+    h[6] = (unsigned char)a.ndim;
+    h[7] = (unsigned char)a.eb_mode;
+    for (int i = 0; i < 3; i++) put64(8 + 8 * i, i < a.ndim ? a.dims[i] : 0ull);
+    double eu = a.eb_user, ed = st->eb_d;
+    memcpy(h + 32, &eu, 8);
+    memcpy(h + 40, &ed, 8);
+    float ef = st->eb_f;
+    memcpy(h + 48, &ef, 4);
+    put32(52, a.radius);
+    put32(56, (uint32_t)kLanes);
+    put32(60, flags);
+    put64(64, a.nblk);
+    put64(72, n_rec);
+    put64(80, n_rec - st->n_patch);
+    put64(88, st->n_patch);
+    put64(96, payload);
+    put64(104, total);
+    put32(112, (uint32_t)a.select);
+    for (int i = 0; i < 3; i++) put32(116 + 4 * i, st->ncodec[i]);
   }
   __syncthreads();
-  return total;
+  if (s_total > a.cap) return;
+  uint8_t* ar = a.ar;
+  for (int i = tid; i < kHdr / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(ar)[i] = s_hdr[i];
+  // zero padding: codec section, blk_bytes section, payload tail
+  for (uint64_t i = kHdr + a.nblk + tid; i < a.off_bb; i += blockDim.x) ar[i] = 0;
+  for (uint64_t i = a.off_bb + 4ull * a.nblk + tid; i < a.off_rec; i += blockDim.x) ar[i] = 0;
+  const uint64_t pay_end = a.off_rec + 8 * st->n_rec + st->payload;
+  for (uint64_t i = pay_end + tid; i < s_off_books; i += blockDim.x) ar[i] = 0;
+  uint64_t o = s_off_books;
+  if (s_flags & 1) {
+    for (int i = tid; i < kNsymCode; i += blockDim.x) ar[o + i] = a.lens[i];
+    o += kNsymCode;
+  }
+  if (s_flags & 2) {
+    for (int i = tid; i < kNsymCode + kNsymLen; i += blockDim.x) ar[o + i] = a.lens[kNsymCode + i];
+  }
 }
+
+constexpr int kEncThreads = 256;
+constexpr int kBufBytes = 16384;  // payload assembly buffer
 
 __device__ int mlp_pick_warp(const float* __restrict__ w, const float* f) {
   const int lane = threadIdx.x & 31;
@@ -635,21 +757,33 @@ __device__ int mlp_pick_warp(const float* __restrict__ w, const float* f) {
   return c;
 }
 
+// interleaved-stream units from per-thread bit partials: thread t's symbols all belong
+// to lane t % 32 (strided mapping over 256 threads); called by warp 0
+__device__ __forceinline__ uint32_t units_from_partials(const uint32_t* part) {
+  const int lane = threadIdx.x & 31;
+  uint32_t bits = 0;
+#pragma unroll
+  for (int wv = 0; wv < kEncThreads / 32; wv++) bits += part[32 * wv + lane];
+  return warp_sum(ihs_lane_units(bits));
+}
+
 __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t* s_c = reinterpret_cast<uint16_t*>(smem);        // 4096 codes
-  uint16_t* s_rv = s_c + kSlots;                            // run values
-  uint16_t* s_rl = s_rv + kSlots;                           // run lengths
-  uint32_t* s_buf = reinterpret_cast<uint32_t*>(s_rl + kSlots);  // 4096 words
-  uint32_t* s_head = s_buf + kBufWords;                     // 128
-  uint32_t* s_woff = s_head + kSlots / 32;                  // 128
-  uint32_t* s_scan = s_woff + kSlots / 32;                  // 33
-  uint64_t* s_scan64 = reinterpret_cast<uint64_t*>(s_scan + 34);  // 33
-  __shared__ uint32_t s_tile, s_codec;
+  uint16_t* s_c = reinterpret_cast<uint16_t*>(smem);             // 4096 codes
+  uint16_t* s_rv = s_c + kSlots;                                 // run values
+  uint16_t* s_rl = s_rv + kSlots;                                // run lengths
+  uint32_t* s_buf = reinterpret_cast<uint32_t*>(s_rl + kSlots);  // 16 KB
+  uint32_t* s_head = s_buf + kBufBytes / 4;                      // 128
+  uint32_t* s_woff = s_head + kSlots / 32;                       // 129 (+3)
+  uint32_t* s_next = s_woff + kSlots / 32 + 4;                   // 128
+  uint32_t* s_part = s_next + kSlots / 32;                       // 2 x 256
+  uint32_t* s_scan = s_part + 2 * kEncThreads;                   // 34
+  uint64_t* s_scan64 = reinterpret_cast<uint64_t*>(s_scan + 34); // 33
+  __shared__ uint32_t s_tile, s_codec, s_units[3];
   __shared__ uint64_t s_prefix;
   __shared__ float s_feat[8];
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, wid = tid >> 5;
   if (tid == 0) s_tile = atomicAdd(&a.st->ticket_encode, 1u);
   __syncthreads();
   const uint32_t b = s_tile;
@@ -672,83 +806,72 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   }
   __syncthreads();
 
-  // runs (needed by every mode except forced HUFF)
-  const bool need_runs = sel != SEL_HUFF;
+  // runs (every mode except forced Huffman)
   uint32_t nr = 0;
-  if (need_runs) {
+  if (sel != SEL_HUFF) {
+    nr = block_run_heads(s_c, m, s_head, s_woff, s_next);
+#pragma unroll 4
     for (int i = 0; i < kSlots / kEncThreads; i++) {
       const uint32_t j = tid + kEncThreads * i;
-      const bool head = j < m && (j == 0 || s_c[j] != s_c[j - 1]);
-      const uint32_t hb = __ballot_sync(~0u, head);
-      if ((tid & 31) == 0) s_head[j >> 5] = hb;
-    }
-    __syncthreads();
-    uint32_t tot;
-    const uint32_t wo = block_excl_scan<uint32_t>(tid < kSlots / 32 ? __popc(s_head[tid]) : 0u, s_scan, &tot);
-    nr = tot;
-    if (tid < kSlots / 32) {
-      uint32_t mask = s_head[tid];
-      uint32_t ri = wo;
-      while (mask) {
-        const int bit = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const uint32_t j = tid * 32 + bit;
-        uint32_t nxt;
-        if (mask) {
-          nxt = tid * 32 + (__ffs(mask) - 1);
-        } else {
-          nxt = m;
-          for (int wd = tid + 1; wd < kSlots / 32; wd++) {
-            uint32_t hm = s_head[wd];
-            if (hm) {
-              nxt = wd * 32 + (__ffs(hm) - 1);
-              break;
-            }
-          }
+      if (j < m) {
+        const uint32_t hb = s_head[j >> 5], bit = j & 31;
+        if ((hb >> bit) & 1u) {
+          const uint32_t ri = s_woff[j >> 5] + __popc(hb & ((1u << bit) - 1u));
+          s_rv[ri] = s_c[j];
+          s_rl[ri] = (uint16_t)(next_head(s_head, s_next, j, m) - j);
         }
-        s_rv[ri] = s_c[j];
-        s_rl[ri] = (uint16_t)(nxt - j);
-        ri++;
       }
     }
     __syncthreads();
   }
 
-  // sizes
-  const uint32_t S = (m + kHuffSeg - 1) / kHuffSeg;
-  const uint32_t hdr_bytes = (2 * S + 3) & ~3u;
-  uint64_t size_h = ~0ull, size_r = ~0ull, size_rh = ~0ull;
-  if (sel == SEL_HUFF || sel == SEL_EXHAUSTIVE) {
-    uint32_t sb[4] = {0, 0, 0, 0};
-#pragma unroll
+  // exact sizes: Huffman units from per-lane bit totals
+  auto huff_units = [&]() {
+    uint32_t bits = 0;
+#pragma unroll 4
     for (int i = 0; i < kSlots / kEncThreads; i++) {
       const uint32_t j = tid + kEncThreads * i;
-      if (j < m) sb[i >> 2] += __ldg(&clen[s_c[j]]);
+      if (j < m) bits += __ldg(&clen[s_c[j]]);
     }
-    uint64_t sz = hdr_bytes;
-    for (int s = 0; s < 4; s++) {
-      uint32_t t = block_sum<uint32_t>(sb[s], s_scan);
-      sz += 4ull * ((t + 31) / 32);
+    s_part[tid] = bits;
+    __syncthreads();
+    if (tid < 32) {
+      const uint32_t u = units_from_partials(s_part);
+      if (tid == 0) s_units[0] = u;
     }
-    size_h = sz;
-  }
-  if (sel == SEL_RLE || sel == SEL_EXHAUSTIVE) size_r = 4ull * nr;
-  uint32_t vbits = 0, lbits = 0;
-  if (sel == SEL_RLE_HUFF || sel == SEL_EXHAUSTIVE) {
+    __syncthreads();
+    return s_units[0];
+  };
+  auto rlehuff_units = [&]() {
     uint32_t vb = 0, lb = 0;
     for (uint32_t i = tid; i < nr; i += kEncThreads) {
       vb += __ldg(&vlen[s_rv[i]]);
       lb += __ldg(&llen[s_rl[i] - 1]);
     }
-    vbits = block_sum<uint32_t>(vb, s_scan);
-    lbits = block_sum<uint32_t>(lb, s_scan);
-    size_rh = 8ull + 4ull * ((vbits + 31) / 32) + 4ull * ((lbits + 31) / 32);
+    s_part[tid] = vb;
+    s_part[kEncThreads + tid] = lb;
+    __syncthreads();
+    if (tid < 32) {
+      const uint32_t vu = units_from_partials(s_part);
+      const uint32_t lu = units_from_partials(s_part + kEncThreads);
+      if (tid == 0) {
+        s_units[1] = vu;
+        s_units[2] = lu;
+      }
+    }
+    __syncthreads();
+  };
+  uint64_t size_h = ~0ull, size_r = ~0ull, size_rh = ~0ull;
+  if (sel == SEL_HUFF || sel == SEL_EXHAUSTIVE) size_h = (2ull * huff_units() + 3) & ~3ull;
+  if (sel == SEL_RLE || sel == SEL_EXHAUSTIVE) size_r = 4ull * nr;
+  if (sel == SEL_RLE_HUFF || sel == SEL_EXHAUSTIVE) {
+    rlehuff_units();
+    size_rh = (8ull + 2ull * (s_units[1] + s_units[2]) + 3) & ~3ull;
   }
 
   // selection
   if (sel == SEL_HEURISTIC || sel == SEL_LEARNED) {
-    // block histogram from the runs, then the statistics of the features
-    uint32_t* s_hist = s_buf;  // 1024 words
+    uint32_t* s_hist = s_buf;  // 1024 words, before the payload is assembled
     for (int i = tid; i < kNsymCode; i += kEncThreads) s_hist[i] = 0;
     __syncthreads();
     for (uint32_t i = tid; i < nr; i += kEncThreads) atomicAdd(&s_hist[s_rv[i]], (uint32_t)s_rl[i]);
@@ -787,7 +910,8 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
       if (tid == 0) {
         const uint32_t zero = s_hist[r];
         const uint32_t outl = s_hist[0];
-        uint32_t near1 = s_hist[r] + (r + 1 < 2 * r ? s_hist[r + 1] : 0u) + (r - 1 > 0 ? s_hist[r - 1] : 0u);
+        const uint32_t near1 =
+            s_hist[r] + (r + 1 < 2 * r ? s_hist[r + 1] : 0u) + (r - 1 > 0 ? s_hist[r - 1] : 0u);
         const float fm = (float)m;
         s_feat[0] = (float)zero / fm;
         s_feat[1] = (float)NH / (float)((uint64_t)m * 65536ull);
@@ -822,30 +946,10 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   }
   __syncthreads();
   const int codec = (int)s_codec;
-  // exact size of the chosen codec (computed here if the mode skipped it)
-  if (codec == CODEC_HUFF && size_h == ~0ull) {
-    uint32_t sb[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < kSlots / kEncThreads; i++) {
-      const uint32_t j = tid + kEncThreads * i;
-      if (j < m) sb[i >> 2] += __ldg(&clen[s_c[j]]);
-    }
-    uint64_t sz = hdr_bytes;
-    for (int s = 0; s < 4; s++) {
-      uint32_t t = block_sum<uint32_t>(sb[s], s_scan);
-      sz += 4ull * ((t + 31) / 32);
-    }
-    size_h = sz;
-  }
+  if (codec == CODEC_HUFF && size_h == ~0ull) size_h = (2ull * huff_units() + 3) & ~3ull;
   if (codec == CODEC_RLE_HUFF && size_rh == ~0ull) {
-    uint32_t vb = 0, lb = 0;
-    for (uint32_t i = tid; i < nr; i += kEncThreads) {
-      vb += __ldg(&vlen[s_rv[i]]);
-      lb += __ldg(&llen[s_rl[i] - 1]);
-    }
-    vbits = block_sum<uint32_t>(vb, s_scan);
-    lbits = block_sum<uint32_t>(lb, s_scan);
-    size_rh = 8ull + 4ull * ((vbits + 31) / 32) + 4ull * ((lbits + 31) / 32);
+    rlehuff_units();
+    size_rh = (8ull + 2ull * (s_units[1] + s_units[2]) + 3) & ~3ull;
   }
   const uint64_t size = codec == CODEC_HUFF ? size_h : (codec == CODEC_RLE ? 4ull * nr : size_rh);
   if (tid == 0) {
@@ -853,34 +957,28 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
     atomicAdd(&a.st->ncodec[codec], 1u);
     atomicAdd(&a.st->payload, (unsigned long long)size);
   }
-  __syncthreads();
 
-  // payload assembly in shared memory (every chosen size fits 16 KB unless a forced
-  // Huffman mode meets codes longer than 32 bits on average; those blocks go direct)
-  const bool in_smem = size <= (uint64_t)kBufWords * 4;
-  if (in_smem && codec != CODEC_RLE) {
-    for (int i = tid; i < kBufWords; i += kEncThreads) s_buf[i] = 0;
-    __syncthreads();
+  // payload assembly in shared memory while predecessors publish (every chosen size
+  // fits 16 KB unless a forced Huffman mode meets very long codes; those go direct)
+  auto assemble = [&](uint16_t* out16) {
     if (codec == CODEC_HUFF) {
-      uint32_t wo = hdr_bytes / 4;
-      for (uint32_t s = 0; s < S; s++) {
-        const int cnt = (int)min((uint32_t)kHuffSeg, m - s * kHuffSeg);
-        const uint32_t bits = encode_seq(s_c + s * kHuffSeg, cnt, 0, clen, ccode, s_buf + wo, s_scan);
-        const uint32_t nw = (bits + 31) / 32;
-        if (tid == 0) reinterpret_cast<uint16_t*>(s_buf)[s] = (uint16_t)nw;
-        wo += nw;
-      }
-    } else {
-      const uint32_t vw = (vbits + 31) / 32;
+      const uint32_t u = ihs_encode_block(s_c, m, 0, clen, ccode, out16, s_part);
+      if ((u & 1u) && tid == 0) out16[u] = 0;
+    } else if (codec == CODEC_RLE_HUFF) {
+      const uint32_t vu = s_units[1], lu = s_units[2];
       if (tid == 0) {
-        s_buf[0] = nr;
-        s_buf[1] = vw;
+        uint32_t* out32 = reinterpret_cast<uint32_t*>(out16);
+        out32[0] = nr;
+        out32[1] = vu;
+        if ((vu + lu) & 1u) out16[4 + vu + lu] = 0;
       }
-      encode_seq(s_rv, (int)nr, 0, vlen, vcode, s_buf + 2, s_scan);
-      encode_seq(s_rl, (int)nr, -1, llen, lcode, s_buf + 2 + vw, s_scan);
+      ihs_encode_block(s_rv, nr, 0, vlen, vcode, out16 + 4, s_part);
+      ihs_encode_block(s_rl, nr, -1, llen, lcode, out16 + 4 + vu, s_part);
     }
-    __syncthreads();
-  }
+  };
+  const bool in_smem = size <= (uint64_t)kBufBytes;
+  if (in_smem) assemble(reinterpret_cast<uint16_t*>(s_buf));
+  __syncthreads();
 
   // placement
   if (tid < 32) {
@@ -892,7 +990,7 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   const uint64_t dst_off = off_pay + s_prefix;
   if (tid == 0) {
     a.ar[a.off_codec + b] = (uint8_t)codec;
-    if (a.off_bb + 4ull * b + 4 <= a.cap) reinterpret_cast<uint32_t*>(a.ar + a.off_bb)[b] = (uint32_t)size;
+    reinterpret_cast<uint32_t*>(a.ar + a.off_bb)[b] = (uint32_t)size;
   }
   if (dst_off + size > a.cap) {
     if (tid == 0) atomicOr(&a.st->status, ERR_CAPACITY);
@@ -909,96 +1007,24 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   } else if (in_smem) {
     for (uint32_t i = tid; i < nwords; i += kEncThreads) dst[i] = s_buf[i];
   } else {
-    // direct path: zero the block's own region, then OR the bits in place
-    for (uint32_t i = tid; i < nwords; i += kEncThreads) dst[i] = 0u;
-    __syncthreads();
-    if (codec == CODEC_HUFF) {
-      uint32_t wo = hdr_bytes / 4;
-      for (uint32_t s = 0; s < S; s++) {
-        const int cnt = (int)min((uint32_t)kHuffSeg, m - s * kHuffSeg);
-        const uint32_t bits = encode_seq(s_c + s * kHuffSeg, cnt, 0, clen, ccode, dst + wo, s_scan);
-        const uint32_t nw = (bits + 31) / 32;
-        if (tid == 0) atomicOr(&dst[s >> 1], nw << ((s & 1) * 16));
-        wo += nw;
-      }
-    } else {
-      const uint32_t vw = (vbits + 31) / 32;
-      if (tid == 0) {
-        dst[0] = nr;
-        dst[1] = vw;
-      }
-      encode_seq(s_rv, (int)nr, 0, vlen, vcode, dst + 2, s_scan);
-      encode_seq(s_rl, (int)nr, -1, llen, lcode, dst + 2 + vw, s_scan);
-    }
+    assemble(reinterpret_cast<uint16_t*>(dst));
+  }
+  // the last block to finish writes the header, section padding and books
+  __shared__ bool s_last;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(&a.st->encode_done, 1u) == a.g.nblk - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    finalize_body(a.fin);
   }
 }
 
-static size_t encode_smem_bytes() { return kSlots * 2 * 3 + kBufWords * 4 + 2 * (kSlots / 32) * 4 + 34 * 4 + 33 * 8 + 16; }
-
-// =================================================================================
-// header, section padding and books
-// =================================================================================
-__global__ void finalize_kernel(FinalizeArgs a) {
-  __shared__ uint32_t s_hdr[kHdr / 4];
-  __shared__ uint64_t s_total, s_off_books;
-  __shared__ uint32_t s_flags;
-  DevState* st = a.st;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    const uint64_t n_rec = st->n_rec, payload = st->payload;
-    const uint32_t flags = (st->ncodec[CODEC_HUFF] ? 1u : 0u) | (st->ncodec[CODEC_RLE_HUFF] ? 2u : 0u);
-    const uint64_t off_pay = a.off_rec + 8 * n_rec;
-    const uint64_t off_books = off_pay + ((payload + 7) & ~7ull);
-    const uint64_t total = off_books + ((flags & 1) ? kNsymCode : 0) + ((flags & 2) ? kNsymCode + kNsymLen : 0);
-    s_total = total;
-    s_off_books = off_books;
-    s_flags = flags;
-    st->total = total;
-    if (total > a.cap) atomicOr(&st->status, ERR_CAPACITY);
-    for (int i = 0; i < kHdr / 4; i++) s_hdr[i] = 0;
-    unsigned char* h = reinterpret_cast<unsigned char*>(s_hdr);
-    auto put32 = [&](int off, uint32_t v) { memcpy(h + off, &v, 4); };
-    auto put64 = [&](int off, uint64_t v) { memcpy(h + off, &v, 8); };
-    put32(0, kMagic);
-    h[4] = (unsigned char)(kVersion & 0xff);
-    h[5] = (unsigned char)(kVersion >> 8);
-    h[6] = (unsigned char)a.ndim;
-    h[7] = (unsigned char)a.eb_mode;
-    for (int i = 0; i < 3; i++) put64(8 + 8 * i, i < a.ndim ? a.dims[i] : 0ull);
-    double eu = a.eb_user, ed = st->eb_d;
-    memcpy(h + 32, &eu, 8);
-    memcpy(h + 40, &ed, 8);
-    float ef = st->eb_f;
-    memcpy(h + 48, &ef, 4);
-    put32(52, a.radius);
-    put32(56, (uint32_t)kHuffSeg);
-    put32(60, flags);
-    put64(64, a.nblk);
-    put64(72, n_rec);
-    put64(80, n_rec - st->n_patch);
-    put64(88, st->n_patch);
-    put64(96, payload);
-    put64(104, total);
-    put32(112, (uint32_t)a.select);
-    for (int i = 0; i < 3; i++) put32(116 + 4 * i, st->ncodec[i]);
-  }
-  __syncthreads();
-  if (s_total > a.cap) return;
-  uint8_t* ar = a.ar;
-  for (int i = tid; i < kHdr / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(ar)[i] = s_hdr[i];
-  // zero padding: codec section, blk_bytes section, payload tail
-  for (uint64_t i = kHdr + a.nblk + tid; i < a.off_bb; i += blockDim.x) ar[i] = 0;
-  for (uint64_t i = a.off_bb + 4ull * a.nblk + tid; i < a.off_rec; i += blockDim.x) ar[i] = 0;
-  const uint64_t pay_end = a.off_rec + 8 * st->n_rec + st->payload;
-  for (uint64_t i = pay_end + tid; i < s_off_books; i += blockDim.x) ar[i] = 0;
-  uint64_t o = s_off_books;
-  if (s_flags & 1) {
-    for (int i = tid; i < kNsymCode; i += blockDim.x) ar[o + i] = a.lens[i];
-    o += kNsymCode;
-  }
-  if (s_flags & 2) {
-    for (int i = tid; i < kNsymCode + kNsymLen; i += blockDim.x) ar[o + i] = a.lens[kNsymCode + i];
-  }
+static size_t encode_smem_bytes() {
+  return kSlots * 2 * 3 + kBufBytes + (kSlots / 32) * 4 * 3 + 16 + 2 * kEncThreads * 4 + 34 * 4 + 33 * 8 + 16;
 }
 
 // =================================================================================
@@ -1055,11 +1081,5 @@ cudaError_t launch_encode(const EncodeArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
-  trace_begin(K_FINALIZE, s);
-  finalize_kernel<<<1, 256, 0, s>>>(a);
-  trace_end(K_FINALIZE, s);
-  return cudaGetLastError();
-}
 
 }  // namespace cszp

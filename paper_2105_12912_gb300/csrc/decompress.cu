@@ -1,10 +1,11 @@
 // Decompression kernels of cszp (sm_103a).
 //
-//   dec_prep_kernel        codec / block-size validation, payload offsets (scan)
-//   dec_records_kernel     record validation, first record of every block
-//   dec_tables_kernel      canonical decode tables + 12-bit lookup table per book
-//   huff_decode_kernel     one thread per 1024-symbol Huffman segment
-//   rle_decode_kernel      one CTA per RLE / RLE+Huffman block
+//   dec_setup_kernel       codec / block-size validation and payload offsets (scan),
+//                          decode tables + 12-bit lookup table per book, record
+//                          validation and each block's first record
+//   stream_decode_kernel   one warp per interleaved 32-lane stream (Huffman code
+//                          streams, RLE+Huffman value and length streams)
+//   rle_expand_kernel      one CTA per RLE / RLE+Huffman block: runs to codes
 //   reconstruct_kernel<ND> fuse outliers (q' = q - r, or delta), N-D partial sums
 //                          per chunk (Alg. 1 l.9-13, Sec. IV-B2), scale by 2eb,
 //                          verbatim patches
@@ -18,7 +19,7 @@ __device__ __forceinline__ void flag(DevState* st, uint32_t bits) { atomicOr(&st
 // =================================================================================
 // archive validation and offsets
 // =================================================================================
-__global__ __launch_bounds__(1024) void dec_prep_kernel(DecodeArgs a) {
+__device__ void dec_prep_body(const DecodeArgs& a) {
   __shared__ uint64_t s_scan[33];
   __shared__ uint32_t s_nc[3];
   const int tid = threadIdx.x;
@@ -48,11 +49,11 @@ __global__ __launch_bounds__(1024) void dec_prep_kernel(DecodeArgs a) {
   if (bad) flag(a.st, ERR_CORRUPT);
 }
 
-__global__ void dec_records_kernel(DecodeArgs a) {
+__device__ void dec_records_body(const DecodeArgs& a, uint32_t cta, uint32_t nctas) {
   const uint32_t* rec = reinterpret_cast<const uint32_t*>(a.ar + a.off_rec);
   const uint64_t nslots = (uint64_t)a.g.nblk * kSlots;
   const uint64_t n = a.n_rec > (uint64_t)a.g.nblk + 1 ? a.n_rec : (uint64_t)a.g.nblk + 1;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+  for (uint64_t i = cta * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)nctas * blockDim.x) {
     if (i < a.n_rec) {
       const uint32_t key = rec[2 * i];
       bool bad = (i + 1 < a.n_rec) && key >= rec[2 * (i + 1)];
@@ -81,13 +82,13 @@ __global__ void dec_records_kernel(DecodeArgs a) {
 
 // One CTA per book: lengths from the archive, Kraft check, canonical tables and a
 // 12-bit lookup table.
-__global__ __launch_bounds__(1024) void dec_tables_kernel(DecodeArgs a) {
+__device__ void dec_tables_body(const DecodeArgs& a, int book) {
   __shared__ uint8_t s_len[kNsymLen];
   __shared__ uint16_t s_wcnt[(kNsymLen / 32) * (kMaxLen + 1)];
   __shared__ CanonSmem cs;
   __shared__ uint32_t s_cnt[kMaxLen + 2];
   __shared__ uint32_t s_bad;
-  const int book = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const int nsym = book == 2 ? kNsymLen : kNsymCode;
   DecTab* t = &a.tabs[book];
   const bool present = book == 0 ? (a.flags & 1u) : (a.flags & 2u);
@@ -133,7 +134,31 @@ __global__ __launch_bounds__(1024) void dec_tables_kernel(DecodeArgs a) {
     t->count[l] = cs.cnt[l];
     t->off[l] = cs.off[l];
   }
-  if (tid == 0) t->present = 1;
+  if (tid == 0) {
+    // canonical codes of length l, left-justified to 64 bits, occupy
+    // [first_l << (64-l), (first_l + count_l) << (64-l)); these ends never decrease
+    uint32_t mx = 0;
+    unsigned long long lim = 0, full = 0;
+    for (int l = 1; l <= kMaxLen; l++) {
+      if (cs.cnt[l]) {
+        mx = l;
+        const unsigned long long end = cs.first[l] + cs.cnt[l];
+        if (l == 64) {
+          lim = end;
+        } else if ((end >> l) != 0) {
+          full |= ~0ull << l;  // the code space is exhausted from this length on
+          lim = 0;
+        } else {
+          lim = end << (64 - l);
+        }
+      }
+      t->limit[l] = lim;
+    }
+    t->fullmask = full;
+    t->limit[0] = 0;
+    t->maxlen = mx;
+    t->present = 1;
+  }
   // lookup: for each 12-bit prefix, the shortest matching code of length <= 12
   for (int v = tid; v < (1 << kLutBits); v += blockDim.x) {
     uint32_t e = 0;
@@ -148,130 +173,205 @@ __global__ __launch_bounds__(1024) void dec_tables_kernel(DecodeArgs a) {
   }
 }
 
-// =================================================================================
-// canonical Huffman decoding
-// =================================================================================
-struct BitReader {
-  const uint32_t* wp;
-  uint32_t wleft;
-  uint64_t bb;  // MSB-aligned bit buffer
-  int nb;       // valid bits in bb
-  __device__ __forceinline__ void refill() {
-    while (nb <= 32 && wleft) {
-      bb |= (uint64_t)(*wp++) << (32 - nb);
-      nb += 32;
-      wleft--;
-    }
+// One launch for archive set-up: CTA 0 validates codecs and scans block sizes, CTAs
+// 1-3 build the decode tables of the three books, the rest validate records and find
+// each block's first record.
+__global__ __launch_bounds__(1024) void dec_setup_kernel(DecodeArgs a) {
+  if (blockIdx.x == 0) {
+    dec_prep_body(a);
+  } else if (blockIdx.x <= 3) {
+    dec_tables_body(a, (int)blockIdx.x - 1);
+  } else {
+    dec_records_body(a, blockIdx.x - 4, gridDim.x - 4);
   }
-};
-
-// Decode one symbol; -1 when the stream ends or no code matches.
-__device__ __forceinline__ int decode_one(BitReader& br, const uint32_t* lut, const unsigned long long* first,
-                                          const uint32_t* count, const uint32_t* off,
-                                          const uint16_t* sorted) {
-  br.refill();
-  if (br.nb == 0) return -1;
-  const uint32_t e = lut[br.bb >> (64 - kLutBits)];
-  const int l = (int)(e & 0xffu);
-  if (l && l <= br.nb) {
-    br.bb <<= l;
-    br.nb -= l;
-    return (int)(e >> 8);
-  }
-  uint64_t c = 0;
-  for (int k = 1; k <= kMaxLen; k++) {
-    if (br.nb == 0) {
-      br.refill();
-      if (br.nb == 0) return -1;
-    }
-    c = (c << 1) | (br.bb >> 63);
-    br.bb <<= 1;
-    br.nb--;
-    if (count[k] && c >= first[k] && c - first[k] < count[k]) return (int)sorted[off[k] + (uint32_t)(c - first[k])];
-  }
-  return -1;
 }
 
-constexpr int kHuffDecThreads = 128;
+// =================================================================================
+// interleaved Huffman streams: one warp decodes one stream (see common.cuh)
+// =================================================================================
+struct BookView {
+  const uint32_t* lut;  // 1 << kLutBits entries
+  const unsigned long long* first;
+  const unsigned long long* limit;
+  const uint32_t* count;
+  const uint32_t* off;
+  const uint16_t* sorted;
+  int maxlen;
+  unsigned long long fullmask;
+};
 
-__global__ __launch_bounds__(kHuffDecThreads) void huff_decode_kernel(DecodeArgs a) {
-  __shared__ uint32_t s_lut[1 << kLutBits];
-  __shared__ unsigned long long s_first[kMaxLen + 1];
-  __shared__ uint32_t s_count[kMaxLen + 1], s_off[kMaxLen + 1];
-  const DecTab* t = &a.tabs[0];
-  if (!(a.flags & 1u) || (a.st->status & ERR_CORRUPT)) return;
-  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) s_lut[i] = t->lut[i];
+// Length of the codeword that is a prefix of the nb valid top bits of bb (0 if none
+// fits in nb bits), and its symbol.  Short codes come from the lookup table; longer
+// ones from the smallest length whose left-justified end exceeds bb, which is the
+// true length whenever it is <= nb (zero bits below nb cannot complete a shorter
+// codeword).
+__device__ __forceinline__ int ihs_match(uint64_t bb, int nb, const BookView& bk, int& sym) {
+  if (nb <= 0) return 0;
+  const uint32_t e = bk.lut[bb >> (64 - kLutBits)];
+  const int l = (int)(e & 0xffu);
+  if (l) {
+    if (l <= nb) {
+      sym = (int)(e >> 8);
+      return l;
+    }
+    return 0;
+  }
+  if (nb <= kLutBits) return 0;
+  int lo = kLutBits + 1, hi = bk.maxlen + 1;  // smallest k whose codes end above bb
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (((bk.fullmask >> mid) & 1ull) || bb < bk.limit[mid]) hi = mid;
+    else lo = mid + 1;
+  }
+  if (lo > bk.maxlen || lo > nb) return 0;
+  const uint64_t c = bb >> (64 - lo);
+  if (c < bk.first[lo] || c - bk.first[lo] >= bk.count[lo]) return 0;  // not a codeword
+  sym = (int)bk.sorted[bk.off[lo] + (uint32_t)(c - bk.first[lo])];
+  return lo;
+}
+
+// One warp decodes N symbols (+add) from in[0..avail) into out[].  Returns false
+// (warp-uniform) if the stream is damaged; *used gets the units read.
+// The warp reads the stream strictly in order, so the next 96 units are kept in three
+// 32-unit register windows (lane i holds unit base+i of each); a top-up takes its unit
+// from a window by shuffle and a window is reloaded (one 64-byte load) two windows
+// before it is needed, so no load sits on the decode's critical path.
+__device__ bool ihs_decode_warp(const uint16_t* __restrict__ in, uint32_t avail, uint32_t N,
+                                const BookView& bk, uint16_t* out, int add, uint32_t* used) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t T = (N + 31) / 32;
+  auto fetch = [&](uint32_t i) -> uint32_t { return i < avail ? (uint32_t)__ldg(&in[i]) : 0u; };
+  uint32_t w0 = fetch(lane), w1 = fetch(32 + lane), w2 = fetch(64 + lane);
+  uint32_t wbase = 0;  // stream index of w0's lane 0
+  uint64_t bb = 0;
+  int nb = 0;
+  uint32_t cur = 0;
+  bool bad = false;
+  for (uint32_t t = 0; t < T; t++) {
+    const bool active = 32 * t + lane < N && !bad;
+    int sym = 0, ml = active ? ihs_match(bb, nb, bk, sym) : 0;
+    bool need = active && ml == 0;
+    uint32_t ballot;
+    while ((ballot = __ballot_sync(~0u, need)) != 0u) {
+      const uint32_t pos = cur + __popc(ballot & ((1u << lane) - 1u));
+      const uint32_t rel = pos - wbase;  // < 64 while cur - wbase < 32
+      const uint32_t u0 = __shfl_sync(~0u, w0, rel & 31);
+      const uint32_t u1 = __shfl_sync(~0u, w1, rel & 31);
+      if (need) {
+        if (nb > 64 - 16 || pos >= avail) {
+          bad = true;
+          need = false;
+        } else {
+          bb |= (uint64_t)(rel < 32 ? u0 : u1) << (48 - nb);
+          nb += 16;
+          ml = ihs_match(bb, nb, bk, sym);  // only lanes that took a unit look again
+          need = ml == 0;
+        }
+      }
+      cur += __popc(ballot);
+      if (cur - wbase >= 32) {
+        w0 = w1;
+        w1 = w2;
+        wbase += 32;
+        w2 = fetch(wbase + 64 + lane);
+      }
+    }
+    if (active && !bad) {
+      out[32 * t + lane] = (uint16_t)(sym + add);
+      bb = ml >= 64 ? 0ull : bb << ml;
+      nb -= ml;
+    }
+  }
+  *used = cur;
+  return !__any_sync(~0u, bad);
+}
+
+constexpr int kStreamWarps = 8;
+
+// Entropy decoding, one warp per interleaved stream: a Huffman block's code stream
+// (warp slot 0; slot 1 idles) or an RLE+Huffman block's value (slot 0) and length
+// (slot 1) streams.  The lookup tables of the books present sit in shared memory.
+// Runs of RLE+Huffman blocks go to the workspace run arrays.
+__global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_kernel(DecodeArgs a) {
+  extern __shared__ __align__(16) uint32_t s_luts[];  // [3][1 << kLutBits]
+  __shared__ unsigned long long s_first[kMaxLen + 1], s_limit[kMaxLen + 1];
+  __shared__ uint32_t s_off[kMaxLen + 1], s_count[kMaxLen + 1];
+  if (a.st->status & ERR_CORRUPT) return;
+  const bool huff = (a.flags & 1u) != 0, rle = (a.flags & 2u) != 0;
+  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) {
+    if (huff) s_luts[i] = a.tabs[0].lut[i];
+    if (rle) {
+      s_luts[(1 << kLutBits) + i] = a.tabs[1].lut[i];
+      s_luts[2 * (1 << kLutBits) + i] = a.tabs[2].lut[i];
+    }
+  }
   for (int i = threadIdx.x; i <= kMaxLen; i += blockDim.x) {
-    s_first[i] = t->first[i];
-    s_count[i] = t->count[i];
-    s_off[i] = t->off[i];
+    s_first[i] = a.tabs[0].first[i];
+    s_limit[i] = a.tabs[0].limit[i];
+    s_off[i] = a.tabs[0].off[i];
+    s_count[i] = a.tabs[0].count[i];
   }
   __syncthreads();
-  if (!t->present) return;
-  const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint32_t b = (uint32_t)(gid >> 2), s = (uint32_t)(gid & 3);
+  const uint32_t gw = blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
+  const uint32_t b = gw >> 1, which = gw & 1;
   if (b >= a.g.nblk) return;
-  if (a.ar[a.off_codec + b] != CODEC_HUFF) return;
+  const int codec = a.ar[a.off_codec + b];
+  if (codec == CODEC_RLE || (codec == CODEC_HUFF && which == 1)) return;
+  const bool lane0 = (threadIdx.x & 31) == 0;
   uint32_t org[3], w[3];
   block_box(a.g, b, org, w);
   const uint32_t m = w[0] * w[1] * w[2];
-  const uint32_t S = (m + kHuffSeg - 1) / kHuffSeg;
-  if (s >= S) return;
   const uint64_t bytes = a.blk_off[b + 1] - a.blk_off[b];
   const uint8_t* pay = a.ar + a.off_pay + a.blk_off[b];
-  const uint32_t hdr = (2 * S + 3) & ~3u;
-  if (hdr > bytes) {
-    flag(a.st, ERR_CORRUPT);
-    return;
-  }
-  const uint16_t* nw16 = reinterpret_cast<const uint16_t*>(pay);
-  uint64_t w0 = hdr / 4, nwtot = hdr / 4;
-  for (uint32_t k = 0; k < S; k++) {
-    if (k < s) w0 += nw16[k];
-    nwtot += nw16[k];
-  }
-  const uint32_t nw = nw16[s];
-  if (4 * nwtot != bytes) {
-    if (s == 0) flag(a.st, ERR_CORRUPT);
-    return;
-  }
-  BitReader br{reinterpret_cast<const uint32_t*>(pay) + w0, nw, 0ull, 0};
-  const uint32_t cnt = min((uint32_t)kHuffSeg, m - s * kHuffSeg);
-  uint16_t* out = a.codes + (uint64_t)b * kSlots + s * kHuffSeg;
-  const uint32_t lim = 2 * a.radius;
-  uint32_t i = 0;
-  for (; i + 8 <= cnt; i += 8) {
-    uint32_t v[4];
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const int sym = decode_one(br, s_lut, s_first, s_count, s_off, t->sorted);
-      if (sym < 0 || (uint32_t)sym >= lim) {
-        flag(a.st, ERR_CORRUPT);
-        return;
-      }
-      if (k & 1) v[k >> 1] |= (uint32_t)sym << 16;
-      else v[k >> 1] = (uint32_t)sym;
-    }
-    *reinterpret_cast<uint4*>(out + i) = make_uint4(v[0], v[1], v[2], v[3]);
-  }
-  for (; i < cnt; i++) {
-    const int sym = decode_one(br, s_lut, s_first, s_count, s_off, t->sorted);
-    if (sym < 0 || (uint32_t)sym >= lim) {
-      flag(a.st, ERR_CORRUPT);
+  uint32_t used = 0;
+  bool ok;
+  if (codec == CODEC_HUFF) {
+    const DecTab* t = &a.tabs[0];
+    if (!t->present) {
+      if (lane0) flag(a.st, ERR_CORRUPT);
       return;
     }
-    out[i] = (uint16_t)sym;
+    const BookView bk{s_luts, s_first, s_limit, s_count, s_off, t->sorted, (int)t->maxlen, t->fullmask};
+    ok = ihs_decode_warp(reinterpret_cast<const uint16_t*>(pay), (uint32_t)(bytes / 2), m, bk,
+                         a.codes + (uint64_t)b * kSlots, 0, &used);
+    ok = ok && ((2ull * used + 3) & ~3ull) == bytes;
+  } else {
+    const DecTab* t = &a.tabs[1 + which];
+    if (!t->present) {
+      if (lane0) flag(a.st, ERR_CORRUPT);
+      return;
+    }
+    const uint32_t* p32 = reinterpret_cast<const uint32_t*>(pay);
+    const uint32_t nr = bytes >= 8 ? p32[0] : 0u, vu = bytes >= 8 ? p32[1] : 0u;
+    if (bytes < 8 || nr > m || 8ull + 2ull * vu > bytes) {
+      if (lane0) flag(a.st, ERR_CORRUPT);
+      return;
+    }
+    const uint32_t lavail = (uint32_t)((bytes - 8) / 2 - vu);
+    const BookView bk{s_luts + (1 + which) * (1 << kLutBits), t->first, t->limit, t->count, t->off, t->sorted,
+                      (int)t->maxlen, t->fullmask};
+    const uint16_t* p16 = reinterpret_cast<const uint16_t*>(pay) + 4;
+    if (which == 0) {
+      ok = ihs_decode_warp(p16, vu, nr, bk, a.runv + (uint64_t)b * kSlots, 0, &used);
+      ok = ok && used == vu;
+    } else {
+      ok = ihs_decode_warp(p16 + vu, lavail, nr, bk, a.runl + (uint64_t)b * kSlots, 1, &used);
+      ok = ok && ((8ull + 2ull * (vu + used) + 3) & ~3ull) == bytes;
+    }
   }
+  if (!ok && lane0) flag(a.st, ERR_CORRUPT);
 }
 
 constexpr int kRleThreads = 256;
 
-__global__ __launch_bounds__(kRleThreads) void rle_decode_kernel(DecodeArgs a) {
+// RLE and RLE+Huffman blocks: run starts by a block scan, then every code position
+// finds its run by binary search.
+__global__ __launch_bounds__(kRleThreads) void rle_expand_kernel(DecodeArgs a) {
   __shared__ uint16_t s_v[kSlots];
   __shared__ uint16_t s_l[kSlots];
   __shared__ uint32_t s_start[kSlots + 1];
   __shared__ uint32_t s_scan[33];
-  __shared__ uint32_t s_nr, s_bad;
+  __shared__ uint32_t s_bad;
   const uint32_t b = blockIdx.x;
   const int tid = threadIdx.x;
   const int codec = a.ar[a.off_codec + b];
@@ -283,55 +383,28 @@ __global__ __launch_bounds__(kRleThreads) void rle_decode_kernel(DecodeArgs a) {
   const uint64_t bytes = a.blk_off[b + 1] - a.blk_off[b];
   const uint8_t* pay = a.ar + a.off_pay + a.blk_off[b];
   const uint32_t lim = 2 * a.radius;
+  uint32_t nr;
+  const uint16_t *v, *l;
+  if (codec == CODEC_RLE) {
+    nr = (uint32_t)(bytes / 4);
+    v = reinterpret_cast<const uint16_t*>(pay);
+    l = v + nr;
+  } else {
+    nr = reinterpret_cast<const uint32_t*>(pay)[0];
+    v = a.runv + (uint64_t)b * kSlots;
+    l = a.runl + (uint64_t)b * kSlots;
+  }
+  if (nr > m) {
+    if (tid == 0) flag(a.st, ERR_CORRUPT);
+    return;
+  }
   if (tid == 0) s_bad = 0;
   __syncthreads();
-  if (codec == CODEC_RLE) {
-    const uint64_t nr = bytes / 4;
-    if (nr > m) {
-      if (tid == 0) flag(a.st, ERR_CORRUPT);
-      return;
-    }
-    const uint16_t* p16 = reinterpret_cast<const uint16_t*>(pay);
-    for (uint32_t i = tid; i < nr; i += blockDim.x) {
-      s_v[i] = p16[i];
-      s_l[i] = p16[nr + i];
-    }
-    if (tid == 0) s_nr = (uint32_t)nr;
-  } else {
-    const uint32_t* p32 = reinterpret_cast<const uint32_t*>(pay);
-    uint32_t nr = 0, vw = 0;
-    if (bytes >= 8) {
-      nr = p32[0];
-      vw = p32[1];
-    }
-    if (bytes < 8 || nr > m || 8ull + 4ull * vw > bytes) {
-      if (tid == 0) flag(a.st, ERR_CORRUPT);
-      return;
-    }
-    const uint32_t lw = (uint32_t)((bytes - 8 - 4ull * vw) / 4);
-    // values on warp 0 lane 0, lengths on warp 1 lane 0
-    if (tid == 0 || tid == 32) {
-      const DecTab* t = &a.tabs[tid == 0 ? 1 : 2];
-      if (!t->present) {
-        s_bad = 1;
-      } else {
-        BitReader br = tid == 0 ? BitReader{p32 + 2, vw, 0ull, 0} : BitReader{p32 + 2 + vw, lw, 0ull, 0};
-        uint16_t* dst = tid == 0 ? s_v : s_l;
-        for (uint32_t i = 0; i < nr; i++) {
-          const int sym = decode_one(br, t->lut, t->first, t->count, t->off, t->sorted);
-          if (sym < 0) {
-            s_bad = 1;
-            break;
-          }
-          dst[i] = (uint16_t)(tid == 0 ? sym : sym + 1);
-        }
-      }
-    }
-    if (tid == 0) s_nr = nr;
+  for (uint32_t i = tid; i < nr; i += blockDim.x) {
+    s_v[i] = v[i];
+    s_l[i] = l[i];
   }
   __syncthreads();
-  const uint32_t nr = s_nr;
-  // run starts by a block scan over contiguous shares of the runs
   const uint32_t per = (nr + blockDim.x - 1) / blockDim.x;
   const uint32_t lo = min(nr, tid * per), hi = min(nr, lo + per);
   uint32_t sum = 0;
@@ -351,16 +424,51 @@ __global__ __launch_bounds__(kRleThreads) void rle_decode_kernel(DecodeArgs a) {
     if (tid == 0) flag(a.st, ERR_CORRUPT);
     return;
   }
-  uint16_t* out = a.codes + (uint64_t)b * kSlots;
-  for (uint32_t j = tid; j < m; j += blockDim.x) {
-    uint32_t l = 0, h = nr;  // last run with start <= j
-    while (h - l > 1) {
-      const uint32_t mid = (l + h) >> 1;
-      if (s_start[mid] <= j) l = mid;
-      else h = mid;
-    }
-    out[j] = s_v[l];
+  // run index of every position: mark run starts, then a running maximum
+  uint32_t* s_idx = s_start;  // starts are no longer needed once marked below
+  uint32_t my_starts[16];
+  const uint32_t cnt = hi - lo;
+  for (uint32_t i = 0; i < cnt && i < 16; i++) my_starts[i] = s_start[lo + i];
+  __syncthreads();
+  for (int i = tid; i < kSlots; i += blockDim.x) s_idx[i] = 0;
+  __syncthreads();
+  if (cnt <= 16) {
+    for (uint32_t i = 0; i < cnt; i++)
+      if (my_starts[i] < m) s_idx[my_starts[i]] = lo + i;
   }
+  __syncthreads();
+  // contiguous 16 positions per thread: local running max, then a block scan of maxima
+  uint32_t run = 0;
+  const uint32_t p0 = 16 * tid;
+#pragma unroll
+  for (int i = 0; i < 16; i++) run = max(run, s_idx[p0 + i]);
+  // exclusive running max over threads (warp scan + per-warp carries)
+  uint32_t incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(~0u, incl, o);
+    if ((tid & 31) >= o) incl = max(incl, u);
+  }
+  if ((tid & 31) == 31) s_scan[tid >> 5] = incl;
+  __syncthreads();
+  uint32_t carry = 0;
+  for (int wv = 0; wv < (tid >> 5); wv++) carry = max(carry, s_scan[wv]);
+  uint32_t excl = __shfl_up_sync(~0u, incl, 1);
+  if ((tid & 31) == 0) excl = 0;
+  uint32_t cur = max(carry, excl);
+  uint16_t* out = a.codes + (uint64_t)b * kSlots;
+  uint32_t vals[8];
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    cur = max(cur, s_idx[p0 + i]);
+    const uint16_t v = s_v[cur];
+    if (i & 1) vals[i >> 1] |= (uint32_t)v << 16;
+    else vals[i >> 1] = v;
+  }
+  // positions >= m get whatever run they fall in; they are never read
+  uint4* o4 = reinterpret_cast<uint4*>(out + p0);
+  o4[0] = make_uint4(vals[0], vals[1], vals[2], vals[3]);
+  o4[1] = make_uint4(vals[4], vals[5], vals[6], vals[7]);
 }
 
 // =================================================================================
@@ -501,25 +609,20 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) 
 }
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
-  trace_begin(K_DEC_PREP, s);
-  dec_prep_kernel<<<1, 1024, 0, s>>>(a);
-  trace_end(K_DEC_PREP, s);
   const uint64_t n = (a.n_rec > (uint64_t)a.g.nblk + 1 ? a.n_rec : (uint64_t)a.g.nblk + 1);
-  uint64_t grid = (n + 255) / 256;
-  if (grid > 4096) grid = 4096;
-  trace_begin(K_DEC_RECORDS, s);
-  dec_records_kernel<<<(unsigned)grid, 256, 0, s>>>(a);
-  trace_end(K_DEC_RECORDS, s);
-  trace_begin(K_DEC_TABLES, s);
-  dec_tables_kernel<<<3, 1024, 0, s>>>(a);
-  trace_end(K_DEC_TABLES, s);
-  const uint64_t nseg = (uint64_t)a.g.nblk * 4;
-  trace_begin(K_HUFF_DECODE, s);
-  huff_decode_kernel<<<(unsigned)((nseg + kHuffDecThreads - 1) / kHuffDecThreads), kHuffDecThreads, 0, s>>>(a);
-  trace_end(K_HUFF_DECODE, s);
-  trace_begin(K_RLE_DECODE, s);
-  rle_decode_kernel<<<a.g.nblk, kRleThreads, 0, s>>>(a);
-  trace_end(K_RLE_DECODE, s);
+  uint64_t rec_ctas = (n + 1023) / 1024;
+  if (rec_ctas > 1024) rec_ctas = 1024;
+  trace_begin(K_DEC_SETUP, s);
+  dec_setup_kernel<<<(unsigned)(4 + rec_ctas), 1024, 0, s>>>(a);
+  trace_end(K_DEC_SETUP, s);
+  const size_t lut_bytes = 3 * (1u << kLutBits) * sizeof(uint32_t);
+  cudaFuncSetAttribute(stream_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lut_bytes);
+  trace_begin(K_STREAM_DECODE, s);
+  stream_decode_kernel<<<(2 * a.g.nblk + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps, lut_bytes, s>>>(a);
+  trace_end(K_STREAM_DECODE, s);
+  trace_begin(K_RLE_EXPAND, s);
+  rle_expand_kernel<<<a.g.nblk, kRleThreads, 0, s>>>(a);
+  trace_end(K_RLE_EXPAND, s);
   trace_begin(K_RECONSTRUCT, s);
   if (a.g.ndim == 1)
     reconstruct_kernel<1><<<a.g.nblk, kRecThreads, 0, s>>>(a);

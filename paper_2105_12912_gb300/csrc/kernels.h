@@ -33,6 +33,19 @@ struct BookArgs {
   DevState* st;
 };
 
+struct FinalizeArgs {
+  DevState* st;
+  uint8_t* ar;
+  uint64_t cap;
+  int ndim, eb_mode;
+  uint64_t dims[3];
+  double eb_user;
+  uint32_t radius;
+  int select;
+  uint64_t nblk, off_bb, off_rec;
+  const uint8_t* lens;
+};
+
 struct EncodeArgs {
   Geom g;
   DevState* st;
@@ -48,27 +61,18 @@ struct EncodeArgs {
   uint64_t off_codec, off_bb, off_rec;
   uint64_t* lb;
   uint32_t spin_limit;
-};
-
-struct FinalizeArgs {
-  DevState* st;
-  uint8_t* ar;
-  uint64_t cap;
-  int ndim, eb_mode;
-  uint64_t dims[3];
-  double eb_user;
-  uint32_t radius;
-  int select;
-  uint64_t nblk, off_bb, off_rec;
-  const uint8_t* lens;
+  FinalizeArgs fin;  // used by the last block to finish
 };
 
 // decode tables of one canonical book
 struct DecTab {
   unsigned long long first[kMaxLen + 1];
+  unsigned long long limit[kMaxLen + 1];  // left-justified end of the codes up to each length
+  unsigned long long fullmask;            // bit l: the codes up to length l reach 2^64
   uint32_t count[kMaxLen + 1];
   uint32_t off[kMaxLen + 1];
   uint32_t present;
+  uint32_t maxlen;
   uint16_t sorted[kNsymLen];
   uint32_t lut[1 << kLutBits];  // (symbol << 8) | length, 0 = longer than kLutBits
 };
@@ -86,6 +90,8 @@ struct DecodeArgs {
   uint32_t* rec_start; // [nblk+1]
   DecTab* tabs;        // [3]
   uint16_t* codes;     // nblk * 4096
+  uint16_t* runv;      // decoded run values of RLE+Huffman blocks (may alias codes)
+  uint16_t* runl;      // nblk * 4096 decoded run lengths
   float* out;
 };
 
@@ -96,12 +102,9 @@ enum KernelId : int {
   K_CONSTRUCT,
   K_CODEBOOK,
   K_ENCODE,
-  K_FINALIZE,
-  K_DEC_PREP,
-  K_DEC_RECORDS,
-  K_DEC_TABLES,
-  K_HUFF_DECODE,
-  K_RLE_DECODE,
+  K_DEC_SETUP,
+  K_STREAM_DECODE,
+  K_RLE_EXPAND,
   K_RECONSTRUCT,
   K_COUNT
 };
@@ -114,7 +117,6 @@ cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, dou
 cudaError_t launch_construct(int ndim, const ConstructArgs& a, cudaStream_t s);
 cudaError_t launch_codebook(const BookArgs& a, cudaStream_t s);
 cudaError_t launch_encode(const EncodeArgs& a, cudaStream_t s);
-cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);
 

@@ -10,9 +10,9 @@
 namespace {
 
 // Scratch for any archive of at most kStaticMaxBlocks codec blocks (the workspace of
-// a 64-block shape is about 670 KiB).  Every GPU that loads the library holds this
+// a 64-block shape is about 1.16 MiB).  Every GPU that loads the library holds this
 // array until the process exits.
-constexpr size_t kStaticScratchBytes = 768 * 1024;
+constexpr size_t kStaticScratchBytes = 1280 * 1024;
 constexpr uint64_t kStaticMaxBlocks = 64;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 

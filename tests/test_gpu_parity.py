@@ -165,3 +165,25 @@ def test_cross_decode(gpu, orc):
     y, st = gpu.decompress(torch.from_numpy(ref).cuda(), ref.size)
     ost, yo = orc.decompress(ref, x.size)
     assert np.array_equal(y.cpu().numpy().ravel().view(np.uint32), yo.view(np.uint32))
+
+
+def test_parity_deep_huffman_codes(gpu, orc):
+    """Residual counts following the Fibonacci numbers give a maximally deep Huffman
+    tree (codes far longer than the 12-bit lookup table), exercising the decoder's
+    long-code search and multi-unit top-ups."""
+    fib = [1, 1]
+    while len(fib) < 28:
+        fib.append(fib[-1] + fib[-2])
+    rng = np.random.default_rng(17)
+    deltas = np.concatenate([np.full(c, i - 14, np.int64) for i, c in enumerate(fib)])
+    rng.shuffle(deltas)
+    n = deltas.size - deltas.size % 256
+    deltas = deltas[:n]
+    x = np.empty(n, np.float32)
+    for c0 in range(0, n, 256):  # prediction restarts at every 256-element chunk
+        x[c0:c0 + 256] = np.cumsum(deltas[c0:c0 + 256])
+    for sel in ("huff", "exhaustive"):
+        _check(gpu, orc, x, eb=0.5, mode="abs", sel=sel)
+    st, ar = orc.compress(x, orc.EB_ABS, 0.5, select=orc.SEL_HUFF)
+    books = orc.sections(ar)["books"][:1024]
+    assert books.max() >= 24  # deep enough to leave the lookup table far behind

@@ -441,3 +441,34 @@ def test_mlp_forward_and_gradient(orc):
             return ((a @ ww[1344:1440].reshape(3, 32).T + ww[1440:1443] - tgt) ** 2).mean()
         fd = (L(wp) - L(wm)) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(fd))
+
+
+# ---------------------------------------------------------------------------------
+# interleaved Huffman stream layout, closed form: with a two-symbol book every code
+# is one bit, so each of the 32 lanes tops up one 16-bit unit at steps 0, 16, 32, ...
+# and the stream is lane 0..31's unit 0, then their unit 1, and so on
+# ---------------------------------------------------------------------------------
+def test_interleaved_stream_layout_one_bit_codes(orc):
+    rng = np.random.default_rng(12)
+    n = 4096
+    d = rng.integers(0, 2, n)                 # residuals 0/1 -> codes 512/513
+    x = np.zeros(n, np.float32)
+    for c0 in range(0, n, 256):               # prediction restarts at every chunk
+        x[c0:c0 + 256] = np.cumsum(d[c0:c0 + 256])
+    st, ar = orc.compress(x, orc.EB_ABS, 0.5, select=orc.SEL_HUFF)
+    sec = orc.sections(ar)
+    books = sec["books"]
+    assert books[512] == 1 and books[513] == 1 and books[:1024].sum() == 2
+    units = sec["payload"].view(np.uint16)
+    assert units.size == 32 * 8                # 128 bits per lane -> 8 units each
+    expect = np.zeros((8, 32), np.uint16)
+    for lane in range(32):
+        bits = d[lane::32]                     # the lane's symbols, one bit each
+        for k in range(8):
+            v = 0
+            for b in bits[16 * k:16 * k + 16]:
+                v = (v << 1) | int(b)
+            expect[k, lane] = v
+    assert np.array_equal(units, expect.ravel())
+    st, y = orc.decompress(ar, n)
+    assert np.array_equal(y, x)
