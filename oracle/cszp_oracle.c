@@ -197,7 +197,7 @@ static int exceeds(float x, float y, float eb) {
  * Prequantization (Sec. IV-A1, Alg. 1 l.2): d° = round(d / 2eb), so that
  * |d - d°*2eb| < eb in exact arithmetic.  In FP32 the product d*(1/2eb) and the
  * reconstruction fl32(d°*2eb) both round, so:
- *   k0 = round-half-away(fl32(x * ebx2_r));
+ *   k0 = nearest integer to fl32(x * ebx2_r), ties to even;
  *   if the reconstruction of k0 misses x by more than eb_f, try the neighbour
  *   integer on x's side; if neither meets the bound, keep k0 and mark the value
  *   for a verbatim patch (the SZ family's "unpredictable" fallback).
@@ -208,7 +208,7 @@ int orc_prequant(float x, float eb_f, float ebx2_f, float ebx2_r, int32_t* k, in
   if (!isfinite(x)) return ORC_E_NONFINITE;
   float v = x * ebx2_r;
   if (!(fabsf(v) < 8388608.0f)) return ORC_E_RANGE;
-  int32_t k0 = (int32_t)roundf(v);
+  int32_t k0 = (int32_t)rintf(v); /* nearest integer, ties to even (IEEE default mode) */
   float x0 = (float)k0 * ebx2_f;
   *patch = 0;
   if (!exceeds(x, x0, eb_f)) {
@@ -364,8 +364,17 @@ static uint64_t make_runs(const uint16_t* c, uint64_t m, run_t* out) {
   return nr;
 }
 
-int orc_run_stats(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_t* val_hist,
-                  uint32_t* len_hist, uint32_t* nruns) {
+/*
+ * Run eligibility (a reading): a block whose runs average fewer than 4 codes
+ * (4 * runs > m) gains nothing from Huffman-coding its runs, so in the adaptive modes
+ * it never uses RLE+Huffman and its runs stay out of the run books (plain RLE needs
+ * no book and stays available to the exhaustive choice).  Forced RLE and RLE+Huffman
+ * make every block eligible.
+ */
+static int run_eligible(uint64_t nr, uint64_t m, int all_blocks) { return all_blocks || 4 * nr <= m; }
+
+int orc_run_stats(const uint16_t* codes, int ndim, const uint64_t* dims, int all_blocks,
+                  uint32_t* val_hist, uint32_t* len_hist, uint32_t* nruns) {
   geom_t g;
   int st = make_geom(ndim, dims, &g);
   if (st) return st;
@@ -375,10 +384,11 @@ int orc_run_stats(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_
   for (uint64_t b = 0; b < g.nblk; b++) {
     uint64_t m = block_count(&g, b);
     uint64_t nr = make_runs(codes + b * SLOTS, m, runs);
-    for (uint64_t i = 0; i < nr; i++) {
-      val_hist[runs[i].v]++;
-      len_hist[runs[i].len - 1]++;
-    }
+    if (run_eligible(nr, m, all_blocks))
+      for (uint64_t i = 0; i < nr; i++) {
+        val_hist[runs[i].v]++;
+        len_hist[runs[i].len - 1]++;
+      }
     nruns[b] = (uint32_t)nr;
   }
   free(runs);
@@ -697,7 +707,7 @@ static void rlehuff_write(const run_t* runs, uint64_t nr, const uint8_t* vlen,
 
 int orc_block_sizes(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_t radius,
                     const uint8_t* code_len, const uint8_t* val_len, const uint8_t* len_len,
-                    uint32_t lanes, uint64_t* sizes) {
+                    uint32_t lanes, int all_blocks, uint64_t* sizes) {
   geom_t g;
   int st = make_geom(ndim, dims, &g);
   if (st) return st;
@@ -716,7 +726,10 @@ int orc_block_sizes(const uint16_t* codes, int ndim, const uint64_t* dims, uint3
     int miss_h = 0, miss_r = 0;
     sizes[3 * b + ORC_CODEC_HUFF] = huff_size(c, m, code_len, ccode, &miss_h);
     sizes[3 * b + ORC_CODEC_RLE] = 4 * nr;
-    sizes[3 * b + ORC_CODEC_RLE_HUFF] = rlehuff_size(runs, nr, val_len, vcode, len_len, lcode, &miss_r);
+    if (run_eligible(nr, m, all_blocks))
+      sizes[3 * b + ORC_CODEC_RLE_HUFF] = rlehuff_size(runs, nr, val_len, vcode, len_len, lcode, &miss_r);
+    else
+      sizes[3 * b + ORC_CODEC_RLE_HUFF] = UINT64_MAX;
     missing |= miss_h | miss_r;
   }
   free(runs);
@@ -1047,7 +1060,8 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
   st = orc_construct(x, ndim, dims, eb_f, ebx2_f, ebx2_r, radius, codes, rk, rv, 2 * g.nelem + 1,
                      &nrec, hist);
   if (st) goto done;
-  orc_run_stats(codes, ndim, dims, vh, lh, nruns);
+  const int all_blocks = select == ORC_SEL_RLE_HUFF || select == ORC_SEL_RLE;
+  orc_run_stats(codes, ndim, dims, all_blocks, vh, lh, nruns);
 
   uint8_t clen[NSYM_CODE], vlen[NSYM_CODE], llen[NSYM_LEN];
   uint64_t ccode[NSYM_CODE], vcode[NSYM_CODE], lcode[NSYM_LEN];
@@ -1057,7 +1071,7 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
   orc_canonical_codes(clen, NSYM_CODE, ccode);
   orc_canonical_codes(vlen, NSYM_CODE, vcode);
   orc_canonical_codes(llen, NSYM_LEN, lcode);
-  st = orc_block_sizes(codes, ndim, dims, radius, clen, vlen, llen, LANES, sizes);
+  st = orc_block_sizes(codes, ndim, dims, radius, clen, vlen, llen, LANES, all_blocks, sizes);
   if (st) goto done;
 
   /* codec per block */
@@ -1072,6 +1086,8 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
       c = ORC_CODEC_HUFF;
       if (s[ORC_CODEC_RLE_HUFF] < s[c]) c = ORC_CODEC_RLE_HUFF;
       if (s[ORC_CODEC_RLE] < s[c]) c = ORC_CODEC_RLE;
+    } else if (!run_eligible(nruns[b], block_count(&g, b), 0)) {
+      c = ORC_CODEC_HUFF; /* heuristic and learned choose between Huffman and RLE+Huffman */
     } else if (select == ORC_SEL_HEURISTIC) {
       uint32_t bh[NSYM_CODE] = {0};
       uint64_t m = block_count(&g, b);

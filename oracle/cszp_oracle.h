@@ -81,20 +81,21 @@ int orc_construct(const float* x, int ndim, const uint64_t* dims, float eb_f, fl
                   float ebx2_r, uint32_t radius, uint16_t* codes, uint32_t* rec_key,
                   uint32_t* rec_val, uint64_t rec_cap, uint64_t* n_rec, uint32_t* hist);
 
-/* runs of each block: value histogram [1024], length histogram [4096] (index len-1),
-   runs per block */
-int orc_run_stats(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_t* val_hist,
-                  uint32_t* len_hist, uint32_t* nruns);
+/* runs of each block: value histogram [1024], length histogram [4096] (index len-1)
+   over run-eligible blocks (every block if all_blocks), runs per block */
+int orc_run_stats(const uint16_t* codes, int ndim, const uint64_t* dims, int all_blocks,
+                  uint32_t* val_hist, uint32_t* len_hist, uint32_t* nruns);
 
 /* Huffman code lengths (two-queue construction) and canonical codes */
 int orc_huffman_lengths(const uint32_t* freq, int nsym, uint8_t* len);
 int orc_canonical_codes(const uint8_t* len, int nsym, uint64_t* code);
 
-/* per-block exact encoded sizes [nblk][3] (bytes) for the three codecs; lanes must
-   be 32 (the interleave width of Huffman streams) */
+/* per-block exact encoded sizes [nblk][3] (bytes) for the three codecs (UINT64_MAX for
+   RLE+Huffman of a block that is not run-eligible); lanes must be 32 (the interleave
+   width of Huffman streams) */
 int orc_block_sizes(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_t radius,
                     const uint8_t* code_len, const uint8_t* val_len, const uint8_t* len_len,
-                    uint32_t lanes, uint64_t* sizes);
+                    uint32_t lanes, int all_blocks, uint64_t* sizes);
 
 /* per-block selector features [nblk][8] */
 int orc_block_features(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_t radius,

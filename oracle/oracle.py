@@ -53,10 +53,11 @@ def lib():
             "orc_geometry": (C.c_int, [C.c_int, _u64p, _u64p, _u64p]),
             "orc_construct": (C.c_int, [_f32p, C.c_int, _u64p, C.c_float, C.c_float, C.c_float, C.c_uint32,
                                         _u16p, _u32p, _u32p, C.c_uint64, _u64p, _u32p]),
-            "orc_run_stats": (C.c_int, [_u16p, C.c_int, _u64p, _u32p, _u32p, _u32p]),
+            "orc_run_stats": (C.c_int, [_u16p, C.c_int, _u64p, C.c_int, _u32p, _u32p, _u32p]),
             "orc_huffman_lengths": (C.c_int, [_u32p, C.c_int, _u8p]),
             "orc_canonical_codes": (C.c_int, [_u8p, C.c_int, _u64p]),
-            "orc_block_sizes": (C.c_int, [_u16p, C.c_int, _u64p, C.c_uint32, _u8p, _u8p, _u8p, C.c_uint32, _u64p]),
+            "orc_block_sizes": (C.c_int, [_u16p, C.c_int, _u64p, C.c_uint32, _u8p, _u8p, _u8p, C.c_uint32, C.c_int,
+                                          _u64p]),
             "orc_block_features": (C.c_int, [_u16p, C.c_int, _u64p, C.c_uint32, _f32p]),
             "orc_heuristic_pick": (C.c_int, [_u32p, C.c_int, C.c_uint32]),
             "orc_log2_q16": (C.c_uint32, [C.c_uint64]),
@@ -160,14 +161,14 @@ def construct(x, eb_f, ebx2_f, ebx2_r, radius=512):
     return {"codes": codes, "keys": keys[:n].copy(), "vals": vals[:n].copy(), "hist": hist, "nblk": nblk}
 
 
-def run_stats(codes, dims):
+def run_stats(codes, dims, all_blocks=True):
     nblk, _ = geometry(dims)
     codes = np.ascontiguousarray(codes, dtype=np.uint16)
     vh = np.zeros(1024, dtype=np.uint32)
     lh = np.zeros(4096, dtype=np.uint32)
     nr = np.zeros(nblk, dtype=np.uint32)
-    st = lib().orc_run_stats(_p(codes, _u16p), len(dims), _p(_dims(dims), _u64p), _p(vh, _u32p), _p(lh, _u32p),
-                             _p(nr, _u32p))
+    st = lib().orc_run_stats(_p(codes, _u16p), len(dims), _p(_dims(dims), _u64p), int(all_blocks), _p(vh, _u32p),
+                             _p(lh, _u32p), _p(nr, _u32p))
     if st:
         raise OracleError(st, "run_stats")
     return vh, lh, nr
@@ -191,13 +192,13 @@ def canonical_codes(lengths):
     return code
 
 
-def block_sizes(codes, dims, radius, code_len, val_len, len_len):
+def block_sizes(codes, dims, radius, code_len, val_len, len_len, all_blocks=True):
     nblk, _ = geometry(dims)
     out = np.zeros((nblk, 3), dtype=np.uint64)
     c = np.ascontiguousarray(codes, dtype=np.uint16)
     a, b, d = (np.ascontiguousarray(v, dtype=np.uint8) for v in (code_len, val_len, len_len))
     st = lib().orc_block_sizes(_p(c, _u16p), len(dims), _p(_dims(dims), _u64p), int(radius), _p(a, _u8p),
-                               _p(b, _u8p), _p(d, _u8p), 32, _p(out, _u64p))
+                               _p(b, _u8p), _p(d, _u8p), 32, int(all_blocks), _p(out, _u64p))
     if st:
         raise OracleError(st, "block_sizes")
     return out
