@@ -38,18 +38,19 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["2d", "1d", "3d"], default="2d")
     p.add_argument("--select", default="exhaustive")
+    p.add_argument("--n3d", type=int, default=512, help="side of the 3-D workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
 
-def workload_spec(name, rank=0):
+def workload_spec(name, rank=0, n3d=512):
     from paper_2105_12912_gb300 import synth
     if name == "2d":
         return synth.workload_2d(seed=2 + 1000 * rank)
     if name == "1d":
         return synth.workload_1d(seed=1 + 1000 * rank)
-    return synth.workload_3d(seed=3 + 1000 * rank, eb=1e-4)
+    return synth.workload_3d(n=n3d, seed=3 + 1000 * rank, eb=1e-4)
 
 
 def measured_peak_hbm():
@@ -141,7 +142,7 @@ def run_reference(args):
         return
     from oracle import oracle as O
     from paper_2105_12912_gb300 import synth
-    spec = workload_spec(args.workload)
+    spec = workload_spec(args.workload, 0, args.n3d)
     x = synth.make_field(spec, "cpu").numpy()
     # bounded sample: a slab of the field along the slowest axis (~1.3M elements)
     rows = max(1, min(x.shape[0], int(math.ceil(1_300_000 / max(1, x.size // x.shape[0])))))
@@ -199,13 +200,15 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream()
 
-    spec = workload_spec(args.workload, rank)
+    spec = workload_spec(args.workload, rank, args.n3d)
     x = synth.make_field(spec, dev)
     n = x.numel()
     bytes_in = 4 * n
     dims = tuple(x.shape)
     ws = api.Workspace(dev)
-    arc = torch.empty(api.max_archive_bytes(dims), dtype=torch.uint8, device=dev)
+    # archive buffer: twice the input is ample for these fields (the worst-case bound,
+    # csz_max_archive_bytes, is 32 B per element); a smaller buffer is an error, not UB
+    arc = torch.empty(min(api.max_archive_bytes(dims), 8 * n + (1 << 20)), dtype=torch.uint8, device=dev)
     rec = torch.empty_like(x)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 

@@ -287,6 +287,7 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   ca.hist_len = at<uint32_t>(d_ws, L.hist_len);
   ca.lb = at<uint64_t>(d_ws, L.lb_c);
   ca.spin_limit = g_spin_limit;
+  ca.all_runs = (select == SEL_RLE || select == SEL_RLE_HUFF) ? 1 : 0;
   if (launch_construct(ndim, ca, s) != cudaSuccess) return CSZ_E_CUDA;
 
   BookArgs ba;
@@ -308,6 +309,7 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   ea.bcodes = ba.codes;
   ea.mlp_w = opt ? opt->selector_weights : nullptr;
   ea.feat_out = nullptr;
+  ea.all_runs = ca.all_runs;
   ea.ar = d_ar;
   ea.cap = cap;
   ea.off_codec = kHdr;

@@ -231,7 +231,7 @@ __device__ __forceinline__ bool exceeds_exact(float x, float y, float eb) {
   return s > 0.0f ? e > 0.0f : e < 0.0f;
 }
 
-// k0 = round-half-away(fl32(x/2eb)); if fl32(k0*2eb) misses x by more than eb, try the
+// k0 = nearest integer to fl32(x/2eb), ties to even; if fl32(k0*2eb) misses x by more than eb, try the
 // neighbour integer on x's side, else keep k0 and ask for a verbatim patch.
 // Returns ERR_* bits (0 on success).
 __device__ __forceinline__ uint32_t prequant(float x, float eb_f, float ebx2_f, float ebx2_r,
@@ -241,7 +241,7 @@ __device__ __forceinline__ uint32_t prequant(float x, float eb_f, float ebx2_f, 
   if (!isfinite(x)) return ERR_NONFINITE;
   float v = __fmul_rn(x, ebx2_r);
   if (!(fabsf(v) < 8388608.0f)) return ERR_RANGE;
-  int32_t k0 = (int32_t)roundf(v);
+  int32_t k0 = __float2int_rn(v);
   float x0 = __fmul_rn(__int2float_rn(k0), ebx2_f);
   if (!exceeds_exact(x, x0, eb_f)) {
     k = k0;

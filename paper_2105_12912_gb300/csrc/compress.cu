@@ -208,10 +208,122 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
   const int32_t r = (int32_t)a.radius;
   uint32_t err = 0;
 
-  // ---- load and prequantize ------------------------------------------------------
+  // ---- load, prequantize, Lorenzo residual (Sec. IV-B2), postquantize -------------
+  // The residual is the mixed difference (1 - S_x)(1 - S_y)(1 - S_z) k, each shift
+  // reading zero outside the chunk; that expansion is the paper's 1/2/3-D predictor.
+  // Full blocks take it in registers and shuffles; edge blocks stage k in shared
+  // memory.  Outlier deltas are kept in s_k at their positions; outlier and patch
+  // positions are bit masks.
   const float* __restrict__ x = a.x;
   const uint64_t ny = g.n[1], nx = g.n[2];
   const bool aligned = ((((uintptr_t)x) & 15) == 0) && (nx % 4 == 0);
+  const bool full = w[0] == g.blk[0] && w[1] == g.blk[1] && w[2] == g.blk[2];
+  const int lane = tid & 31;
+  auto post = [&](int32_t delta, uint32_t j) -> uint16_t {
+    const uint16_t q = (delta > -r && delta < r) ? (uint16_t)(delta + r) : (uint16_t)0;
+    s_c[j] = q;
+    if (q == 0) s_k[j] = delta;
+    return q;
+  };
+  if (full && (ND != 1 || aligned)) {
+    if (ND == 1) {
+      // thread t: 16 consecutive elements (a warp covers two whole 256-chunks)
+      const float4* x4 = reinterpret_cast<const float4*>(x + org[2]) + 4 * tid;
+      int32_t k[16];
+      uint32_t pm = 0;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const float4 v = __ldcs(&x4[i]);
+        const float f[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          bool p;
+          err |= prequant(f[c], eb_f, ebx2_f, ebx2_r, k[4 * i + c], p);
+          pm |= (uint32_t)p << (4 * i + c);
+        }
+      }
+      const int32_t prev = __shfl_up_sync(~0u, k[15], 1);
+      uint32_t om = 0;
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const uint32_t j = 16 * tid + i;
+        const int32_t left = i ? k[i - 1] : prev;
+        const int32_t delta = (j & 255) ? k[i] - left : k[i];
+        om |= (uint32_t)(post(delta, j) == 0) << i;
+      }
+      const uint32_t om2 = __shfl_down_sync(~0u, om, 1), pm2 = __shfl_down_sync(~0u, pm, 1);
+      if ((lane & 1) == 0) {
+        s_outl[tid >> 1] = om | (om2 << 16);
+        s_patch[tid >> 1] = pm | (pm2 << 16);
+      }
+    } else if (ND == 2) {
+      // thread t: column xx = t & 63 of the 16-row chunk band t >> 6
+      const uint32_t xx = tid & 63, ry = tid >> 6;
+      const float* src = x + (uint64_t)(org[1] + 16 * ry) * nx + org[2] + xx;
+      int32_t k[16];
+      uint32_t pm = 0;
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        bool p;
+        err |= prequant(__ldcs(src + i * nx), eb_f, ebx2_f, ebx2_r, k[i], p);
+        pm |= (uint32_t)p << i;
+      }
+#pragma unroll
+      for (int i = 15; i > 0; i--) k[i] -= k[i - 1];  // y difference within the chunk band
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const int32_t left = __shfl_up_sync(~0u, k[i], 1);
+        const int32_t delta = (xx & 15) ? k[i] - left : k[i];  // x difference
+        const uint32_t j = (16 * ry + i) * 64 + xx;
+        const uint16_t q = post(delta, j);
+        const uint32_t ob = __ballot_sync(~0u, q == 0), pb = __ballot_sync(~0u, (pm >> i) & 1u);
+        if (lane == 0) {
+          s_outl[j >> 5] = ob;
+          s_patch[j >> 5] = pb;
+        }
+      }
+    } else {
+      // thread t: z column of (xx, yy) = (t & 15, t >> 4); z and x differences in
+      // registers and shuffles, the y difference through shared memory
+      const uint32_t xx = tid & 15, yy = tid >> 4;
+      const uint64_t zs = ny * nx;
+      const float* src = x + ((uint64_t)org[0] * ny + org[1] + yy) * nx + org[2] + xx;
+      int32_t k[16];
+      uint32_t pm = 0;
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        bool p;
+        err |= prequant(__ldcs(src + i * zs), eb_f, ebx2_f, ebx2_r, k[i], p);
+        pm |= (uint32_t)p << i;
+      }
+#pragma unroll
+      for (int i = 15; i > 0; i--)
+        if (i & 7) k[i] -= k[i - 1];  // z difference within 8-chunks
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const int32_t left = __shfl_up_sync(~0u, k[i], 1);
+        if (xx & 7) k[i] -= left;  // x difference
+        s_k[(i * 16 + yy) * 16 + xx] = k[i];
+      }
+      __syncthreads();
+      int32_t below[16];
+#pragma unroll
+      for (int i = 0; i < 16; i++) below[i] = (yy & 7) ? s_k[(i * 16 + yy - 1) * 16 + xx] : 0;
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const uint32_t j = (i * 16 + yy) * 16 + xx;
+        const uint16_t q = post(k[i] - below[i], j);
+        const uint32_t ob = __ballot_sync(~0u, q == 0), pb = __ballot_sync(~0u, (pm >> i) & 1u);
+        if (lane == 0) {
+          s_outl[j >> 5] = ob;
+          s_patch[j >> 5] = pb;
+        }
+      }
+    }
+    __syncthreads();
+  } else {
+  // ---- edge blocks: stage k in shared memory, residuals from the staged neighbours --
   auto put_k = [&](uint32_t j, float v) {
     int32_t k;
     bool p;
@@ -285,9 +397,7 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
   }
   __syncthreads();
 
-  // ---- Lorenzo residual (Sec. IV-B2 predictors, chunk-local) and postquant -------
   int32_t dl[kPer];
-  const bool full = w[0] == g.blk[0] && w[1] == g.blk[1] && w[2] == g.blk[2];
   auto residual = [&](uint32_t j, uint32_t zz, uint32_t yy, uint32_t xx, uint32_t sy, uint32_t sz) -> int32_t {
     const bool hx = (xx % Chunk<ND>::x) != 0;
     const bool hy = ND >= 2 && (yy % Chunk<ND>::y) != 0;
@@ -331,6 +441,7 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kPer; i++) s_k[tid + kConstructThreads * i] = dl[i];
+  }
 
   // ---- record count per thread (contiguous 16 slots) and tile aggregate ----------
   const uint32_t lo = tid * kPer;
@@ -357,10 +468,10 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
   }
 
   // ---- runs: heads, lengths, histograms (code hist = sum of run lengths) ---------
-  block_run_heads(s_c, m, s_head, s_woff, s_next);
-  {
-    // single-element runs (the common case on rough data) are counted in a register
-    // and added once, so the shared run-length bin for length 1 is not contended
+  const uint32_t nruns = block_run_heads(s_c, m, s_head, s_woff, s_next);
+  if (a.all_runs || 4 * nruns <= m) {
+    // run-eligible block: code histogram from the runs, plus run values and lengths;
+    // single-element runs are counted in a register and added once
     uint32_t ones = 0;
 #pragma unroll 4
     for (int i = 0; i < kPer; i++) {
@@ -378,6 +489,13 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
     }
     ones = warp_sum(ones);
     if ((tid & 31) == 0 && ones) add16(s_hl, 0, ones);
+  } else {
+    // runs too short to matter (see run eligibility): codes only
+#pragma unroll 4
+    for (int i = 0; i < kPer; i++) {
+      const uint32_t j = tid + kConstructThreads * i;
+      if (j < m) add16(s_hc, s_c[j], 1u);
+    }
   }
 
   // ---- place records: exclusive prefix over tiles, then ordered writes -----------
@@ -806,10 +924,14 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   }
   __syncthreads();
 
-  // runs (every mode except forced Huffman)
+  // runs: counted in every mode except forced Huffman; extracted (values, lengths)
+  // only when a run codec or the run statistics need them
   uint32_t nr = 0;
-  if (sel != SEL_HUFF) {
-    nr = block_run_heads(s_c, m, s_head, s_woff, s_next);
+  bool have_runs = false;
+  if (sel != SEL_HUFF) nr = block_run_heads(s_c, m, s_head, s_woff, s_next);
+  const bool eligible = a.all_runs || 4 * nr <= m;
+  auto extract_runs = [&]() {
+    if (have_runs) return;
 #pragma unroll 4
     for (int i = 0; i < kSlots / kEncThreads; i++) {
       const uint32_t j = tid + kEncThreads * i;
@@ -823,7 +945,9 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
       }
     }
     __syncthreads();
-  }
+    have_runs = true;
+  };
+  if (sel != SEL_HUFF && eligible && sel != SEL_RLE) extract_runs();
 
   // exact sizes: Huffman units from per-lane bit totals
   auto huff_units = [&]() {
@@ -864,13 +988,15 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   uint64_t size_h = ~0ull, size_r = ~0ull, size_rh = ~0ull;
   if (sel == SEL_HUFF || sel == SEL_EXHAUSTIVE) size_h = (2ull * huff_units() + 3) & ~3ull;
   if (sel == SEL_RLE || sel == SEL_EXHAUSTIVE) size_r = 4ull * nr;
-  if (sel == SEL_RLE_HUFF || sel == SEL_EXHAUSTIVE) {
+  if ((sel == SEL_RLE_HUFF || sel == SEL_EXHAUSTIVE) && eligible) {
     rlehuff_units();
     size_rh = (8ull + 2ull * (s_units[1] + s_units[2]) + 3) & ~3ull;
   }
 
   // selection
-  if (sel == SEL_HEURISTIC || sel == SEL_LEARNED) {
+  if ((sel == SEL_HEURISTIC || sel == SEL_LEARNED) && !eligible) {
+    if (tid == 0) s_codec = CODEC_HUFF;  // both pick between Huffman and RLE+Huffman
+  } else if (sel == SEL_HEURISTIC || sel == SEL_LEARNED) {
     uint32_t* s_hist = s_buf;  // 1024 words, before the payload is assembled
     for (int i = tid; i < kNsymCode; i += kEncThreads) s_hist[i] = 0;
     __syncthreads();
@@ -946,6 +1072,7 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   }
   __syncthreads();
   const int codec = (int)s_codec;
+  if (codec == CODEC_RLE || codec == CODEC_RLE_HUFF) extract_runs();
   if (codec == CODEC_HUFF && size_h == ~0ull) size_h = (2ull * huff_units() + 3) & ~3ull;
   if (codec == CODEC_RLE_HUFF && size_rh == ~0ull) {
     rlehuff_units();

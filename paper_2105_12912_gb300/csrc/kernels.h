@@ -22,6 +22,7 @@ struct ConstructArgs {
   uint32_t* hist_len;  // [4096]
   uint64_t* lb;        // look-back state [nblk], zeroed
   uint32_t spin_limit;
+  int all_runs;        // every block's runs feed the run books (forced run codecs)
 };
 
 struct BookArgs {
@@ -56,6 +57,7 @@ struct EncodeArgs {
   const uint64_t* bcodes;
   const float* mlp_w;
   float* feat_out;  // optional [nblk][8] features (LEARNED mode)
+  int all_runs;     // every block may use run codecs (forced RLE / RLE+Huffman)
   uint8_t* ar;
   uint64_t cap;
   uint64_t off_codec, off_bb, off_rec;
