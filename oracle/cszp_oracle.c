@@ -1028,6 +1028,51 @@ size_t orc_max_archive_bytes(int ndim, const uint64_t* dims) {
   return (size_t)(HDR + align8(g.nblk) + align8(4 * g.nblk) + 16 * g.nelem + payload + 6144);
 }
 
+/* smallest exact size; ties prefer HUFF, then RLE_HUFF, then RLE */
+static int exhaustive_pick(const uint64_t* s) {
+  int c = ORC_CODEC_HUFF;
+  if (s[ORC_CODEC_RLE_HUFF] < s[c]) c = ORC_CODEC_RLE_HUFF;
+  if (s[ORC_CODEC_RLE] < s[c]) c = ORC_CODEC_RLE;
+  return c;
+}
+
+/*
+ * Learned selection: the codec with the smallest predicted size (first index on
+ * ties); when the runner-up is predicted within ORC_MLP_MARGIN of it the network is
+ * not trusted and the exact sizes decide, as in exhaustive selection (the exhaustive
+ * choice is the selector's fallback).  All comparisons are plain FP32 compares, so a
+ * NaN prediction never triggers the fallback and never wins.
+ */
+int orc_learned_pick(const float* y, const uint64_t* s) {
+  int c = 0;
+  for (int k = 1; k < 3; k++)
+    if (y[k] < y[c]) c = k;
+  int r = -1;
+  for (int k = 0; k < 3; k++)
+    if (k != c && (r < 0 || y[k] < y[r])) r = k;
+  const float gap = y[r] - y[c];
+  if (gap < ORC_MLP_MARGIN) c = exhaustive_pick(s);
+  return c;
+}
+
+int orc_selector_targets(const uint64_t* sizes, int ndim, const uint64_t* dims, float* target,
+                         uint8_t* valid) {
+  geom_t g;
+  int st = make_geom(ndim, dims, &g);
+  if (st) return st;
+  for (uint64_t b = 0; b < g.nblk; b++) {
+    const uint64_t m = block_count(&g, b);
+    const int64_t lm = orc_log2_q16(m);
+    valid[b] = sizes[3 * b + ORC_CODEC_RLE_HUFF] != UINT64_MAX;
+    for (int c = 0; c < 3; c++) {
+      const uint64_t sz = sizes[3 * b + c];
+      target[3 * b + c] =
+          sz == UINT64_MAX ? 0.0f : (float)((int64_t)orc_log2_q16(8 * sz) - lm) * (1.0f / 65536.0f);
+    }
+  }
+  return ORC_OK;
+}
+
 int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, double eb,
                  uint32_t radius, int select, const float* mlp_w, uint8_t* out, size_t cap,
                  size_t* out_bytes) {
@@ -1082,10 +1127,7 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
     if (select <= ORC_SEL_RLE_HUFF) {
       c = select;
     } else if (select == ORC_SEL_EXHAUSTIVE) {
-      /* smallest size; ties prefer HUFF, then RLE_HUFF, then RLE */
-      c = ORC_CODEC_HUFF;
-      if (s[ORC_CODEC_RLE_HUFF] < s[c]) c = ORC_CODEC_RLE_HUFF;
-      if (s[ORC_CODEC_RLE] < s[c]) c = ORC_CODEC_RLE;
+      c = exhaustive_pick(s);
     } else if (!run_eligible(nruns[b], block_count(&g, b), 0)) {
       c = ORC_CODEC_HUFF; /* heuristic and learned choose between Huffman and RLE+Huffman */
     } else if (select == ORC_SEL_HEURISTIC) {
@@ -1097,9 +1139,7 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
       float f[8], y[3];
       features_of(codes + b * SLOTS, block_count(&g, b), radius, f);
       orc_mlp_forward(mlp_w, f, 1, y);
-      c = 0;
-      for (int k = 1; k < 3; k++)
-        if (y[k] < y[c]) c = k;
+      c = orc_learned_pick(y, s);
     }
     codec[b] = (uint8_t)c;
     ncodec[c]++;

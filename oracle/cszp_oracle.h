@@ -53,6 +53,9 @@ enum { ORC_CODEC_HUFF = 0, ORC_CODEC_RLE = 1, ORC_CODEC_RLE_HUFF = 2 };
 #define ORC_MLP_OUT 3
 #define ORC_MLP_PARAMS (ORC_MLP_H * ORC_MLP_IN + ORC_MLP_H + ORC_MLP_H * ORC_MLP_H + ORC_MLP_H + \
                         ORC_MLP_OUT * ORC_MLP_H + ORC_MLP_OUT)
+/* learned selection falls back to the exact sizes when the runner-up prediction is
+   within this many log2 units (about 2%) of the best */
+#define ORC_MLP_MARGIN 0.028569152f
 
 /* ---- whole-pipeline entry points ------------------------------------------------ */
 size_t orc_max_archive_bytes(int ndim, const uint64_t* dims);
@@ -100,6 +103,16 @@ int orc_block_sizes(const uint16_t* codes, int ndim, const uint64_t* dims, uint3
 /* per-block selector features [nblk][8] */
 int orc_block_features(const uint16_t* codes, int ndim, const uint64_t* dims, uint32_t radius,
                        float* feat);
+
+/* training rows of the learned selector from exact sizes [nblk][3]: target[b][c] is
+   log2 of codec c's bits per element in Q16 steps, ((log2q16(8 size) - log2q16(m)) /
+   65536, exact in FP32); valid[b] = 1 where the block is run-eligible, i.e. where
+   the learned selector decides (other blocks are Huffman-coded) */
+int orc_selector_targets(const uint64_t* sizes, int ndim, const uint64_t* dims, float* target,
+                         uint8_t* valid);
+
+/* the learned selector's pick from predictions y[3] and exact sizes s[3] */
+int orc_learned_pick(const float* y, const uint64_t* s);
 
 /* the paper's histogram heuristic for one block: returns the codec it picks */
 int orc_heuristic_pick(const uint32_t* block_hist, int nsym, uint32_t m);

@@ -64,6 +64,8 @@ def lib():
             "orc_mlp_forward": (None, [_f32p, _f32p, C.c_uint64, _f32p]),
             "orc_mlp_loss_grad_f64": (C.c_double, [_f32p, _f32p, _f32p, C.c_uint64, _f64p]),
             "orc_decode_codes": (C.c_int, [_u8p, C.c_size_t, _u16p, C.c_uint64]),
+            "orc_selector_targets": (C.c_int, [_u64p, C.c_int, _u64p, _f32p, _u8p]),
+            "orc_learned_pick": (C.c_int, [_f32p, _u64p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -238,6 +240,25 @@ def mlp_loss_grad(w, feat, target):
     g = np.zeros(MLP_PARAMS, dtype=np.float64)
     loss = lib().orc_mlp_loss_grad_f64(_p(w, _f32p), _p(f, _f32p), _p(t, _f32p), f.shape[0], _p(g, _f64p))
     return float(loss), g
+
+
+def selector_targets(sizes, dims):
+    """Training targets (log2 bits per element, Q16-exact) and the run-eligible mask."""
+    nblk, _ = geometry(dims)
+    sz = np.ascontiguousarray(sizes, dtype=np.uint64).reshape(nblk, 3)
+    tgt = np.zeros((nblk, 3), dtype=np.float32)
+    valid = np.zeros(nblk, dtype=np.uint8)
+    st = lib().orc_selector_targets(_p(sz, _u64p), len(dims), _p(_dims(dims), _u64p), _p(tgt, _f32p),
+                                    _p(valid, _u8p))
+    if st:
+        raise OracleError(st, "selector_targets")
+    return tgt, valid
+
+
+def learned_pick(y, sizes):
+    yy = np.ascontiguousarray(y, dtype=np.float32).reshape(3)
+    s = np.ascontiguousarray(sizes, dtype=np.uint64).reshape(3)
+    return int(lib().orc_learned_pick(_p(yy, _f32p), _p(s, _u64p)))
 
 
 def decode_codes(ar, dims):

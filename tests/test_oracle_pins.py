@@ -444,6 +444,77 @@ def test_mlp_forward_and_gradient(orc):
 
 
 # ---------------------------------------------------------------------------------
+# learned selection: argmin of the predictions, exact sizes when the two best are
+# within the margin; training targets are log2 bits per element
+# ---------------------------------------------------------------------------------
+def test_learned_pick_rule(orc):
+    s = np.array([900, 40, 60], np.uint64)  # exact: RLE smallest
+    assert orc.learned_pick([1.0, 5.0, 9.0], s) == orc.CODEC_HUFF       # clear-cut: trust the net
+    assert orc.learned_pick([5.0, 9.0, 1.0], s) == orc.CODEC_RLE_HUFF
+    assert orc.learned_pick([1.0, 1.01, 9.0], s) == orc.CODEC_RLE       # within 2%: exact sizes
+    assert orc.learned_pick([2.0, 2.0, 2.0], s) == orc.CODEC_RLE
+    assert orc.learned_pick([1.0, 1.0 + 0.03, 9.0], s) == orc.CODEC_HUFF  # just outside the margin
+    # exhaustive ties prefer HUFF, then RLE+Huffman, then RLE
+    assert orc.learned_pick([0.0, 0.0, 0.0], np.array([8, 8, 8], np.uint64)) == orc.CODEC_HUFF
+    assert orc.learned_pick([0.0, 0.0, 0.0], np.array([12, 8, 8], np.uint64)) == orc.CODEC_RLE_HUFF
+    # a NaN prediction neither wins nor triggers the fallback
+    assert orc.learned_pick([np.nan, 3.0, 4.0], s) == orc.CODEC_HUFF
+    assert orc.learned_pick([3.0, np.nan, 1.0], s) == orc.CODEC_RLE_HUFF
+
+
+def test_selector_targets_closed_form(orc):
+    dims = (3 * 4096 + 100,)
+    sizes = np.array([[512, 4, 12], [4096, 64, 2048], [999, 8, np.iinfo(np.uint64).max],
+                      [50, 4, 13]], np.uint64)
+    tgt, valid = orc.selector_targets(sizes, dims)
+    assert valid.tolist() == [1, 1, 0, 1]
+    # powers of two are exact: 512 B over 4096 elements = 1 bit each -> 0
+    assert tgt[0, 0] == 0.0 and tgt[1, 0] == 3.0 and tgt[0, 1] == np.float32(-7.0)
+    m = np.array([4096, 4096, 4096, 100], np.float64)
+    want = np.log2(8 * sizes.astype(np.float64)[[0, 1, 3]] / m[[0, 1, 3], None])
+    assert np.abs(tgt[[0, 1, 3]] - want).max() <= 2.0 / 65536
+    assert tgt[2, 2] == 0.0
+
+
+def test_learned_mode_reduces_to_other_selectors(orc):
+    """A network with zero weights predicts its output bias for every block: a bias
+    that strongly favours Huffman gives the forced-Huffman choice on every block, an
+    all-equal bias falls back to the exact sizes everywhere (the exhaustive choice).
+    Archives then match byte for byte except the header's selector field."""
+    rng = np.random.default_rng(21)
+    x = rng.standard_normal((40, 90, 70)).astype(np.float32).cumsum(axis=2).astype(np.float32)
+    x[:, :, :35] = 0.0
+    w = np.zeros(orc.MLP_PARAMS, np.float32)
+
+    def body(ar):
+        a = ar.copy()
+        a[112:116] = 0
+        return a
+    w[-3:] = [0.0, 10.0, 10.0]
+    _, a_l = orc.compress(x, orc.EB_REL, 1e-3, select=orc.SEL_LEARNED, mlp_w=w)
+    _, a_h = orc.compress(x, orc.EB_REL, 1e-3, select=orc.SEL_HUFF)
+    assert np.array_equal(body(a_l), body(a_h))
+    w[-3:] = [4.0, 4.0, 4.0]
+    _, a_l = orc.compress(x, orc.EB_REL, 1e-3, select=orc.SEL_LEARNED, mlp_w=w)
+    _, a_e = orc.compress(x, orc.EB_REL, 1e-3, select=orc.SEL_EXHAUSTIVE)
+    assert np.array_equal(body(a_l), body(a_e))
+    assert orc.parse_header(a_e)["n_codec"][1] > 0  # the zero half is run coded
+    # RLE favoured: every run-eligible block is RLE, the others Huffman
+    w[-3:] = [10.0, 0.0, 10.0]
+    _, a_r = orc.compress(x, orc.EB_REL, 1e-3, select=orc.SEL_LEARNED, mlp_w=w)
+    codec = orc.sections(a_r)["codec"]
+    st, ebd, ebf, x2, xr = orc.eb_params(orc.EB_REL, 1e-3, float(x.min()), float(x.max()))
+    c = orc.construct(x, ebf, x2, xr)
+    _, _, nr = orc.run_stats(c["codes"], x.shape, all_blocks=False)
+    nblk, _ = orc.geometry(x.shape)
+    bz, by, bx = np.meshgrid(np.arange(3), np.arange(6), np.arange(5), indexing="ij")
+    m = (np.minimum(16, 40 - 16 * bz) * np.minimum(16, 90 - 16 * by) * np.minimum(16, 70 - 16 * bx)).ravel()
+    assert m.size == nblk
+    elig = 4 * nr.astype(np.int64) <= m
+    assert np.array_equal(codec, np.where(elig, orc.CODEC_RLE, orc.CODEC_HUFF).astype(np.uint8))
+
+
+# ---------------------------------------------------------------------------------
 # interleaved Huffman stream layout, closed form: with a two-symbol book every code
 # is one bit, so each of the 32 lanes tops up one 16-bit unit at steps 0, 16, 32, ...
 # and the stream is lane 0..31's unit 0, then their unit 1, and so on
