@@ -129,6 +129,58 @@ csz_status csz_decompress(const uint8_t* d_archive, size_t bytes, float* d_out,
 csz_status csz_decompress_static(const uint8_t* d_archive, size_t bytes, float* d_out,
                                  uint64_t out_cap_elems, void* stream);
 
+/*
+ * Learned codec selector (an extension beside the paper's Sec. III-B heuristic; the
+ * paper has no learned selector).  The network maps 8 per-block statistics to the
+ * predicted log2 bits per element of HUFF, RLE and RLE_HUFF; CSZ_SEL_LEARNED codes
+ * each run-eligible block (at most one run per four codes) with the smallest
+ * prediction, falling back to the exact sizes when the two best predictions are
+ * within log2(1.02); other blocks are Huffman coded.  Parameters: CSZ_MLP_PARAMS
+ * FP32 values, W1[32][8] b1[32] W2[32][32] b2[32] W3[3][32] b3[3] (row = output unit).
+ *
+ * csz_selector_rows: the method's own training data for one field.  Runs the
+ * compression pipeline with exhaustive sizing but writes no archive; for every codec
+ * block b (block-major order, as in the archive) it writes
+ *   d_feat[b][8]    features: zero-residual fraction, code entropy (bits), top-code
+ *                   probability, |delta|<=1 fraction, runs per element, outlier
+ *                   fraction, mean |delta|/r, fraction of codes differing from the
+ *                   code 8 positions on (each a ratio of integers, one FP32 division)
+ *   d_target[b][3]  log2 of each codec's bits per element, in 1/65536 steps
+ *   d_sizes[b][3]   each codec's exact payload bytes (0xffffffff: not applicable)
+ *   d_valid[b]      1 where the learned selector decides the block
+ * Each output holds nblk rows.  Workspace, arguments and errors as for
+ * csz_compress (radius 0 = 512).  Synchronises.
+ */
+csz_status csz_selector_rows(const float* d_field, int ndim, const uint64_t* dims, int eb_mode,
+                             double eb, uint32_t radius, void* d_workspace, size_t workspace_bytes,
+                             float* d_feat, float* d_target, uint32_t* d_sizes, uint8_t* d_valid,
+                             void* stream);
+
+/* Network outputs d_out[nrows][3] for d_feat[nrows][8], computed exactly as the
+   encoder computes them (fused multiply-add chains from the bias, inputs in order).
+   Synchronises. */
+csz_status csz_selector_predict(const float* d_weights, const float* d_feat, uint64_t nrows,
+                                float* d_out, void* stream);
+
+/* Device workspace of csz_selector_grad / csz_selector_train for nrows rows. */
+size_t csz_selector_workspace_bytes(uint64_t nrows);
+
+/* Mean squared error over the rows with d_valid[r] != 0 (d_valid may be NULL: all
+   rows) and all 3 outputs, and its gradient d_grad[CSZ_MLP_PARAMS] (FP32, summed in
+   a fixed order: reproducible).  *h_loss (may be NULL) receives the loss.
+   Synchronises. */
+csz_status csz_selector_grad(const float* d_weights, const float* d_feat, const float* d_target,
+                             const uint8_t* d_valid, uint64_t nrows, float* d_grad, double* h_loss,
+                             void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) on d_weights in
+   place, learning rate decaying linearly from lr to lr/10.  *h_loss receives the
+   loss at the weights the last step started from.  Synchronises once, at the end. */
+csz_status csz_selector_train(float* d_weights, const float* d_feat, const float* d_target,
+                              const uint8_t* d_valid, uint64_t nrows, uint32_t steps, float lr,
+                              void* d_workspace, size_t workspace_bytes, double* h_loss,
+                              void* stream);
+
 /* Human-readable name of a status. */
 const char* csz_status_string(int status);
 

@@ -38,6 +38,15 @@ SIGNATURES = {
     "csz_decompress": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t,
                                  C.c_void_p]),
     "csz_decompress_static": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint64, C.c_void_p]),
+    "csz_selector_rows": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint64), C.c_int, C.c_double, C.c_uint32,
+                                    C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "csz_selector_workspace_bytes": (C.c_size_t, [C.c_uint64]),
+    "csz_selector_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "csz_selector_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
+                                    C.POINTER(C.c_double), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "csz_selector_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32,
+                                     C.c_float, C.c_void_p, C.c_size_t, C.POINTER(C.c_double), C.c_void_p]),
     "csz_status_string": (C.c_char_p, [C.c_int]),
     "csz_kernel_count": (C.c_int, []),
     "csz_kernel_name": (C.c_char_p, [C.c_int]),

@@ -142,6 +142,106 @@ def header(archive) -> dict:
                 n_patch=npatch, payload=payload, total=total, select=select, n_codec=(nh, nr, nrh))
 
 
+# ---------------------------------------------------------------------------------
+# learned selector: training rows, inference, gradient, training
+# ---------------------------------------------------------------------------------
+def _f32_cuda(t, name, shape=None):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def nblocks(dims) -> int:
+    d = [int(v) for v in dims]
+    if len(d) == 1:
+        return -(-d[0] // 4096)
+    if len(d) == 2:
+        return -(-d[0] // 64) * -(-d[1] // 64)
+    return -(-d[0] // 16) * -(-d[1] // 16) * -(-d[2] // 16)
+
+
+def selector_rows(field: torch.Tensor, eb: float, eb_mode: str = "rel", radius: int = 512, out=None,
+                  workspace: Workspace | None = None, stream=None):
+    """Training rows of the learned selector for every codec block of `field`:
+    dict(feat [nblk,8] f32, target [nblk,3] f32 (log2 bits/element), sizes [nblk,3] i32
+    (exact bytes, -1 where a codec does not apply), valid [nblk] u8).  `out` may hold
+    preallocated tensors of those shapes (views into larger buffers are fine)."""
+    if not (field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()):
+        raise ValueError("field must be a contiguous float32 CUDA tensor")
+    dims = tuple(field.shape)
+    nb = nblocks(dims)
+    dev = field.device
+    if out is None:
+        out = dict(feat=torch.empty((nb, 8), dtype=torch.float32, device=dev),
+                   target=torch.empty((nb, 3), dtype=torch.float32, device=dev),
+                   sizes=torch.empty((nb, 3), dtype=torch.int32, device=dev),
+                   valid=torch.empty(nb, dtype=torch.uint8, device=dev))
+    for k, shp in (("feat", (nb, 8)), ("target", (nb, 3)), ("sizes", (nb, 3)), ("valid", (nb,))):
+        t = out[k]
+        if not (t.is_cuda and t.is_contiguous() and tuple(t.shape) == shp):
+            raise ValueError(f"out[{k!r}] must be a contiguous CUDA tensor of shape {shp}")
+    ws = _ws(dev, workspace).get(workspace_bytes(dims) or 256)
+    st = L.lib().csz_selector_rows(C.c_void_p(field.data_ptr()), len(dims), L.dims_array(dims),
+                                   EB_MODES[eb_mode] if isinstance(eb_mode, str) else int(eb_mode), float(eb),
+                                   int(radius), C.c_void_p(ws.data_ptr()), ws.numel(),
+                                   C.c_void_p(out["feat"].data_ptr()), C.c_void_p(out["target"].data_ptr()),
+                                   C.c_void_p(out["sizes"].data_ptr()), C.c_void_p(out["valid"].data_ptr()),
+                                   _stream_ptr(stream))
+    _check(st, "csz_selector_rows")
+    return out
+
+
+def selector_predict(weights: torch.Tensor, feat: torch.Tensor, stream=None) -> torch.Tensor:
+    """Network outputs [n,3] for feature rows [n,8] (the encoder's own forward pass)."""
+    n = feat.shape[0]
+    out = torch.empty((n, 3), dtype=torch.float32, device=feat.device)
+    st = L.lib().csz_selector_predict(_f32_cuda(weights, "weights", (MLP_PARAMS,)), _f32_cuda(feat, "feat", (n, 8)),
+                                      n, C.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    _check(st, "csz_selector_predict")
+    return out
+
+
+def _valid_ptr(valid, n):
+    if valid is None:
+        return None
+    if not (valid.is_cuda and valid.dtype == torch.uint8 and valid.is_contiguous() and valid.numel() == n):
+        raise ValueError("valid must be a contiguous uint8 CUDA tensor with one entry per row")
+    return C.c_void_p(valid.data_ptr())
+
+
+def _train_ws(n, device):
+    return torch.empty(int(L.lib().csz_selector_workspace_bytes(n)), dtype=torch.uint8, device=device)
+
+
+def selector_grad(weights, feat, target, valid=None, stream=None):
+    """(mean squared error, its gradient [1443]) over the rows with valid != 0."""
+    n = feat.shape[0]
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=feat.device)
+    ws = _train_ws(n, feat.device)
+    loss = C.c_double(0.0)
+    st = L.lib().csz_selector_grad(_f32_cuda(weights, "weights", (MLP_PARAMS,)), _f32_cuda(feat, "feat", (n, 8)),
+                                   _f32_cuda(target, "target", (n, 3)), _valid_ptr(valid, n), n,
+                                   C.c_void_p(grad.data_ptr()), C.byref(loss), C.c_void_p(ws.data_ptr()),
+                                   ws.numel(), _stream_ptr(stream))
+    _check(st, "csz_selector_grad")
+    return float(loss.value), grad
+
+
+def selector_train(weights, feat, target, valid=None, steps: int = 2000, lr: float = 3e-3, stream=None):
+    """Full-batch Adam on `weights` in place; returns the loss at the last step."""
+    n = feat.shape[0]
+    ws = _train_ws(n, feat.device)
+    loss = C.c_double(0.0)
+    st = L.lib().csz_selector_train(_f32_cuda(weights, "weights", (MLP_PARAMS,)), _f32_cuda(feat, "feat", (n, 8)),
+                                    _f32_cuda(target, "target", (n, 3)), _valid_ptr(valid, n), n, int(steps),
+                                    float(lr), C.c_void_p(ws.data_ptr()), ws.numel(), C.byref(loss),
+                                    _stream_ptr(stream))
+    _check(st, "csz_selector_train")
+    return float(loss.value)
+
+
 def status_string(st: int) -> str:
     return L.lib().csz_status_string(int(st)).decode()
 

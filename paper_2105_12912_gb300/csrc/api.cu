@@ -195,7 +195,7 @@ extern "C" {
 
 static const char* const kKernelNames[K_COUNT] = {
     "range", "abs_params", "construct", "codebook", "encode", "dec_setup",
-    "stream_decode", "rle_expand", "reconstruct"};
+    "stream_decode", "rle_expand", "reconstruct", "mlp_predict", "mlp_grad", "mlp_update"};
 
 int csz_kernel_count(void) { return K_COUNT; }
 
@@ -247,14 +247,30 @@ size_t csz_workspace_bytes(int ndim, const uint64_t* dims) {
   return (size_t)layout(g).total;
 }
 
-csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
+}  // extern "C"
+
+namespace {
+
+// Outputs of the analysis pass (selector training rows) instead of an archive.
+struct Analysis {
+  float* feat;
+  float* target;
+  uint32_t* sizes;
+  uint8_t* valid;
+};
+
+// The compression pipeline on the caller's stream: value range or bound, Lorenzo
+// construction, books, per-block selection and encoding (or, with `an`, the analysis
+// of every block), then one synchronisation to read the device status and size.
+csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
                         const csz_options* opt, void* d_ws, size_t ws_bytes, uint8_t* d_ar, size_t cap,
-                        size_t* h_bytes, void* stream) {
+                        size_t* h_bytes, const Analysis* an, void* stream) {
   Geom g;
-  if (!d_field || !d_ar || !h_bytes || !d_ws) return CSZ_E_ARG;
+  if (!d_field || !d_ws) return CSZ_E_ARG;
+  if (!an && (!d_ar || !h_bytes)) return CSZ_E_ARG;
   if (!make_geom(ndim, dims, g)) return CSZ_E_ARG;
   const uint32_t radius = (opt && opt->radius) ? opt->radius : 512u;
-  const int select = opt ? (int)opt->select : SEL_EXHAUSTIVE;
+  const int select = an ? SEL_EXHAUSTIVE : (opt ? (int)opt->select : SEL_EXHAUSTIVE);
   if (radius > 512 || select < 0 || select > SEL_LEARNED) return CSZ_E_ARG;
   if (select == SEL_LEARNED && !(opt && opt->selector_weights)) return CSZ_E_ARG;
   if (opt)
@@ -265,7 +281,7 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   if (ws_bytes < L.total) return CSZ_E_CAPACITY;
   const uint64_t off_bb = kHdr + a8(g.nblk);
   const uint64_t off_rec = off_bb + a8(4ull * g.nblk);
-  if (cap < off_rec) return CSZ_E_CAPACITY;
+  if (!an && cap < off_rec) return CSZ_E_CAPACITY;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DevState* st = at<DevState>(d_ws, L.st);
 
@@ -280,14 +296,15 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   ca.st = st;
   ca.radius = radius;
   ca.codes = at<uint16_t>(d_ws, L.codes);
-  ca.rec = reinterpret_cast<uint32_t*>(d_ar + off_rec);
-  ca.rec_cap = (cap - off_rec) / 8;
+  ca.rec = an ? nullptr : reinterpret_cast<uint32_t*>(d_ar + off_rec);
+  ca.rec_cap = an ? 0 : (cap - off_rec) / 8;
   ca.hist_code = at<uint32_t>(d_ws, L.hist_code);
   ca.hist_val = at<uint32_t>(d_ws, L.hist_val);
   ca.hist_len = at<uint32_t>(d_ws, L.hist_len);
   ca.lb = at<uint64_t>(d_ws, L.lb_c);
   ca.spin_limit = g_spin_limit;
   ca.all_runs = (select == SEL_RLE || select == SEL_RLE_HUFF) ? 1 : 0;
+  ca.no_records = an ? 1 : 0;
   if (launch_construct(ndim, ca, s) != cudaSuccess) return CSZ_E_CUDA;
 
   BookArgs ba;
@@ -300,6 +317,7 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   if (launch_codebook(ba, s) != cudaSuccess) return CSZ_E_CUDA;
 
   EncodeArgs ea;
+  memset(&ea, 0, sizeof(ea));
   ea.g = g;
   ea.st = st;
   ea.radius = radius;
@@ -308,8 +326,14 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   ea.lens = ba.lens;
   ea.bcodes = ba.codes;
   ea.mlp_w = opt ? opt->selector_weights : nullptr;
-  ea.feat_out = nullptr;
   ea.all_runs = ca.all_runs;
+  if (an) {
+    ea.analyze = 1;
+    ea.feat_out = an->feat;
+    ea.tgt_out = an->target;
+    ea.size_out = an->sizes;
+    ea.valid_out = an->valid;
+  }
   ea.ar = d_ar;
   ea.cap = cap;
   ea.off_codec = kHdr;
@@ -339,8 +363,30 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
   trace_collect();
   const csz_status r = fold(hs.status);
   if (r != CSZ_OK) return r;
-  *h_bytes = (size_t)hs.total;
+  if (h_bytes) *h_bytes = an ? 0 : (size_t)hs.total;
   return CSZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
+                        const csz_options* opt, void* d_ws, size_t ws_bytes, uint8_t* d_ar, size_t cap,
+                        size_t* h_bytes, void* stream) {
+  return run_pipeline(d_field, ndim, dims, eb_mode, eb, opt, d_ws, ws_bytes, d_ar, cap, h_bytes, nullptr, stream);
+}
+
+csz_status csz_selector_rows(const float* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
+                             uint32_t radius, void* d_ws, size_t ws_bytes, float* d_feat, float* d_target,
+                             uint32_t* d_sizes, uint8_t* d_valid, void* stream) {
+  if (!d_feat || !d_target || !d_sizes || !d_valid) return CSZ_E_ARG;
+  csz_options opt;
+  memset(&opt, 0, sizeof(opt));
+  opt.radius = radius;
+  opt.select = CSZ_SEL_EXHAUSTIVE;
+  const Analysis an{d_feat, d_target, d_sizes, d_valid};
+  return run_pipeline(d_field, ndim, dims, eb_mode, eb, &opt, d_ws, ws_bytes, nullptr, 0, nullptr, &an, stream);
 }
 
 csz_status csz_archive_info(const uint8_t* h, size_t bytes, int* ndim, uint64_t* dims, double* eb_abs,

@@ -34,6 +34,17 @@ constexpr int kLutBits = 12;
 constexpr uint32_t kSpinLimit = 1u << 20;
 
 enum : int { CODEC_HUFF = 0, CODEC_RLE = 1, CODEC_RLE_HUFF = 2 };
+
+// learned selector: MLP 8 -> 32 -> 32 -> 3 with ReLU, parameters packed as
+// W1[32][8] b1[32] W2[32][32] b2[32] W3[3][32] b3[3]
+constexpr int kMlpIn = 8, kMlpHid = 32, kMlpOut = 3;
+constexpr int kMlpW1 = 0, kMlpB1 = kMlpW1 + kMlpHid * kMlpIn, kMlpW2 = kMlpB1 + kMlpHid,
+              kMlpB2 = kMlpW2 + kMlpHid * kMlpHid, kMlpW3 = kMlpB2 + kMlpHid,
+              kMlpB3 = kMlpW3 + kMlpOut * kMlpHid, kMlpParams = kMlpB3 + kMlpOut;
+static_assert(kMlpParams == 1443, "MLP parameter count");
+// the runner-up within this many log2 units (about 2%) of the best prediction sends
+// the block to exact sizes
+constexpr float kMlpMargin = 0.028569152f;
 enum : int { SEL_HUFF = 0, SEL_RLE = 1, SEL_RLE_HUFF = 2, SEL_HEURISTIC = 3, SEL_EXHAUSTIVE = 4, SEL_LEARNED = 5 };
 
 // device status bits, folded into a csz_status by the host
@@ -546,5 +557,30 @@ __device__ inline uint32_t ihs_encode_block(const uint16_t* sym, uint32_t N, int
 
 // Units lane `lane` of a stream needs: ceil(bits/16), given its bit total.
 __device__ __forceinline__ uint32_t ihs_lane_units(uint32_t bits) { return (bits + 15) / 16; }
+
+
+// One forward pass of the selector MLP by a full warp: lane i owns hidden unit i, and
+// every dot product is a chain of fused multiply-adds from the bias over the inputs
+// in order (so the FP32 result is reproducible by any implementation that chains the
+// same way).  f: the 8 features (same in every lane); y: the 3 outputs, in every lane.
+__device__ __forceinline__ void mlp_forward_warp(const float* __restrict__ w, const float* f, float* y) {
+  const int lane = threadIdx.x & 31;
+  float acc = __ldg(&w[kMlpB1 + lane]);
+#pragma unroll
+  for (int j = 0; j < kMlpIn; j++) acc = fmaf(__ldg(&w[kMlpW1 + lane * kMlpIn + j]), f[j], acc);
+  const float h1 = acc > 0.0f ? acc : 0.0f;
+  acc = __ldg(&w[kMlpB2 + lane]);
+#pragma unroll
+  for (int j = 0; j < kMlpHid; j++)
+    acc = fmaf(__ldg(&w[kMlpW2 + lane * kMlpHid + j]), __shfl_sync(~0u, h1, j), acc);
+  const float h2 = acc > 0.0f ? acc : 0.0f;
+  const int o = lane < kMlpOut ? lane : 0;
+  acc = __ldg(&w[kMlpB3 + o]);
+#pragma unroll
+  for (int j = 0; j < kMlpHid; j++)
+    acc = fmaf(__ldg(&w[kMlpW3 + o * kMlpHid + j]), __shfl_sync(~0u, h2, j), acc);
+#pragma unroll
+  for (int c = 0; c < kMlpOut; c++) y[c] = __shfl_sync(~0u, acc, c);
+}
 
 }  // namespace cszp

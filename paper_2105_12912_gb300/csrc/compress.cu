@@ -499,6 +499,14 @@ __global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructA
   }
 
   // ---- place records: exclusive prefix over tiles, then ordered writes -----------
+  if (a.no_records) {
+    __syncthreads();
+    flush16(s_hc, kNsymCode / 2, a.hist_code);
+    flush16(s_hv, kNsymCode / 2, a.hist_val);
+    flush16(s_hl, kNsymLen / 2, a.hist_len);
+    if (err) atomicOr(&a.st->status, err);
+    return;
+  }
   if (tid < 32) {
     uint64_t pre = lookback_warp(a.lb, b, tile_total, &a.st->status, a.spin_limit);
     if (tid == 0) s_prefix = pre;
@@ -844,34 +852,31 @@ __device__ void finalize_body(const FinalizeArgs& a) {
 constexpr int kEncThreads = 256;
 constexpr int kBufBytes = 16384;  // payload assembly buffer
 
-__device__ int mlp_pick_warp(const float* __restrict__ w, const float* f) {
-  const int lane = threadIdx.x & 31;
-  const float* W1 = w;
-  const float* b1 = W1 + 32 * 8;
-  const float* W2 = b1 + 32;
-  const float* b2 = W2 + 32 * 32;
-  const float* W3 = b2 + 32;
-  const float* b3 = W3 + 3 * 32;
-  float acc = __ldg(&b1[lane]);
-#pragma unroll
-  for (int j = 0; j < 8; j++) acc = fmaf(__ldg(&W1[lane * 8 + j]), f[j], acc);
-  const float h1 = acc > 0.0f ? acc : 0.0f;
-  acc = __ldg(&b2[lane]);
-#pragma unroll
-  for (int j = 0; j < 32; j++) acc = fmaf(__ldg(&W2[lane * 32 + j]), __shfl_sync(~0u, h1, j), acc);
-  const float h2 = acc > 0.0f ? acc : 0.0f;
-  const int o = lane < 3 ? lane : 0;
-  acc = __ldg(&b3[o]);
-#pragma unroll
-  for (int j = 0; j < 32; j++) acc = fmaf(__ldg(&W3[o * 32 + j]), __shfl_sync(~0u, h2, j), acc);
-  const float y0 = __shfl_sync(~0u, acc, 0), y1 = __shfl_sync(~0u, acc, 1), y2 = __shfl_sync(~0u, acc, 2);
+// Learned pick from the network's three predictions (identical in every lane): the
+// smallest (first index on ties), and whether the runner-up lies within the margin,
+// in which case the caller decides by exact sizes.  Plain FP32 compares only.
+__device__ __forceinline__ int learned_pick(const float* y, bool& fallback) {
   int c = 0;
-  float best = y0;
-  if (y1 < best) {
-    c = 1;
-    best = y1;
+  if (y[1] < y[c]) c = 1;
+  if (y[2] < y[c]) c = 2;
+  int r = -1;
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+    if (k != c && (r < 0 || y[k] < y[r])) r = k;
+  const float gap = y[r] - y[c];
+  fallback = gap < kMlpMargin;
+  return c;
+}
+
+// smallest exact size; ties prefer HUFF, then RLE_HUFF, then RLE
+__device__ __forceinline__ int exhaustive_pick(uint64_t sh, uint64_t sr, uint64_t srh) {
+  int c = CODEC_HUFF;
+  uint64_t best = sh;
+  if (srh < best) {
+    c = CODEC_RLE_HUFF;
+    best = srh;
   }
-  if (y2 < best) c = 2;
+  if (sr < best) c = CODEC_RLE;
   return c;
 }
 
@@ -924,11 +929,13 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   }
   __syncthreads();
 
-  // runs: counted in every mode except forced Huffman; extracted (values, lengths)
-  // only when a run codec or the run statistics need them
+  // Analysis (selector training data): every size and every feature of every block,
+  // no payload.  Otherwise runs are counted in every mode except forced Huffman and
+  // extracted (values, lengths) only when a run codec or the statistics need them.
+  const bool analyze = a.analyze != 0;
   uint32_t nr = 0;
   bool have_runs = false;
-  if (sel != SEL_HUFF) nr = block_run_heads(s_c, m, s_head, s_woff, s_next);
+  if (sel != SEL_HUFF || analyze) nr = block_run_heads(s_c, m, s_head, s_woff, s_next);
   const bool eligible = a.all_runs || 4 * nr <= m;
   auto extract_runs = [&]() {
     if (have_runs) return;
@@ -947,7 +954,7 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
     __syncthreads();
     have_runs = true;
   };
-  if (sel != SEL_HUFF && eligible && sel != SEL_RLE) extract_runs();
+  if (analyze || (sel != SEL_HUFF && eligible && sel != SEL_RLE)) extract_runs();
 
   // exact sizes: Huffman units from per-lane bit totals
   auto huff_units = [&]() {
@@ -986,17 +993,22 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
     __syncthreads();
   };
   uint64_t size_h = ~0ull, size_r = ~0ull, size_rh = ~0ull;
-  if (sel == SEL_HUFF || sel == SEL_EXHAUSTIVE) size_h = (2ull * huff_units() + 3) & ~3ull;
-  if (sel == SEL_RLE || sel == SEL_EXHAUSTIVE) size_r = 4ull * nr;
-  if ((sel == SEL_RLE_HUFF || sel == SEL_EXHAUSTIVE) && eligible) {
-    rlehuff_units();
-    size_rh = (8ull + 2ull * (s_units[1] + s_units[2]) + 3) & ~3ull;
-  }
+  auto exact_sizes = [&](bool h, bool rl, bool rh) {
+    if (h && size_h == ~0ull) size_h = (2ull * huff_units() + 3) & ~3ull;
+    if (rl) size_r = 4ull * nr;
+    if (rh && eligible && size_rh == ~0ull) {
+      rlehuff_units();
+      size_rh = (8ull + 2ull * (s_units[1] + s_units[2]) + 3) & ~3ull;
+    }
+  };
+  exact_sizes(analyze || sel == SEL_HUFF || sel == SEL_EXHAUSTIVE, analyze || sel == SEL_RLE || sel == SEL_EXHAUSTIVE,
+              analyze || sel == SEL_RLE_HUFF || sel == SEL_EXHAUSTIVE);
 
   // selection
-  if ((sel == SEL_HEURISTIC || sel == SEL_LEARNED) && !eligible) {
+  const bool statistics = analyze || ((sel == SEL_HEURISTIC || sel == SEL_LEARNED) && eligible);
+  if ((sel == SEL_HEURISTIC || sel == SEL_LEARNED) && !eligible && !analyze) {
     if (tid == 0) s_codec = CODEC_HUFF;  // both pick between Huffman and RLE+Huffman
-  } else if (sel == SEL_HEURISTIC || sel == SEL_LEARNED) {
+  } else if (statistics) {
     uint32_t* s_hist = s_buf;  // 1024 words, before the payload is assembled
     for (int i = tid; i < kNsymCode; i += kEncThreads) s_hist[i] = 0;
     __syncthreads();
@@ -1017,7 +1029,7 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
     f1 = block_max_u32(f1, s_scan);
     const int64_t Lm = log2_q16(m);
     const int64_t NH = (int64_t)m * Lm - (int64_t)S_;
-    if (sel == SEL_HEURISTIC) {
+    if (sel == SEL_HEURISTIC && !analyze) {
       if (tid == 0) {
         int64_t Rm = 0;
         if (10ll * f1 > 4ll * m) {
@@ -1049,35 +1061,46 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
         s_feat[7] = (float)var8 / fm;
       }
       __syncthreads();
-      if (tid < 32) {
-        const int c = mlp_pick_warp(a.mlp_w, s_feat);
-        if (tid == 0) s_codec = (uint32_t)c;
+      if (analyze) {
+        // one training row: features, log2 bits per element of each codec (Q16-exact),
+        // exact sizes, and whether the learned selector decides this block
+        if (tid < kMlpIn) a.feat_out[(uint64_t)b * kMlpIn + tid] = s_feat[tid];
+        if (tid < kMlpOut) {
+          const uint64_t sz = tid == CODEC_HUFF ? size_h : (tid == CODEC_RLE ? size_r : size_rh);
+          const bool have = sz != ~0ull;
+          a.size_out[(uint64_t)b * kMlpOut + tid] = have ? (uint32_t)sz : 0xffffffffu;
+          a.tgt_out[(uint64_t)b * kMlpOut + tid] =
+              have ? (float)((int64_t)log2_q16(8 * sz) - (int64_t)log2_q16(m)) * (1.0f / 65536.0f) : 0.0f;
+          if (tid == 0) a.valid_out[b] = eligible ? 1 : 0;
+        }
+        return;
       }
-      if (a.feat_out && tid < 8) a.feat_out[(uint64_t)b * 8 + tid] = s_feat[tid];
+      __shared__ bool s_fallback;
+      if (tid < 32) {
+        float y[kMlpOut];
+        mlp_forward_warp(a.mlp_w, s_feat, y);
+        bool fb;
+        const int c = learned_pick(y, fb);
+        if (tid == 0) {
+          s_codec = (uint32_t)c;
+          s_fallback = fb;
+        }
+      }
+      __syncthreads();
+      if (s_fallback) {
+        // the network is unsure: exact sizes decide
+        exact_sizes(true, true, true);
+        if (tid == 0) s_codec = (uint32_t)exhaustive_pick(size_h, size_r, size_rh);
+      }
     }
     __syncthreads();
   } else if (tid == 0) {
-    if (sel <= SEL_RLE_HUFF) {
-      s_codec = (uint32_t)sel;
-    } else {
-      int c = CODEC_HUFF;
-      uint64_t best = size_h;
-      if (size_rh < best) {
-        c = CODEC_RLE_HUFF;
-        best = size_rh;
-      }
-      if (size_r < best) c = CODEC_RLE;
-      s_codec = (uint32_t)c;
-    }
+    s_codec = sel <= SEL_RLE_HUFF ? (uint32_t)sel : (uint32_t)exhaustive_pick(size_h, size_r, size_rh);
   }
   __syncthreads();
   const int codec = (int)s_codec;
   if (codec == CODEC_RLE || codec == CODEC_RLE_HUFF) extract_runs();
-  if (codec == CODEC_HUFF && size_h == ~0ull) size_h = (2ull * huff_units() + 3) & ~3ull;
-  if (codec == CODEC_RLE_HUFF && size_rh == ~0ull) {
-    rlehuff_units();
-    size_rh = (8ull + 2ull * (s_units[1] + s_units[2]) + 3) & ~3ull;
-  }
+  exact_sizes(codec == CODEC_HUFF, codec == CODEC_RLE, codec == CODEC_RLE_HUFF);
   const uint64_t size = codec == CODEC_HUFF ? size_h : (codec == CODEC_RLE ? 4ull * nr : size_rh);
   if (tid == 0) {
     lookback_publish(a.lb, b, size);

@@ -23,6 +23,7 @@ struct ConstructArgs {
   uint64_t* lb;        // look-back state [nblk], zeroed
   uint32_t spin_limit;
   int all_runs;        // every block's runs feed the run books (forced run codecs)
+  int no_records;      // analysis only: codes and histograms, no outlier/patch records
 };
 
 struct BookArgs {
@@ -56,8 +57,14 @@ struct EncodeArgs {
   const uint8_t* lens;
   const uint64_t* bcodes;
   const float* mlp_w;
-  float* feat_out;  // optional [nblk][8] features (LEARNED mode)
   int all_runs;     // every block may use run codecs (forced RLE / RLE+Huffman)
+  // analysis mode (selector training rows, no archive): per block the 8 features, the
+  // 3 log2-size targets, the 3 exact sizes and whether the learned selector decides it
+  int analyze;
+  float* feat_out;      // [nblk][8]
+  float* tgt_out;       // [nblk][3]
+  uint32_t* size_out;   // [nblk][3], 0xffffffff where a codec does not apply
+  uint8_t* valid_out;   // [nblk]
   uint8_t* ar;
   uint64_t cap;
   uint64_t off_codec, off_bb, off_rec;
@@ -108,6 +115,9 @@ enum KernelId : int {
   K_STREAM_DECODE,
   K_RLE_EXPAND,
   K_RECONSTRUCT,
+  K_MLP_PREDICT,
+  K_MLP_GRAD,
+  K_MLP_UPDATE,
   K_COUNT
 };
 void trace_begin(int id, cudaStream_t s);
