@@ -41,10 +41,14 @@ bool make_geom(int ndim, const uint64_t* dims, Geom& g) {
 }
 
 // Workspace: [DevState | histograms | look-back states] (zeroed per compression),
-// books, decode tables and offsets, block-major code stream.
+// books, decode tables and offsets, block-major code stream, decoded run lengths
+// (the part decompression needs ends at dec_total), then compression-only scratch:
+// per-block record counts, patch / outlier bit masks, outlier residuals and record
+// offsets.
 struct Layout {
-  uint64_t st, hist_code, hist_val, hist_len, lb_c, lb_e, zero_end;
-  uint64_t lens, bcodes, feat, blk_off, rec_start, tabs, codes, runl, total;
+  uint64_t st, hist_code, hist_val, hist_len, lb_e, zero_end;
+  uint64_t lens, bcodes, blk_off, rec_start, tabs, codes, runl, dec_total;
+  uint64_t counts, masks, deltas, rec_off, total;
 };
 
 Layout layout(const Geom& g) {
@@ -58,8 +62,6 @@ Layout layout(const Geom& g) {
   o += kNsymCode * 4;
   L.hist_len = o;
   o += kNsymLen * 4;
-  L.lb_c = o;
-  o += 8ull * g.nblk;
   L.lb_e = o;
   o += 8ull * g.nblk;
   L.zero_end = o;
@@ -68,8 +70,6 @@ Layout layout(const Geom& g) {
   o += a256(2 * kNsymCode + kNsymLen);
   L.bcodes = o;
   o += 8ull * (2 * kNsymCode + kNsymLen);
-  L.feat = o;
-  o += a256(32ull * g.nblk);
   L.blk_off = o;
   o += a256(8ull * (g.nblk + 1));
   L.rec_start = o;
@@ -80,6 +80,15 @@ Layout layout(const Geom& g) {
   o += a256(2ull * kSlots * g.nblk);
   L.runl = o;
   o += a256(2ull * kSlots * g.nblk);
+  L.dec_total = o;
+  L.counts = o;
+  o += a256(4ull * g.nblk);
+  L.masks = o;
+  o += a256(1024ull * g.nblk);
+  L.deltas = o;
+  o += a256(4ull * kSlots * g.nblk);
+  L.rec_off = o;
+  o += a256(8ull * g.nblk);
   L.total = o;
   return L;
 }
@@ -290,30 +299,49 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
                                         : launch_abs_params(st, eb, s);
   if (e != cudaSuccess) return CSZ_E_CUDA;
 
-  ConstructArgs ca;
+  ConstructTask task;
+  memset(&task, 0, sizeof(task));
+  ConstructArgs& ca = task.a;
   ca.x = d_field;
   ca.g = g;
   ca.st = st;
   ca.radius = radius;
   ca.codes = at<uint16_t>(d_ws, L.codes);
-  ca.rec = an ? nullptr : reinterpret_cast<uint32_t*>(d_ar + off_rec);
-  ca.rec_cap = an ? 0 : (cap - off_rec) / 8;
   ca.hist_code = at<uint32_t>(d_ws, L.hist_code);
   ca.hist_val = at<uint32_t>(d_ws, L.hist_val);
   ca.hist_len = at<uint32_t>(d_ws, L.hist_len);
-  ca.lb = at<uint64_t>(d_ws, L.lb_c);
+  ca.counts = at<uint32_t>(d_ws, L.counts);
+  ca.masks = at<uint32_t>(d_ws, L.masks);
+  ca.deltas = at<int32_t>(d_ws, L.deltas);
   ca.spin_limit = g_spin_limit;
   ca.all_runs = (select == SEL_RLE || select == SEL_RLE_HUFF) ? 1 : 0;
-  ca.no_records = an ? 1 : 0;
-  if (launch_construct(ndim, ca, s) != cudaSuccess) return CSZ_E_CUDA;
+  prepare_construct_task(task);
+  if (launch_construct(task, &st->ticket_construct, s) != cudaSuccess) return CSZ_E_CUDA;
 
   BookArgs ba;
+  memset(&ba, 0, sizeof(ba));
   ba.hist_code = ca.hist_code;
   ba.hist_val = ca.hist_val;
   ba.hist_len = ca.hist_len;
   ba.lens = at<uint8_t>(d_ws, L.lens);
   ba.codes = at<uint64_t>(d_ws, L.bcodes);
   ba.st = st;
+  RecordArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  if (!an) {
+    // a fourth CTA beside the book builders scans the record counts; the encode
+    // CTAs then write each block's records
+    ra.x = d_field;
+    ra.counts = ca.counts;
+    ra.masks = ca.masks;
+    ra.deltas = ca.deltas;
+    ra.rec_off = at<uint64_t>(d_ws, L.rec_off);
+    ra.rec = reinterpret_cast<uint32_t*>(d_ar + off_rec);
+    ra.rec_cap = (cap - off_rec) / 8;
+    ba.place_records = 1;
+    ba.nblk = g.nblk;
+    ba.rec = ra;
+  }
   if (launch_codebook(ba, s) != cudaSuccess) return CSZ_E_CUDA;
 
   EncodeArgs ea;
@@ -341,6 +369,8 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
   ea.off_rec = off_rec;
   ea.lb = at<uint64_t>(d_ws, L.lb_e);
   ea.spin_limit = g_spin_limit;
+  ea.place_records = an ? 0 : 1;
+  ea.rec = ra;
   FinalizeArgs& fa = ea.fin;
   fa.st = st;
   fa.ar = d_ar;
@@ -418,7 +448,7 @@ csz_status csz_decompress(const uint8_t* d_ar, size_t bytes, float* d_out, uint6
   if (r != CSZ_OK) return r;
   if (out_cap < g.nelem) return CSZ_E_CAPACITY;
   const Layout L = layout(g);
-  if (ws_bytes < L.total) return CSZ_E_CAPACITY;
+  if (ws_bytes < L.dec_total) return CSZ_E_CAPACITY;
   DevState* st = at<DevState>(d_ws, L.st);
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return CSZ_E_CUDA;
   DecodeArgs da;

@@ -249,9 +249,10 @@ __device__ __forceinline__ uint32_t prequant(float x, float eb_f, float ebx2_f, 
                                              int32_t& k, bool& patch) {
   patch = false;
   k = 0;
-  if (!isfinite(x)) return ERR_NONFINITE;
-  float v = __fmul_rn(x, ebx2_r);
-  if (!(fabsf(v) < 8388608.0f)) return ERR_RANGE;
+  const float v = __fmul_rn(x, ebx2_r);
+  // one compare covers both failures: ebx2_r is finite and positive, so |v| < 2^23
+  // holds only for finite x
+  if (!(fabsf(v) < 8388608.0f)) return isfinite(x) ? ERR_RANGE : ERR_NONFINITE;
   int32_t k0 = __float2int_rn(v);
   float x0 = __fmul_rn(__int2float_rn(k0), ebx2_f);
   if (!exceeds_exact(x, x0, eb_f)) {
@@ -365,52 +366,72 @@ __device__ inline void canonical_build(const uint8_t* len, int nsym, CanonSmem* 
 // head[w] bit b: position 32w+b starts a run; woff[w]: runs before word w;
 // nexthead[w]: first run start at or after word w's first position (m if none).
 // ---------------------------------------------------------------------------------
-__device__ inline uint32_t block_run_heads(const uint16_t* c, uint32_t m, uint32_t* head, uint32_t* woff,
-                                           uint32_t* nexthead) {
+// Run heads of the block's codes c[0..m) as bit words head[j >> 5] (bit j & 31 set
+// where a run starts).  Returns, in lane 0 of each warp, the number of heads in the
+// words that warp wrote (0 elsewhere).  Reads c only; no barrier.
+__device__ inline uint32_t run_head_words(const uint16_t* c, uint32_t m, uint32_t* head) {
   const int tid = threadIdx.x, lane = tid & 31;
+  uint32_t n = 0;
+#pragma unroll 4
   for (int i = 0; i < kSlots / 256; i++) {
     const uint32_t j = tid + 256 * i;
     const bool h = j < m && (j == 0 || c[j] != c[j - 1]);
     const uint32_t hb = __ballot_sync(~0u, h);
-    if (lane == 0) head[j >> 5] = hb;
+    if (lane == 0) {
+      head[j >> 5] = hb;
+      n += __popc(hb);
+    }
   }
+  return n;
+}
+
+// Index of the run heads (warp 0, after the head words are complete): woff[w] = runs
+// starting before word w (woff[kSlots/32] = total), nexthead[w] = first head at or
+// after word w (m if none).
+__device__ inline void run_head_index(const uint32_t* head, uint32_t m, uint32_t* woff, uint32_t* nexthead) {
+  const int lane = threadIdx.x & 31;
+  // lane covers words 4*lane .. 4*lane+3
+  uint32_t cnt[4], first[4];
+  uint32_t tot = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint32_t w = 4 * lane + k, hm = head[w];
+    cnt[k] = __popc(hm);
+    first[k] = hm ? w * 32 + (__ffs(hm) - 1) : 0xffffffffu;
+    tot += cnt[k];
+  }
+  const uint32_t incl = warp_incl_scan(tot);
+  uint32_t run = incl - tot;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    woff[4 * lane + k] = run;
+    run += cnt[k];
+  }
+  // suffix minimum of first-head positions
+  uint32_t lf = min(min(first[0], first[1]), min(first[2], first[3]));
+  uint32_t suf = lf;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_down_sync(~0u, suf, o);
+    if (lane + o < 32) suf = min(suf, v);
+  }
+  uint32_t after = __shfl_down_sync(~0u, suf, 1);
+  if (lane == 31) after = 0xffffffffu;
+  uint32_t cur = after;
+#pragma unroll
+  for (int k = 3; k >= 0; k--) {
+    cur = min(cur, first[k]);
+    nexthead[4 * lane + k] = cur == 0xffffffffu ? m : cur;
+  }
+  if (lane == 31) woff[kSlots / 32] = incl;
+}
+
+// Both of the above for a whole CTA of 256 threads; returns the number of runs.
+__device__ inline uint32_t block_run_heads(const uint16_t* c, uint32_t m, uint32_t* head, uint32_t* woff,
+                                           uint32_t* nexthead) {
+  run_head_words(c, m, head);
   __syncthreads();
-  if (tid < 32) {
-    // lane covers words 4*lane .. 4*lane+3
-    uint32_t cnt[4], first[4];
-    uint32_t tot = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const uint32_t w = 4 * lane + k, hm = head[w];
-      cnt[k] = __popc(hm);
-      first[k] = hm ? w * 32 + (__ffs(hm) - 1) : 0xffffffffu;
-      tot += cnt[k];
-    }
-    const uint32_t incl = warp_incl_scan(tot);
-    uint32_t run = incl - tot;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      woff[4 * lane + k] = run;
-      run += cnt[k];
-    }
-    // suffix minimum of first-head positions
-    uint32_t lf = min(min(first[0], first[1]), min(first[2], first[3]));
-    uint32_t suf = lf;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_down_sync(~0u, suf, o);
-      if (lane + o < 32) suf = min(suf, v);
-    }
-    uint32_t after = __shfl_down_sync(~0u, suf, 1);
-    if (lane == 31) after = 0xffffffffu;
-    uint32_t cur = after;
-#pragma unroll
-    for (int k = 3; k >= 0; k--) {
-      cur = min(cur, first[k]);
-      nexthead[4 * lane + k] = cur == 0xffffffffu ? m : cur;
-    }
-    if (lane == 31) woff[kSlots / 32] = incl;
-  }
+  if (threadIdx.x < 32) run_head_index(head, m, woff, nexthead);
   __syncthreads();
   return woff[kSlots / 32];
 }

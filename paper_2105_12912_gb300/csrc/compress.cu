@@ -2,10 +2,8 @@
 //
 // Pipeline (one stream, no host round trip until the end):
 //   range_kernel / abs_params_kernel  value range (REL) and the FP32 error bound
-//   construct_kernel<ND>              prequant + chunk-local Lorenzo + postquant
-//                                     (Alg. 1 l.1-8), outlier/patch records placed by
-//                                     decoupled look-back, code / run-value /
-//                                     run-length histograms
+//   construct_kernel (construct.cu)   prequant + chunk-local Lorenzo + postquant,
+//                                     records, histograms
 //   codebook_kernel                   three canonical Huffman books
 //   encode_kernel                     per block: exact sizes or heuristic / MLP pick,
 //                                     payload placement by decoupled look-back, payload
@@ -121,431 +119,6 @@ __global__ __launch_bounds__(256) void range_kernel(const float* __restrict__ x,
   }
 }
 
-// =================================================================================
-// Lorenzo construction
-// =================================================================================
-
-template <int ND>
-struct Chunk;
-template <>
-struct Chunk<1> {
-  static constexpr uint32_t z = 1, y = 1, x = 256;
-};
-template <>
-struct Chunk<2> {
-  static constexpr uint32_t z = 1, y = 16, x = 16;
-};
-template <>
-struct Chunk<3> {
-  static constexpr uint32_t z = 8, y = 8, x = 8;
-};
-
-constexpr int kConstructThreads = 256;
-constexpr int kPer = kSlots / kConstructThreads;  // 16 elements per thread
-
-// packed 16-bit counter pairs in a u32 word (per-CTA counts stay below 65536)
-__device__ __forceinline__ void add16(uint32_t* words, uint32_t bin, uint32_t v) {
-  atomicAdd(&words[bin >> 1], v << ((bin & 1u) * 16u));
-}
-
-__device__ __forceinline__ void flush16(const uint32_t* words, int nwords, uint32_t* global) {
-  for (int i = threadIdx.x; i < nwords; i += blockDim.x) {
-    uint32_t v = words[i];
-    if (v & 0xffffu) atomicAdd(&global[2 * i], v & 0xffffu);
-    if (v >> 16) atomicAdd(&global[2 * i + 1], v >> 16);
-  }
-}
-
-// coordinates of dense in-block index j
-template <int ND>
-__device__ __forceinline__ void dense_coords(uint32_t j, uint32_t wy, uint32_t wx, uint32_t& zz,
-                                             uint32_t& yy, uint32_t& xx) {
-  if (ND == 1) {
-    zz = 0;
-    yy = 0;
-    xx = j;
-  } else if (ND == 2) {
-    zz = 0;
-    yy = j / wx;
-    xx = j - yy * wx;
-  } else {
-    uint32_t p = wy * wx;
-    zz = j / p;
-    uint32_t r = j - zz * p;
-    yy = r / wx;
-    xx = r - yy * wx;
-  }
-}
-
-template <int ND>
-__global__ __launch_bounds__(kConstructThreads) void construct_kernel(ConstructArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  int32_t* s_k = reinterpret_cast<int32_t*>(smem);             // 4096: k, then delta
-  uint16_t* s_c = reinterpret_cast<uint16_t*>(s_k + kSlots);  // 4096 codes
-  uint32_t* s_hc = reinterpret_cast<uint32_t*>(s_c + kSlots);  // 512 words: code hist
-  uint32_t* s_hv = s_hc + kNsymCode / 2;                       // 512 words: run values
-  uint32_t* s_hl = s_hv + kNsymCode / 2;                       // 2048 words: run lengths
-  uint32_t* s_patch = s_hl + kNsymLen / 2;                     // 128 words
-  uint32_t* s_outl = s_patch + kSlots / 32;                    // 128 words
-  uint32_t* s_head = s_outl + kSlots / 32;                     // 128 words
-  uint32_t* s_woff = s_head + kSlots / 32;                     // 129 (+3) words
-  uint32_t* s_next = s_woff + kSlots / 32 + 4;                 // 128 words
-  uint64_t* s_scan = reinterpret_cast<uint64_t*>(s_next + kSlots / 32);  // 33
-  __shared__ uint32_t s_tile;
-  __shared__ uint64_t s_prefix;
-
-  const int tid = threadIdx.x;
-  if (tid == 0) s_tile = atomicAdd(&a.st->ticket_construct, 1u);
-  for (int i = tid; i < (kNsymCode + kNsymCode + kNsymLen) / 2 + 3 * (kSlots / 32); i += blockDim.x)
-    s_hc[i] = 0;
-  __syncthreads();
-  const uint32_t b = s_tile;
-  const Geom& g = a.g;
-  uint32_t org[3], w[3];
-  block_box(g, b, org, w);
-  const uint32_t m = w[0] * w[1] * w[2];
-  const float eb_f = a.st->eb_f, ebx2_f = a.st->ebx2_f, ebx2_r = a.st->ebx2_r;
-  const int32_t r = (int32_t)a.radius;
-  uint32_t err = 0;
-
-  // ---- load, prequantize, Lorenzo residual (Sec. IV-B2), postquantize -------------
-  // The residual is the mixed difference (1 - S_x)(1 - S_y)(1 - S_z) k, each shift
-  // reading zero outside the chunk; that expansion is the paper's 1/2/3-D predictor.
-  // Full blocks take it in registers and shuffles; edge blocks stage k in shared
-  // memory.  Outlier deltas are kept in s_k at their positions; outlier and patch
-  // positions are bit masks.
-  const float* __restrict__ x = a.x;
-  const uint64_t ny = g.n[1], nx = g.n[2];
-  const bool aligned = ((((uintptr_t)x) & 15) == 0) && (nx % 4 == 0);
-  const bool full = w[0] == g.blk[0] && w[1] == g.blk[1] && w[2] == g.blk[2];
-  const int lane = tid & 31;
-  auto post = [&](int32_t delta, uint32_t j) -> uint16_t {
-    const uint16_t q = (delta > -r && delta < r) ? (uint16_t)(delta + r) : (uint16_t)0;
-    s_c[j] = q;
-    if (q == 0) s_k[j] = delta;
-    return q;
-  };
-  if (full && (ND != 1 || aligned)) {
-    if (ND == 1) {
-      // thread t: 16 consecutive elements (a warp covers two whole 256-chunks)
-      const float4* x4 = reinterpret_cast<const float4*>(x + org[2]) + 4 * tid;
-      int32_t k[16];
-      uint32_t pm = 0;
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const float4 v = __ldcs(&x4[i]);
-        const float f[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-          bool p;
-          err |= prequant(f[c], eb_f, ebx2_f, ebx2_r, k[4 * i + c], p);
-          pm |= (uint32_t)p << (4 * i + c);
-        }
-      }
-      const int32_t prev = __shfl_up_sync(~0u, k[15], 1);
-      uint32_t om = 0;
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const uint32_t j = 16 * tid + i;
-        const int32_t left = i ? k[i - 1] : prev;
-        const int32_t delta = (j & 255) ? k[i] - left : k[i];
-        om |= (uint32_t)(post(delta, j) == 0) << i;
-      }
-      const uint32_t om2 = __shfl_down_sync(~0u, om, 1), pm2 = __shfl_down_sync(~0u, pm, 1);
-      if ((lane & 1) == 0) {
-        s_outl[tid >> 1] = om | (om2 << 16);
-        s_patch[tid >> 1] = pm | (pm2 << 16);
-      }
-    } else if (ND == 2) {
-      // thread t: column xx = t & 63 of the 16-row chunk band t >> 6
-      const uint32_t xx = tid & 63, ry = tid >> 6;
-      const float* src = x + (uint64_t)(org[1] + 16 * ry) * nx + org[2] + xx;
-      int32_t k[16];
-      uint32_t pm = 0;
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        bool p;
-        err |= prequant(__ldcs(src + i * nx), eb_f, ebx2_f, ebx2_r, k[i], p);
-        pm |= (uint32_t)p << i;
-      }
-#pragma unroll
-      for (int i = 15; i > 0; i--) k[i] -= k[i - 1];  // y difference within the chunk band
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const int32_t left = __shfl_up_sync(~0u, k[i], 1);
-        const int32_t delta = (xx & 15) ? k[i] - left : k[i];  // x difference
-        const uint32_t j = (16 * ry + i) * 64 + xx;
-        const uint16_t q = post(delta, j);
-        const uint32_t ob = __ballot_sync(~0u, q == 0), pb = __ballot_sync(~0u, (pm >> i) & 1u);
-        if (lane == 0) {
-          s_outl[j >> 5] = ob;
-          s_patch[j >> 5] = pb;
-        }
-      }
-    } else {
-      // thread t: z column of (xx, yy) = (t & 15, t >> 4); z and x differences in
-      // registers and shuffles, the y difference through shared memory
-      const uint32_t xx = tid & 15, yy = tid >> 4;
-      const uint64_t zs = ny * nx;
-      const float* src = x + ((uint64_t)org[0] * ny + org[1] + yy) * nx + org[2] + xx;
-      int32_t k[16];
-      uint32_t pm = 0;
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        bool p;
-        err |= prequant(__ldcs(src + i * zs), eb_f, ebx2_f, ebx2_r, k[i], p);
-        pm |= (uint32_t)p << i;
-      }
-#pragma unroll
-      for (int i = 15; i > 0; i--)
-        if (i & 7) k[i] -= k[i - 1];  // z difference within 8-chunks
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const int32_t left = __shfl_up_sync(~0u, k[i], 1);
-        if (xx & 7) k[i] -= left;  // x difference
-        s_k[(i * 16 + yy) * 16 + xx] = k[i];
-      }
-      __syncthreads();
-      int32_t below[16];
-#pragma unroll
-      for (int i = 0; i < 16; i++) below[i] = (yy & 7) ? s_k[(i * 16 + yy - 1) * 16 + xx] : 0;
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const uint32_t j = (i * 16 + yy) * 16 + xx;
-        const uint16_t q = post(k[i] - below[i], j);
-        const uint32_t ob = __ballot_sync(~0u, q == 0), pb = __ballot_sync(~0u, (pm >> i) & 1u);
-        if (lane == 0) {
-          s_outl[j >> 5] = ob;
-          s_patch[j >> 5] = pb;
-        }
-      }
-    }
-    __syncthreads();
-  } else {
-  // ---- edge blocks: stage k in shared memory, residuals from the staged neighbours --
-  auto put_k = [&](uint32_t j, float v) {
-    int32_t k;
-    bool p;
-    err |= prequant(v, eb_f, ebx2_f, ebx2_r, k, p);
-    s_k[j] = k;
-    if (p) atomicOr(&s_patch[j >> 5], 1u << (j & 31));
-  };
-  if (ND == 1) {
-    const uint64_t base = org[2];
-    if (m == (uint32_t)kSlots && aligned) {
-      const float4* x4 = reinterpret_cast<const float4*>(x + base);
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        uint32_t f = tid + kConstructThreads * i;
-        float4 v = __ldcs(&x4[f]);
-        put_k(4 * f + 0, v.x);
-        put_k(4 * f + 1, v.y);
-        put_k(4 * f + 2, v.z);
-        put_k(4 * f + 3, v.w);
-      }
-    } else {
-      for (uint32_t j = tid; j < m; j += kConstructThreads) put_k(j, x[base + j]);
-    }
-  } else if (ND == 2) {
-    const uint64_t base = (uint64_t)org[1] * nx + org[2];
-    if (w[2] == 64 && aligned) {
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        uint32_t f = tid + kConstructThreads * i;
-        uint32_t yy = f >> 4, c4 = f & 15;
-        if (yy < w[1]) {
-          float4 v = __ldcs(reinterpret_cast<const float4*>(x + base + yy * nx + 4 * c4));
-          uint32_t j = yy * 64 + 4 * c4;
-          put_k(j + 0, v.x);
-          put_k(j + 1, v.y);
-          put_k(j + 2, v.z);
-          put_k(j + 3, v.w);
-        }
-      }
-    } else {
-      for (uint32_t j = tid; j < m; j += kConstructThreads) {
-        uint32_t yy = j / w[2], xx = j - yy * w[2];
-        put_k(j, x[base + yy * nx + xx]);
-      }
-    }
-  } else {
-    const uint64_t base = ((uint64_t)org[0] * ny + org[1]) * nx + org[2];
-    if (w[2] == 16 && aligned) {
-      const uint32_t rows = w[0] * w[1];
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        uint32_t f = tid + kConstructThreads * i;
-        uint32_t row = f >> 2, c4 = f & 3;
-        if (row < rows) {
-          uint32_t zz = row / w[1], yy = row - zz * w[1];
-          float4 v = __ldcs(reinterpret_cast<const float4*>(x + base + (zz * ny + yy) * nx + 4 * c4));
-          uint32_t j = row * 16 + 4 * c4;
-          put_k(j + 0, v.x);
-          put_k(j + 1, v.y);
-          put_k(j + 2, v.z);
-          put_k(j + 3, v.w);
-        }
-      }
-    } else {
-      for (uint32_t j = tid; j < m; j += kConstructThreads) {
-        uint32_t zz, yy, xx;
-        dense_coords<3>(j, w[1], w[2], zz, yy, xx);
-        put_k(j, x[base + (zz * ny + yy) * nx + xx]);
-      }
-    }
-  }
-  __syncthreads();
-
-  int32_t dl[kPer];
-  auto residual = [&](uint32_t j, uint32_t zz, uint32_t yy, uint32_t xx, uint32_t sy, uint32_t sz) -> int32_t {
-    const bool hx = (xx % Chunk<ND>::x) != 0;
-    const bool hy = ND >= 2 && (yy % Chunk<ND>::y) != 0;
-    const bool hz = ND >= 3 && (zz % Chunk<ND>::z) != 0;
-    int32_t p;
-    if (ND == 1) {
-      p = hx ? s_k[j - 1] : 0;
-    } else if (ND == 2) {
-      p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) - ((hx && hy) ? s_k[j - sy - 1] : 0);
-    } else {
-      p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) + (hz ? s_k[j - sz] : 0) -
-          ((hx && hy) ? s_k[j - sy - 1] : 0) - ((hx && hz) ? s_k[j - sz - 1] : 0) -
-          ((hy && hz) ? s_k[j - sz - sy] : 0) + ((hx && hy && hz) ? s_k[j - sz - sy - 1] : 0);
-    }
-    return s_k[j] - p;
-  };
-#pragma unroll
-  for (int i = 0; i < kPer; i++) {
-    const uint32_t j = tid + kConstructThreads * i;
-    int32_t delta = 0;
-    uint16_t q = 0;
-    const bool in = j < m;
-    if (in) {
-      if (full) {
-        // interior block: strides are the block extents (powers of two)
-        if (ND == 1) delta = residual(j, 0, 0, j, 0, 0);
-        else if (ND == 2) delta = residual(j, 0, j >> 6, j & 63, 64, 0);
-        else delta = residual(j, j >> 8, (j >> 4) & 15, j & 15, 16, 256);
-      } else {
-        uint32_t zz, yy, xx;
-        dense_coords<ND>(j, w[1], w[2], zz, yy, xx);
-        delta = residual(j, zz, yy, xx, w[2], w[1] * w[2]);
-      }
-      q = (delta > -r && delta < r) ? (uint16_t)(delta + r) : (uint16_t)0;
-    }
-    dl[i] = delta;
-    s_c[j] = q;  // zero beyond m
-    const uint32_t ob = __ballot_sync(~0u, in && q == 0);
-    if ((tid & 31) == 0) s_outl[j >> 5] = ob;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < kPer; i++) s_k[tid + kConstructThreads * i] = dl[i];
-  }
-
-  // ---- record count per thread (contiguous 16 slots) and tile aggregate ----------
-  const uint32_t lo = tid * kPer;
-  const uint32_t ob = (s_outl[lo >> 5] >> (lo & 31)) & 0xffffu;
-  const uint32_t pb = (s_patch[lo >> 5] >> (lo & 31)) & 0xffffu;
-  uint64_t tile_total;
-  const uint64_t my_off = block_excl_scan<uint64_t>((uint64_t)(__popc(ob) + __popc(pb)), s_scan, &tile_total);
-  if (tid == 0) {
-    lookback_publish(a.lb, b, tile_total);
-    if (tile_total) {
-      atomicAdd(&a.st->n_rec, (unsigned long long)tile_total);
-      uint32_t np = 0;
-      for (int i = 0; i < kSlots / 32; i++) np += __popc(s_patch[i]);
-      if (np) atomicAdd(&a.st->n_patch, (unsigned long long)np);
-    }
-  }
-
-  // ---- codes to the block-major stream (whole 4096-slot block, zero tail) --------
-  __syncthreads();
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(s_c);
-    uint4* dst = reinterpret_cast<uint4*>(a.codes + (uint64_t)b * kSlots);
-    for (int i = tid; i < kSlots / 8; i += kConstructThreads) __stcg(&dst[i], src[i]);
-  }
-
-  // ---- runs: heads, lengths, histograms (code hist = sum of run lengths) ---------
-  const uint32_t nruns = block_run_heads(s_c, m, s_head, s_woff, s_next);
-  if (a.all_runs || 4 * nruns <= m) {
-    // run-eligible block: code histogram from the runs, plus run values and lengths;
-    // single-element runs are counted in a register and added once
-    uint32_t ones = 0;
-#pragma unroll 4
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t j = tid + kConstructThreads * i;
-      if (j < m && ((s_head[j >> 5] >> (j & 31)) & 1u)) {
-        const uint32_t v = s_c[j];
-        const uint32_t len = next_head(s_head, s_next, j, m) - j;
-        add16(s_hc, v, len);
-        add16(s_hv, v, 1u);
-        if (len == 1)
-          ones++;
-        else
-          add16(s_hl, len - 1, 1u);
-      }
-    }
-    ones = warp_sum(ones);
-    if ((tid & 31) == 0 && ones) add16(s_hl, 0, ones);
-  } else {
-    // runs too short to matter (see run eligibility): codes only
-#pragma unroll 4
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t j = tid + kConstructThreads * i;
-      if (j < m) add16(s_hc, s_c[j], 1u);
-    }
-  }
-
-  // ---- place records: exclusive prefix over tiles, then ordered writes -----------
-  if (a.no_records) {
-    __syncthreads();
-    flush16(s_hc, kNsymCode / 2, a.hist_code);
-    flush16(s_hv, kNsymCode / 2, a.hist_val);
-    flush16(s_hl, kNsymLen / 2, a.hist_len);
-    if (err) atomicOr(&a.st->status, err);
-    return;
-  }
-  if (tid < 32) {
-    uint64_t pre = lookback_warp(a.lb, b, tile_total, &a.st->status, a.spin_limit);
-    if (tid == 0) s_prefix = pre;
-  }
-  __syncthreads();
-  if (ob | pb) {
-    uint64_t pos = s_prefix + my_off;
-    uint32_t zz, yy, xx;
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t j = lo + i;
-      const uint32_t slot2 = (b * (uint32_t)kSlots + j) * 2u;
-      if ((ob >> i) & 1u) {
-        if (pos < a.rec_cap)
-          reinterpret_cast<uint2*>(a.rec)[pos] = make_uint2(slot2, (uint32_t)s_k[j]);
-        else
-          err |= ERR_CAPACITY;
-        pos++;
-      }
-      if ((pb >> i) & 1u) {
-        dense_coords<ND>(j, w[1], w[2], zz, yy, xx);
-        const uint64_t e = ((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + (org[2] + xx);
-        if (pos < a.rec_cap)
-          reinterpret_cast<uint2*>(a.rec)[pos] = make_uint2(slot2 + 1u, __float_as_uint(x[e]));
-        else
-          err |= ERR_CAPACITY;
-        pos++;
-      }
-    }
-  }
-  if (err) atomicOr(&a.st->status, err);
-  flush16(s_hc, kNsymCode / 2, a.hist_code);
-  flush16(s_hv, kNsymCode / 2, a.hist_val);
-  flush16(s_hl, kNsymLen / 2, a.hist_len);
-}
-
-static size_t construct_smem_bytes() {
-  return kSlots * 4 + kSlots * 2 + (kNsymCode + kNsymCode + kNsymLen) / 2 * 4 + 5 * (kSlots / 32) * 4 + 16 +
-         33 * 8 + 16;
-}
 
 // =================================================================================
 // canonical Huffman books (two-queue construction, Sec. II-A Step-6 via cuSZ)
@@ -590,8 +163,42 @@ __device__ void rank_merge_sort_u64(uint64_t* a, uint64_t* b, int L) {
 // Shared memory (bytes): len 4K | sym 8K | weight by node 32K | parent by node 16K |
 // region A 32K (sort keys, live node list, canonical scratch) | region B 32K (sort
 // scratch, new nodes, depth pass).
+// =================================================================================
+// record offsets: exclusive prefix of the blocks' record counts (one CTA)
+// =================================================================================
+__device__ void record_offsets_body(const BookArgs& a) {
+  __shared__ uint64_t s_scan[33];
+  constexpr int kPerThread = 8;
+  const int tid = threadIdx.x;
+  const uint32_t nblk = a.nblk;
+  uint64_t carry = 0;
+  for (uint32_t base = 0; base < nblk; base += kBookThreads * kPerThread) {
+    const uint32_t b0 = base + tid * kPerThread;
+    uint32_t c[kPerThread];
+    uint64_t mine = 0;
+#pragma unroll
+    for (int i = 0; i < kPerThread; i++) {
+      const uint32_t v = b0 + i < nblk ? a.rec.counts[b0 + i] : 0u;
+      c[i] = (v >> 16) + (v & 0xffffu);
+      mine += c[i];
+    }
+    uint64_t agg;
+    uint64_t off = carry + block_excl_scan<uint64_t>(mine, s_scan, &agg);
+#pragma unroll
+    for (int i = 0; i < kPerThread; i++) {
+      if (b0 + i < nblk) a.rec.rec_off[b0 + i] = off;
+      off += c[i];
+    }
+    carry += agg;
+  }
+}
+
 __global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (blockIdx.x == 3) {
+    record_offsets_body(a);
+    return;
+  }
   const int book = blockIdx.x;
   const int nsym = book == 2 ? kNsymLen : kNsymCode;
   const uint32_t* hist = book == 0 ? a.hist_code : (book == 1 ? a.hist_val : a.hist_len);
@@ -927,6 +534,48 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
     uint4* dst = reinterpret_cast<uint4*>(s_c);
     for (int i = tid; i < kSlots / 8; i += kEncThreads) dst[i] = __ldcs(&src[i]);
   }
+
+  // this block's outlier and patch records, in slot order, at its record offset
+  if (a.place_records && a.rec.counts[b] != 0) {
+    const RecordArgs& R = a.rec;
+    const uint32_t lo = tid * 16;
+    const uint32_t* mw = R.masks + (uint64_t)b * 256;
+    const uint32_t pb = (mw[lo >> 5] >> (lo & 31)) & 0xffffu;
+    const uint32_t ob = (mw[128 + (lo >> 5)] >> (lo & 31)) & 0xffffu;
+    uint64_t pos = R.rec_off[b] + block_excl_scan<uint64_t>((uint64_t)(__popc(ob) + __popc(pb)), s_scan64, nullptr);
+    if (ob | pb) {
+      const int32_t* dl = R.deltas + (uint64_t)b * kSlots;
+      const uint64_t ny = a.g.n[1], nx = a.g.n[2];
+      uint32_t err = 0;
+      for (int i = 0; i < 16; i++) {
+        const uint32_t j = lo + i;
+        const uint32_t slot2 = (b * (uint32_t)kSlots + j) * 2u;
+        if ((ob >> i) & 1u) {
+          if (pos < R.rec_cap) reinterpret_cast<uint2*>(R.rec)[pos] = make_uint2(slot2, (uint32_t)dl[j]);
+          else err |= ERR_CAPACITY;
+          pos++;
+        }
+        if ((pb >> i) & 1u) {
+          uint32_t zz = 0, yy = 0, xx = j;
+          if (a.g.ndim == 2) {
+            yy = j / w[2];
+            xx = j - yy * w[2];
+          } else if (a.g.ndim == 3) {
+            const uint32_t pl = w[1] * w[2];
+            zz = j / pl;
+            const uint32_t rr = j - zz * pl;
+            yy = rr / w[2];
+            xx = rr - yy * w[2];
+          }
+          const uint64_t e = ((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + (org[2] + xx);
+          if (pos < R.rec_cap) reinterpret_cast<uint2*>(R.rec)[pos] = make_uint2(slot2 + 1u, __float_as_uint(R.x[e]));
+          else err |= ERR_CAPACITY;
+          pos++;
+        }
+      }
+      if (err) atomicOr(&a.st->status, err);
+    }
+  }
   __syncthreads();
 
   // Analysis (selector training data): every size and every feature of every block,
@@ -1200,26 +849,13 @@ cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_construct(int ndim, const ConstructArgs& a, cudaStream_t s) {
-  const size_t sm = construct_smem_bytes();
-  trace_begin(K_CONSTRUCT, s);
-  if (ndim == 1) {
-    construct_kernel<1><<<a.g.nblk, kConstructThreads, sm, s>>>(a);
-  } else if (ndim == 2) {
-    construct_kernel<2><<<a.g.nblk, kConstructThreads, sm, s>>>(a);
-  } else {
-    construct_kernel<3><<<a.g.nblk, kConstructThreads, sm, s>>>(a);
-  }
-  trace_end(K_CONSTRUCT, s);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_codebook(const BookArgs& a, cudaStream_t s) {
   const size_t sm = codebook_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  const int grid = a.place_records ? 4 : 3;
   trace_begin(K_CODEBOOK, s);
-  codebook_kernel<<<3, kBookThreads, sm, s>>>(a);
+  codebook_kernel<<<grid, kBookThreads, sm, s>>>(a);
   trace_end(K_CODEBOOK, s);
   return cudaGetLastError();
 }

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -15,15 +16,36 @@ struct ConstructArgs {
   DevState* st;
   uint32_t radius;
   uint16_t* codes;     // nblk * 4096, block-major
-  uint32_t* rec;       // archive record section (u32 key, u32 val pairs)
-  uint64_t rec_cap;    // records that fit before the archive capacity ends
   uint32_t* hist_code; // [1024]
   uint32_t* hist_val;  // [1024]
   uint32_t* hist_len;  // [4096]
-  uint64_t* lb;        // look-back state [nblk], zeroed
+  uint32_t* counts;    // [nblk] (outliers << 16) | patches of each block
+  uint32_t* masks;     // [nblk][256] patch bit words [128], then outlier bit words [128]
+  int32_t* deltas;     // [nblk * 4096] outlier residuals by slot (written at outliers only)
   uint32_t spin_limit;
   int all_runs;        // every block's runs feed the run books (forced run codecs)
-  int no_records;      // analysis only: codes and histograms, no outlier/patch records
+};
+
+// Record placement: the exclusive prefix of the blocks' record counts (one CTA of
+// the codebook launch), then each encode CTA writes its block's outlier and patch
+// records in slot order at that offset.
+struct RecordArgs {
+  const float* x;
+  const uint32_t* counts;  // [nblk] (outliers << 16) | patches
+  const uint32_t* masks;   // [nblk][256] patch words, then outlier words
+  const int32_t* deltas;   // [nblk * 4096] outlier residuals by slot
+  uint64_t* rec_off;       // [nblk] exclusive prefix of record counts
+  uint32_t* rec;           // archive record section (u32 key, u32 val pairs)
+  uint64_t rec_cap;        // records that fit before the archive capacity ends
+};
+
+// One field of a construction launch: its arguments and, when TMA can describe
+// the field, the tensor map the kernel fetches tiles with (the struct is 128-byte
+// aligned, as CUtensorMap requires).
+struct ConstructTask {
+  CUtensorMap tmap;
+  ConstructArgs a;
+  int use_tma;
 };
 
 struct BookArgs {
@@ -33,6 +55,9 @@ struct BookArgs {
   uint8_t* lens;    // 1024 + 1024 + 4096
   uint64_t* codes;  // 1024 + 1024 + 4096
   DevState* st;
+  int place_records;  // a fourth CTA scans the record counts into rec.rec_off
+  uint32_t nblk;
+  RecordArgs rec;
 };
 
 struct FinalizeArgs {
@@ -70,6 +95,8 @@ struct EncodeArgs {
   uint64_t off_codec, off_bb, off_rec;
   uint64_t* lb;
   uint32_t spin_limit;
+  int place_records;  // write each block's records (compression, not analysis)
+  RecordArgs rec;
   FinalizeArgs fin;  // used by the last block to finish
 };
 
@@ -126,7 +153,12 @@ void trace_end(int id, cudaStream_t s);
 // ---- launchers (return cudaGetLastError of the launch) ---------------------------
 cudaError_t launch_abs_params(DevState* st, double eb, cudaStream_t s);
 cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, double eb, cudaStream_t s);
-cudaError_t launch_construct(int ndim, const ConstructArgs& a, cudaStream_t s);
+void prepare_construct_task(ConstructTask& t);  // tensor map when TMA applies
+size_t construct_smem_bytes();
+cudaError_t launch_construct(const ConstructTask& one, uint32_t* ticket, cudaStream_t s);
+cudaError_t launch_construct_batch(const ConstructTask* d_tasks, const uint32_t* d_tile0, int nfields,
+                                   uint32_t ntiles, uint32_t* ticket, uint32_t spin_limit, int grid,
+                                   cudaStream_t s);
 cudaError_t launch_codebook(const BookArgs& a, cudaStream_t s);
 cudaError_t launch_encode(const EncodeArgs& a, cudaStream_t s);
 
