@@ -130,6 +130,51 @@ csz_status csz_decompress_static(const uint8_t* d_archive, size_t bytes, float* 
                                  uint64_t out_cap_elems, void* stream);
 
 /*
+ * Batched compression.  Many fields of any shape and dimensionality are compressed
+ * by one launch per stage (value range, construction, books and record offsets,
+ * encoding), each kernel walking a per-field table; the construction and encoding
+ * kernels take the codec blocks of all fields from one ticket.  csz_batch_create
+ * validates the fields, lays out the workspace, uploads the tables, optionally
+ * autotunes the construction kernel's persistent grid on the batch (running it a
+ * few times), and captures the launch sequence into a CUDA graph.  Each
+ * csz_batch_compress replays the graph on `stream` without synchronising; the
+ * archives then hold exactly what csz_compress would write for each field with the
+ * same options.  csz_batch_results synchronises and reads every field's archive
+ * size and status.
+ * The field pointers, archive buffers and workspace are baked into the graph: they
+ * must stay valid, and keep their addresses, until csz_batch_destroy.  One batch
+ * must not be replayed on two streams at once.  Options (radius, selector, MLP
+ * weights) apply to every field.  The handle is host memory owned by the library.
+ */
+typedef struct {
+  const float* d_field; /* device FP32 field, row-major, dims slowest-first */
+  int ndim;
+  uint64_t dims[3];
+  int eb_mode;          /* csz_eb_mode */
+  double eb;
+  uint8_t* d_archive;   /* device archive buffer of archive_cap bytes */
+  size_t archive_cap;
+} csz_field;
+
+typedef struct csz_batch csz_batch;
+
+/* Workspace for a batch (0 if any field is invalid). */
+size_t csz_batch_workspace_bytes(int nfields, const csz_field* fields);
+csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_options* opt,
+                            void* d_workspace, size_t workspace_bytes, int autotune,
+                            void* stream, csz_batch** batch);
+csz_status csz_batch_compress(csz_batch* batch, void* stream);
+/* h_bytes[nfields] / h_status[nfields] (either may be NULL); returns the first
+   failing field's status, or CSZ_OK. */
+csz_status csz_batch_results(csz_batch* batch, uint64_t* h_bytes, int* h_status, void* stream);
+/* The construction grid the autotuner chose and the batch times (ms) it measured
+   with 1..4 resident CTAs per SM (0 where not tried). */
+csz_status csz_batch_info(const csz_batch* batch, int* construct_grid, double* tuned_ms);
+/* Where the last failing csz_batch_create call stopped and the CUDA error it met. */
+const char* csz_batch_last_error(void);
+void csz_batch_destroy(csz_batch* batch);
+
+/*
  * Learned codec selector (an extension beside the paper's Sec. III-B heuristic; the
  * paper has no learned selector).  The network maps 8 per-block statistics to the
  * predicted log2 bits per element of HUFF, RLE and RLE_HUFF; CSZ_SEL_LEARNED codes

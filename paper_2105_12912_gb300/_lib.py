@@ -17,6 +17,11 @@ class csz_options(C.Structure):
                 ("reserved", C.c_uint32 * 4)]
 
 
+class csz_field(C.Structure):
+    _fields_ = [("d_field", C.c_void_p), ("ndim", C.c_int), ("dims", C.c_uint64 * 3), ("eb_mode", C.c_int),
+                ("eb", C.c_double), ("d_archive", C.c_void_p), ("archive_cap", C.c_size_t)]
+
+
 class CszError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
@@ -47,6 +52,14 @@ SIGNATURES = {
                                     C.POINTER(C.c_double), C.c_void_p, C.c_size_t, C.c_void_p]),
     "csz_selector_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32,
                                      C.c_float, C.c_void_p, C.c_size_t, C.POINTER(C.c_double), C.c_void_p]),
+    "csz_batch_workspace_bytes": (C.c_size_t, [C.c_int, C.POINTER(csz_field)]),
+    "csz_batch_create": (C.c_int, [C.c_int, C.POINTER(csz_field), C.POINTER(csz_options), C.c_void_p, C.c_size_t,
+                                   C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "csz_batch_compress": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "csz_batch_results": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int), C.c_void_p]),
+    "csz_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "csz_batch_destroy": (None, [C.c_void_p]),
+    "csz_batch_last_error": (C.c_char_p, []),
     "csz_status_string": (C.c_char_p, [C.c_int]),
     "csz_kernel_count": (C.c_int, []),
     "csz_kernel_name": (C.c_char_p, [C.c_int]),

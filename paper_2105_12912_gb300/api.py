@@ -143,6 +143,86 @@ def header(archive) -> dict:
 
 
 # ---------------------------------------------------------------------------------
+# batched compression (one launch per stage for all fields, replayed as a CUDA graph)
+# ---------------------------------------------------------------------------------
+class BatchCompressor:
+    """Compresses a fixed list of device fields together.  Construction lays out the
+    workspace, uploads the per-field tables, optionally autotunes and captures the
+    launch graph; run() replays it (no host synchronisation); results() reads sizes
+    and statuses.  The field tensors are referenced, not copied: overwrite them in
+    place between runs to compress new data of the same shapes."""
+
+    def __init__(self, fields, ebs, eb_modes="rel", select="exhaustive", radius=512, weights=None,
+                 autotune=True, archive_caps=None, stream=None):
+        n = len(fields)
+        if n == 0:
+            raise ValueError("empty batch")
+        ebs = list(ebs) if hasattr(ebs, "__len__") else [ebs] * n
+        modes = list(eb_modes) if isinstance(eb_modes, (list, tuple)) else [eb_modes] * n
+        dev = fields[0].device
+        self.fields = list(fields)
+        self.archives = []
+        arr = (L.csz_field * n)()
+        for i, x in enumerate(self.fields):
+            if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and 1 <= x.dim() <= 3):
+                raise ValueError("fields must be contiguous float32 CUDA tensors of 1-3 dims")
+            cap = int(archive_caps[i]) if archive_caps is not None else max_archive_bytes(tuple(x.shape))
+            a = torch.empty(max(cap, 1), dtype=torch.uint8, device=dev)
+            self.archives.append(a)
+            f = arr[i]
+            f.d_field = x.data_ptr()
+            f.ndim = x.dim()
+            for k, d in enumerate(x.shape):
+                f.dims[k] = int(d)
+            f.eb_mode = EB_MODES[modes[i]] if isinstance(modes[i], str) else int(modes[i])
+            f.eb = float(ebs[i])
+            f.d_archive = a.data_ptr()
+            f.archive_cap = a.numel()
+        self._arr = arr
+        wsb = int(L.lib().csz_batch_workspace_bytes(n, arr))
+        if wsb == 0:
+            raise ValueError("invalid field in batch")
+        self.workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        opt = L.csz_options()
+        opt.radius = int(radius)
+        opt.select = SELECT[select] if isinstance(select, str) else int(select)
+        self.weights = weights
+        if weights is not None:
+            if not (weights.is_cuda and weights.dtype == torch.float32 and weights.numel() == MLP_PARAMS):
+                raise ValueError("weights must be a float32 CUDA tensor of 1443 parameters")
+            opt.selector_weights = C.c_void_p(weights.data_ptr())
+        h = C.c_void_p()
+        st = L.lib().csz_batch_create(n, arr, C.byref(opt), C.c_void_p(self.workspace.data_ptr()), wsb,
+                                      1 if autotune else 0, _stream_ptr(stream), C.byref(h))
+        if st != L.OK:
+            raise L.CszError(st, "csz_batch_create (" + L.lib().csz_batch_last_error().decode() + ")")
+        self._h = h
+        self.n = n
+
+    def run(self, stream=None):
+        _check(L.lib().csz_batch_compress(self._h, _stream_ptr(stream)), "csz_batch_compress")
+
+    def results(self, stream=None):
+        """(sizes, statuses): per-field archive bytes and csz_status values."""
+        sizes = (C.c_uint64 * self.n)()
+        stats = (C.c_int * self.n)()
+        L.lib().csz_batch_results(self._h, sizes, stats, _stream_ptr(stream))
+        return [int(v) for v in sizes], [int(v) for v in stats]
+
+    def info(self):
+        g = C.c_int()
+        ms = (C.c_double * 4)()
+        L.lib().csz_batch_info(self._h, C.byref(g), ms)
+        return {"construct_grid": int(g.value), "tuned_ms": [float(v) for v in ms]}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            L.lib().csz_batch_destroy(h)
+            self._h = None
+
+
+# ---------------------------------------------------------------------------------
 # learned selector: training rows, inference, gradient, training
 # ---------------------------------------------------------------------------------
 def _f32_cuda(t, name, shape=None):

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libcszp.so")
-SOURCES = ["construct.cu", "compress.cu", "decompress.cu", "api.cu", "selector.cu", "noalloc.cu"]
+SOURCES = ["construct.cu", "compress.cu", "decompress.cu", "api.cu", "batch.cu", "selector.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

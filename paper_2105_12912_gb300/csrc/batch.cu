@@ -1,0 +1,452 @@
+// Batched compression: many fields of any shape and dimensionality go through one
+// launch per stage -- range, construction, books and record offsets, encoding --
+// each kernel walking a per-field table in device memory (the construction and
+// encoding kernels take codec blocks of all fields from one ticket).  The launch
+// sequence is captured once into a CUDA graph and replayed; results stay on the
+// device until the caller reads them.  An autotuner picks the construction kernel's
+// persistent grid (resident CTAs per SM) by timing the candidates on the batch.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cszp.h"
+#include "host.h"
+#include "kernels.h"
+
+using namespace cszp;
+
+struct csz_batch {
+  int nfields = 0;
+  std::vector<Geom> geom;
+  // device tables and regions (inside the caller's workspace)
+  unsigned char* zero_base = nullptr;
+  uint64_t zero_bytes = 0;
+  uint32_t* tickets = nullptr;  // [0] construction, [1] encoding
+  DevState* states = nullptr;   // nfields, kStateStride apart
+  ConstructTask* ctasks = nullptr;
+  uint32_t* tile0 = nullptr;  // nfields + 1
+  RangeTask* rtasks = nullptr;
+  uint32_t* cta0 = nullptr;  // nfields + 1
+  BookArgs* btasks = nullptr;
+  EncodeArgs* etasks = nullptr;
+  uint32_t ntiles = 0, nrange = 0;
+  int construct_grid = 0;  // 0 = default (all resident CTAs)
+  int tuned_grid = 0;
+  double tuned_ms[4] = {0, 0, 0, 0};
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// last CUDA failure inside csz_batch_create (step name and runtime error)
+const char* g_fail_step = "";
+cudaError_t g_fail_err = cudaSuccess;
+
+bool failed(cudaError_t e, const char* step) {
+  if (e == cudaSuccess) return false;
+  g_fail_step = step;
+  g_fail_err = e;
+  return true;
+}
+
+constexpr uint64_t kStateStride = 256;
+static_assert(sizeof(DevState) <= kStateStride, "DevState stride");
+constexpr uint64_t kHistBytes = (kNsymCode + kNsymCode + kNsymLen) * 4;
+
+struct FieldLayout {  // offsets from the start of the per-field part
+  uint64_t lens, bcodes, codes, counts, masks, deltas, rec_off, total;
+};
+
+FieldLayout field_layout(const Geom& g) {
+  FieldLayout L;
+  uint64_t o = 0;
+  L.lens = o;
+  o += a256(2 * kNsymCode + kNsymLen);
+  L.bcodes = o;
+  o += a256(8ull * (2 * kNsymCode + kNsymLen));
+  L.codes = o;
+  o += a256(2ull * kSlots * g.nblk);
+  L.counts = o;
+  o += a256(4ull * g.nblk);
+  L.masks = o;
+  o += a256(1024ull * g.nblk);
+  L.deltas = o;
+  o += a256(4ull * kSlots * g.nblk);
+  L.rec_off = o;
+  o += a256(8ull * g.nblk);
+  L.total = o;
+  return L;
+}
+
+// Whole-batch layout: zeroed part (tickets, states, histograms, look-back states),
+// tables, then the fields' own regions.
+struct BatchLayout {
+  uint64_t tickets, states, hists, lb, zero_end;
+  uint64_t ctasks, tile0, rtasks, cta0, btasks, etasks, fields_begin;
+  std::vector<uint64_t> lb_at, field_at;
+  uint64_t total;
+};
+
+BatchLayout batch_layout(const std::vector<Geom>& gs) {
+  const uint64_t F = gs.size();
+  BatchLayout B;
+  uint64_t o = 0;
+  B.tickets = o;
+  o += 256;
+  B.states = o;
+  o += kStateStride * F;
+  B.hists = o;
+  o += a256(kHistBytes) * F;
+  B.lb = o;
+  B.lb_at.resize(F);
+  for (uint64_t f = 0; f < F; f++) {
+    B.lb_at[f] = o;
+    o += a256(8ull * gs[f].nblk);
+  }
+  B.zero_end = o;
+  B.ctasks = o;
+  o += a256(sizeof(ConstructTask) * F);
+  B.tile0 = o;
+  o += a256(4 * (F + 1));
+  B.rtasks = o;
+  o += a256(sizeof(RangeTask) * F);
+  B.cta0 = o;
+  o += a256(4 * (F + 1));
+  B.btasks = o;
+  o += a256(sizeof(BookArgs) * F);
+  B.etasks = o;
+  o += a256(sizeof(EncodeArgs) * F);
+  B.fields_begin = o;
+  B.field_at.resize(F);
+  for (uint64_t f = 0; f < F; f++) {
+    B.field_at[f] = o;
+    o += field_layout(gs[f]).total;
+  }
+  B.total = o;
+  return B;
+}
+
+csz_status check_fields(int nfields, const csz_field* fields, std::vector<Geom>& gs) {
+  if (nfields <= 0 || !fields) return CSZ_E_ARG;
+  gs.resize(nfields);
+  uint64_t tiles = 0;
+  for (int f = 0; f < nfields; f++) {
+    const csz_field& d = fields[f];
+    if (!make_geom(d.ndim, d.dims, gs[f])) return CSZ_E_ARG;
+    if (!(d.eb > 0.0) || !std::isfinite(d.eb) || (d.eb_mode != CSZ_EB_ABS && d.eb_mode != CSZ_EB_REL))
+      return CSZ_E_ARG;
+    tiles += gs[f].nblk;
+  }
+  if (tiles >= (1ull << 32)) return CSZ_E_ARG;
+  return CSZ_OK;
+}
+
+template <typename T>
+cudaError_t upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s);
+}
+
+// The batch's launch sequence on `s` (also what the graph captures).
+cudaError_t enqueue(const csz_batch* b, int construct_grid, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, s);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_range_batch(b->rtasks, b->cta0, b->nfields, b->nrange, s)) != cudaSuccess) return e;
+  if ((e = launch_construct_batch(b->ctasks, b->tile0, b->nfields, b->ntiles, &b->tickets[0], kSpinLimit,
+                                  construct_grid, s)) != cudaSuccess)
+    return e;
+  if ((e = launch_codebook_batch(b->btasks, b->nfields, s)) != cudaSuccess) return e;
+  return launch_encode_batch(b->etasks, b->tile0, b->nfields, b->ntiles, &b->tickets[1], s);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t csz_batch_workspace_bytes(int nfields, const csz_field* fields) {
+  std::vector<Geom> gs;
+  if (check_fields(nfields, fields, gs) != CSZ_OK) return 0;
+  return (size_t)batch_layout(gs).total;
+}
+
+csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_options* opt, void* d_ws,
+                            size_t ws_bytes, int autotune, void* stream, csz_batch** out) {
+  if (!out || !d_ws) return CSZ_E_ARG;
+  *out = nullptr;
+  std::vector<Geom> gs;
+  csz_status r = check_fields(nfields, fields, gs);
+  if (r != CSZ_OK) return r;
+  const uint32_t radius = (opt && opt->radius) ? opt->radius : 512u;
+  const int select = opt ? (int)opt->select : SEL_EXHAUSTIVE;
+  if (radius > 512 || select < 0 || select > SEL_LEARNED) return CSZ_E_ARG;
+  if (select == SEL_LEARNED && !(opt && opt->selector_weights)) return CSZ_E_ARG;
+  if (opt)
+    for (int i = 0; i < 4; i++)
+      if (opt->reserved[i]) return CSZ_E_ARG;
+  const BatchLayout B = batch_layout(gs);
+  if (ws_bytes < B.total) return CSZ_E_CAPACITY;
+  for (int f = 0; f < nfields; f++) {
+    const uint64_t off_rec = kHdr + a8(gs[f].nblk) + a8(4ull * gs[f].nblk);
+    if (!fields[f].d_field || !fields[f].d_archive) return CSZ_E_ARG;
+    if (fields[f].archive_cap < off_rec) return CSZ_E_CAPACITY;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* ws = static_cast<unsigned char*>(d_ws);
+
+  csz_batch* b = new (std::nothrow) csz_batch();
+  if (!b) return CSZ_E_ARG;
+  b->nfields = nfields;
+  b->geom = gs;
+  b->zero_base = ws;
+  b->zero_bytes = B.zero_end;
+  b->tickets = at<uint32_t>(ws, B.tickets);
+  b->states = at<DevState>(ws, B.states);
+  b->ctasks = at<ConstructTask>(ws, B.ctasks);
+  b->tile0 = at<uint32_t>(ws, B.tile0);
+  b->rtasks = at<RangeTask>(ws, B.rtasks);
+  b->cta0 = at<uint32_t>(ws, B.cta0);
+  b->btasks = at<BookArgs>(ws, B.btasks);
+  b->etasks = at<EncodeArgs>(ws, B.etasks);
+
+  std::vector<ConstructTask> ct(nfields);
+  std::vector<RangeTask> rt(nfields);
+  std::vector<BookArgs> bt(nfields);
+  std::vector<EncodeArgs> et(nfields);
+  std::vector<uint32_t> tile0(nfields + 1), cta0(nfields + 1);
+  uint32_t tiles = 0, ctas = 0;
+  for (int f = 0; f < nfields; f++) {
+    const csz_field& d = fields[f];
+    const Geom& g = gs[f];
+    const FieldLayout FL = field_layout(g);
+    unsigned char* fw = ws + B.field_at[f];
+    DevState* st = reinterpret_cast<DevState*>(ws + B.states + kStateStride * f);
+    uint32_t* hists = reinterpret_cast<uint32_t*>(ws + B.hists + a256(kHistBytes) * f);
+    const uint64_t off_bb = kHdr + a8(g.nblk);
+    const uint64_t off_rec = off_bb + a8(4ull * g.nblk);
+    tile0[f] = tiles;
+    tiles += g.nblk;
+    cta0[f] = ctas;
+    ctas += d.eb_mode == CSZ_EB_REL ? range_ctas(g.nelem) : 1u;
+
+    RangeTask& R = rt[f];
+    R.x = d.d_field;
+    R.n = g.nelem;
+    R.st = st;
+    R.mode = d.eb_mode;
+    R.eb = d.eb;
+
+    memset(&ct[f], 0, sizeof(ConstructTask));
+    ConstructArgs& ca = ct[f].a;
+    ca.x = d.d_field;
+    ca.g = g;
+    ca.st = st;
+    ca.radius = radius;
+    ca.codes = at<uint16_t>(fw, FL.codes);
+    ca.hist_code = hists;
+    ca.hist_val = hists + kNsymCode;
+    ca.hist_len = hists + 2 * kNsymCode;
+    ca.counts = at<uint32_t>(fw, FL.counts);
+    ca.masks = at<uint32_t>(fw, FL.masks);
+    ca.deltas = at<int32_t>(fw, FL.deltas);
+    ca.spin_limit = kSpinLimit;
+    ca.all_runs = (select == SEL_RLE || select == SEL_RLE_HUFF) ? 1 : 0;
+    prepare_construct_task(ct[f]);
+
+    RecordArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.x = d.d_field;
+    ra.counts = ca.counts;
+    ra.masks = ca.masks;
+    ra.deltas = ca.deltas;
+    ra.rec_off = at<uint64_t>(fw, FL.rec_off);
+    ra.rec = reinterpret_cast<uint32_t*>(d.d_archive + off_rec);
+    ra.rec_cap = (d.archive_cap - off_rec) / 8;
+
+    BookArgs& ba = bt[f];
+    memset(&ba, 0, sizeof(ba));
+    ba.hist_code = ca.hist_code;
+    ba.hist_val = ca.hist_val;
+    ba.hist_len = ca.hist_len;
+    ba.lens = at<uint8_t>(fw, FL.lens);
+    ba.codes = at<uint64_t>(fw, FL.bcodes);
+    ba.st = st;
+    ba.place_records = 1;
+    ba.nblk = g.nblk;
+    ba.rec = ra;
+
+    EncodeArgs& ea = et[f];
+    memset(&ea, 0, sizeof(ea));
+    ea.g = g;
+    ea.st = st;
+    ea.radius = radius;
+    ea.select = select;
+    ea.codes = ca.codes;
+    ea.lens = ba.lens;
+    ea.bcodes = ba.codes;
+    ea.mlp_w = opt ? opt->selector_weights : nullptr;
+    ea.all_runs = ca.all_runs;
+    ea.ar = d.d_archive;
+    ea.cap = d.archive_cap;
+    ea.off_codec = kHdr;
+    ea.off_bb = off_bb;
+    ea.off_rec = off_rec;
+    ea.lb = at<uint64_t>(ws, B.lb_at[f]);
+    ea.spin_limit = kSpinLimit;
+    ea.place_records = 1;
+    ea.rec = ra;
+    FinalizeArgs& fa = ea.fin;
+    fa.st = st;
+    fa.ar = d.d_archive;
+    fa.cap = d.archive_cap;
+    fa.ndim = d.ndim;
+    fa.eb_mode = d.eb_mode;
+    for (int i = 0; i < 3; i++) fa.dims[i] = i < d.ndim ? d.dims[i] : 0;
+    fa.eb_user = d.eb;
+    fa.radius = radius;
+    fa.select = select;
+    fa.nblk = g.nblk;
+    fa.off_bb = off_bb;
+    fa.off_rec = off_rec;
+    fa.lens = ba.lens;
+  }
+  tile0[nfields] = tiles;
+  cta0[nfields] = ctas;
+  b->ntiles = tiles;
+  b->nrange = ctas;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = upload(b->ctasks, ct, s);
+  if (e == cudaSuccess) e = upload(b->tile0, tile0, s);
+  if (e == cudaSuccess) e = upload(b->rtasks, rt, s);
+  if (e == cudaSuccess) e = upload(b->cta0, cta0, s);
+  if (e == cudaSuccess) e = upload(b->btasks, bt, s);
+  if (e == cudaSuccess) e = upload(b->etasks, et, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (failed(e, "table upload")) {
+    delete b;
+    return CSZ_E_CUDA;
+  }
+
+  // autotune the construction grid: resident CTAs per SM 1..max, timed on the batch
+  const int full = construct_grid(tiles);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->tuned_grid = full;
+  if (autotune && sms > 0) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 0.0f;
+    for (int k = 1; k <= 4; k++) {
+      int grid = sms * k;
+      if (grid > full) grid = full;
+      float ms = 0.0f;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+        cudaEventRecord(e0, s);
+        e = enqueue(b, grid, s);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (e != cudaSuccess) break;
+      b->tuned_ms[k - 1] = ms;
+      if (best == 0.0f || ms < best) {
+        best = ms;
+        b->tuned_grid = grid;
+      }
+      if (grid == full) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (failed(e, "autotune run")) {
+      delete b;
+      return CSZ_E_CUDA;
+    }
+  }
+  b->construct_grid = b->tuned_grid;
+
+  // capture the launch sequence once, on a private stream (the caller's may be the
+  // legacy default stream, which cannot be captured); replays go to any stream
+  const bool tracing = trace_suspend();
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cap = nullptr;
+  e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  const char* step = "capture stream";
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    step = "begin capture";
+  }
+  if (e == cudaSuccess) {
+    const cudaError_t e2 = enqueue(b, b->construct_grid, cap);
+    e = cudaStreamEndCapture(cap, &graph);
+    step = "end capture";
+    if (e == cudaSuccess && e2 != cudaSuccess) {
+      e = e2;
+      step = "captured launches";
+    }
+  }
+  if (e == cudaSuccess) {
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    step = "instantiate";
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (cap) cudaStreamDestroy(cap);
+  trace_resume(tracing);
+  if (failed(e, step)) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
+    return CSZ_E_CUDA;
+  }
+  *out = b;
+  return CSZ_OK;
+}
+
+csz_status csz_batch_compress(csz_batch* b, void* stream) {
+  if (!b || !b->exec) return CSZ_E_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return CSZ_E_CUDA;
+  trace_count_batch();
+  return CSZ_OK;
+}
+
+csz_status csz_batch_results(csz_batch* b, uint64_t* h_bytes, int* h_status, void* stream) {
+  if (!b) return CSZ_E_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<unsigned char> buf(kStateStride * b->nfields);
+  if (cudaMemcpyAsync(buf.data(), b->states, buf.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CSZ_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  csz_status worst = CSZ_OK;
+  for (int f = 0; f < b->nfields; f++) {
+    DevState st;
+    memcpy(&st, buf.data() + kStateStride * f, sizeof(st));
+    const csz_status r = fold(st.status);
+    if (h_status) h_status[f] = (int)r;
+    if (h_bytes) h_bytes[f] = r == CSZ_OK ? st.total : 0;
+    if (r != CSZ_OK && worst == CSZ_OK) worst = r;
+  }
+  return worst;
+}
+
+csz_status csz_batch_info(const csz_batch* b, int* construct_grid, double* tuned_ms) {
+  if (!b) return CSZ_E_ARG;
+  if (construct_grid) *construct_grid = b->construct_grid;
+  if (tuned_ms)
+    for (int i = 0; i < 4; i++) tuned_ms[i] = b->tuned_ms[i];
+  return CSZ_OK;
+}
+
+const char* csz_batch_last_error(void) {
+  static char buf[160];
+  snprintf(buf, sizeof(buf), "%s: %s", g_fail_step, cudaGetErrorString(g_fail_err));
+  return buf;
+}
+
+void csz_batch_destroy(csz_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  delete b;
+}
+
+}  // extern "C"

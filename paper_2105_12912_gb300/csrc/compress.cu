@@ -48,13 +48,13 @@ __global__ void abs_params_kernel(DevState* st, double eb) {
 
 // Grid-stride min/max with float4 loads; non-finite values are flagged.  The last CTA
 // to finish derives the error bound.
-__global__ __launch_bounds__(256) void range_kernel(const float* __restrict__ x, uint64_t n,
-                                                    DevState* st, int mode, double eb) {
+__device__ void range_body(const float* __restrict__ x, uint64_t n, DevState* st, int mode, double eb,
+                           uint32_t cta, uint32_t nctas) {
   __shared__ uint32_t s_red[2][33];
   __shared__ bool s_last;
   uint32_t lo_inv = 0, hi = 0, bad = 0;
-  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = cta * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)nctas * blockDim.x;
   const bool vec = (((uintptr_t)x) & 15) == 0;
   uint64_t nvec = vec ? n / 4 : 0;
   const float4* x4 = reinterpret_cast<const float4*>(x);
@@ -104,7 +104,7 @@ __global__ __launch_bounds__(256) void range_kernel(const float* __restrict__ x,
     atomicMax(&st->range_lo_inv, a);
     atomicMax(&st->range_hi, b);
     __threadfence();
-    s_last = atomicAdd(&st->range_done, 1u) == gridDim.x - 1;
+    s_last = atomicAdd(&st->range_done, 1u) == nctas - 1;
   }
   __syncthreads();
   if (s_last && threadIdx.x == 0) {
@@ -117,6 +117,30 @@ __global__ __launch_bounds__(256) void range_kernel(const float* __restrict__ x,
     }
     derive_eb(st, mode, eb, key_to_float(~a), key_to_float(b));
   }
+}
+
+__global__ __launch_bounds__(256) void range_kernel(const float* __restrict__ x, uint64_t n, DevState* st, int mode,
+                                                    double eb) {
+  range_body(x, n, st, mode, eb, blockIdx.x, gridDim.x);
+}
+
+// Batch: cta0[f] .. cta0[f+1]-1 are field f's CTAs; an ABS field has one CTA, which
+// only derives the bound.
+__global__ __launch_bounds__(256) void range_batch_kernel(const RangeTask* __restrict__ tasks,
+                                                          const uint32_t* __restrict__ cta0, int nfields) {
+  const uint32_t c = blockIdx.x;
+  int lo = 0, hi = nfields - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cta0[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  const RangeTask& t = tasks[lo];
+  if (t.mode == 0) {
+    if (threadIdx.x == 0) derive_eb(t.st, 0, t.eb, 0.0f, 0.0f);
+    return;
+  }
+  range_body(t.x, t.n, t.st, t.mode, t.eb, c - cta0[lo], cta0[lo + 1] - cta0[lo]);
 }
 
 
@@ -193,13 +217,15 @@ __device__ void record_offsets_body(const BookArgs& a) {
   }
 }
 
-__global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) {
+// One canonical book (role 0 code, 1 run value, 2 run length) or, role 3, the
+// record offsets of a field.
+__device__ void codebook_body(const BookArgs& a, int role) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (blockIdx.x == 3) {
+  if (role == 3) {
     record_offsets_body(a);
     return;
   }
-  const int book = blockIdx.x;
+  const int book = role;
   const int nsym = book == 2 ? kNsymLen : kNsymCode;
   const uint32_t* hist = book == 0 ? a.hist_code : (book == 1 ? a.hist_val : a.hist_len);
   uint8_t* len_out = a.lens + (book == 0 ? 0 : (book == 1 ? kNsymCode : 2 * kNsymCode));
@@ -384,6 +410,13 @@ __global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) {
   canonical_build(s_len, nsym, &cs, reinterpret_cast<uint16_t*>(A), code_out, nullptr);
 }
 
+__global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) { codebook_body(a, blockIdx.x); }
+
+// Batch: four CTAs per field (three books and the record offsets).
+__global__ __launch_bounds__(kBookThreads) void codebook_batch_kernel(const BookArgs* __restrict__ tasks) {
+  codebook_body(tasks[blockIdx.x >> 2], blockIdx.x & 3);
+}
+
 static size_t codebook_smem_bytes() { return 94208 + kNsymLen * 8; }
 
 // =================================================================================
@@ -497,7 +530,8 @@ __device__ __forceinline__ uint32_t units_from_partials(const uint32_t* part) {
   return warp_sum(ihs_lane_units(bits));
 }
 
-__global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
+// Selection and encoding of codec block b of one field (all threads of the CTA).
+__device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint16_t* s_c = reinterpret_cast<uint16_t*>(smem);             // 4096 codes
   uint16_t* s_rv = s_c + kSlots;                                 // run values
@@ -509,14 +543,11 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   uint32_t* s_part = s_next + kSlots / 32;                       // 2 x 256
   uint32_t* s_scan = s_part + 2 * kEncThreads;                   // 34
   uint64_t* s_scan64 = reinterpret_cast<uint64_t*>(s_scan + 34); // 33
-  __shared__ uint32_t s_tile, s_codec, s_units[3];
+  __shared__ uint32_t s_codec, s_units[3];
   __shared__ uint64_t s_prefix;
   __shared__ float s_feat[8];
 
   const int tid = threadIdx.x, wid = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(&a.st->ticket_encode, 1u);
-  __syncthreads();
-  const uint32_t b = s_tile;
   uint32_t org[3], w[3];
   block_box(a.g, b, org, w);
   const uint32_t m = w[0] * w[1] * w[2];
@@ -822,6 +853,37 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
   }
 }
 
+// Blocks are taken in ticket order, so the payload look-back only ever waits on
+// blocks that CTAs already hold.
+__global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&a.st->ticket_encode, 1u);
+  __syncthreads();
+  encode_body(a, s_tile);
+}
+
+// Batch: one CTA per codec block of every field; the ticket runs over the blocks of
+// all fields in order (tile0[f] = first block of field f).
+__global__ __launch_bounds__(kEncThreads) void encode_batch_kernel(const EncodeArgs* __restrict__ tasks,
+                                                                   const uint32_t* __restrict__ tile0, int nfields,
+                                                                   uint32_t* ticket) {
+  __shared__ uint32_t s_tile;
+  __shared__ int s_field;
+  if (threadIdx.x == 0) {
+    const uint32_t t = atomicAdd(ticket, 1u);
+    int lo = 0, hi = nfields - 1;  // last field with tile0[f] <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile0[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    s_field = lo;
+    s_tile = t - tile0[lo];
+  }
+  __syncthreads();
+  encode_body(tasks[s_field], s_tile);
+}
+
 static size_t encode_smem_bytes() {
   return kSlots * 2 * 3 + kBufBytes + (kSlots / 32) * 4 * 3 + 16 + 2 * kEncThreads * 4 + 34 * 4 + 33 * 8 + 16;
 }
@@ -837,14 +899,9 @@ cudaError_t launch_abs_params(DevState* st, double eb, cudaStream_t s) {
 }
 
 cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, double eb, cudaStream_t s) {
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint64_t want = (n / 4 + 255) / 256;
-  uint64_t grid = want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8;
-  if (grid == 0) grid = 1;
+  const uint32_t grid = range_ctas(n);
   trace_begin(K_RANGE, s);
-  range_kernel<<<(unsigned)grid, 256, 0, s>>>(x, n, st, mode, eb);
+  range_kernel<<<grid, 256, 0, s>>>(x, n, st, mode, eb);
   trace_end(K_RANGE, s);
   return cudaGetLastError();
 }
@@ -863,6 +920,46 @@ cudaError_t launch_codebook(const BookArgs& a, cudaStream_t s) {
 cudaError_t launch_encode(const EncodeArgs& a, cudaStream_t s) {
   trace_begin(K_ENCODE, s);
   encode_kernel<<<a.g.nblk, kEncThreads, encode_smem_bytes(), s>>>(a);
+  trace_end(K_ENCODE, s);
+  return cudaGetLastError();
+}
+
+uint32_t range_ctas(uint64_t n) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const uint64_t want = (n / 4 + 255) / 256;
+  const uint64_t grid = want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8;
+  return grid ? (uint32_t)grid : 1u;
+}
+
+cudaError_t launch_range_batch(const RangeTask* d_tasks, const uint32_t* d_cta0, int nfields, uint32_t nctas,
+                               cudaStream_t s) {
+  trace_begin(K_RANGE, s);
+  range_batch_kernel<<<nctas, 256, 0, s>>>(d_tasks, d_cta0, nfields);
+  trace_end(K_RANGE, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_codebook_batch(const BookArgs* d_tasks, int nfields, cudaStream_t s) {
+  const size_t sm = codebook_smem_bytes();
+  cudaError_t e =
+      cudaFuncSetAttribute(codebook_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  trace_begin(K_CODEBOOK, s);
+  codebook_batch_kernel<<<4 * nfields, kBookThreads, sm, s>>>(d_tasks);
+  trace_end(K_CODEBOOK, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode_batch(const EncodeArgs* d_tasks, const uint32_t* d_tile0, int nfields, uint32_t ntiles,
+                                uint32_t* ticket, cudaStream_t s) {
+  trace_begin(K_ENCODE, s);
+  encode_batch_kernel<<<ntiles, kEncThreads, encode_smem_bytes(), s>>>(d_tasks, d_tile0, nfields, ticket);
   trace_end(K_ENCODE, s);
   return cudaGetLastError();
 }

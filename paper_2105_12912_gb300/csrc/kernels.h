@@ -26,6 +26,15 @@ struct ConstructArgs {
   int all_runs;        // every block's runs feed the run books (forced run codecs)
 };
 
+// Value range / error bound of one field of a batch.
+struct RangeTask {
+  const float* x;
+  uint64_t n;
+  DevState* st;
+  int mode;  // CSZ_EB_ABS / CSZ_EB_REL
+  double eb;
+};
+
 // Record placement: the exclusive prefix of the blocks' record counts (one CTA of
 // the codebook launch), then each encode CTA writes its block's outlier and patch
 // records in slot order at that offset.
@@ -149,18 +158,29 @@ enum KernelId : int {
 };
 void trace_begin(int id, cudaStream_t s);
 void trace_end(int id, cudaStream_t s);
+bool trace_suspend();           // stop event tracing (stream capture); returns the old state
+void trace_resume(bool on);
+void trace_count_batch();       // one replay of a compression batch graph: count its launches
 
 // ---- launchers (return cudaGetLastError of the launch) ---------------------------
 cudaError_t launch_abs_params(DevState* st, double eb, cudaStream_t s);
 cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, double eb, cudaStream_t s);
 void prepare_construct_task(ConstructTask& t);  // tensor map when TMA applies
 size_t construct_smem_bytes();
+int construct_grid(uint32_t ntiles);  // persistent grid: all resident CTAs, at most ntiles
 cudaError_t launch_construct(const ConstructTask& one, uint32_t* ticket, cudaStream_t s);
 cudaError_t launch_construct_batch(const ConstructTask* d_tasks, const uint32_t* d_tile0, int nfields,
                                    uint32_t ntiles, uint32_t* ticket, uint32_t spin_limit, int grid,
                                    cudaStream_t s);
 cudaError_t launch_codebook(const BookArgs& a, cudaStream_t s);
 cudaError_t launch_encode(const EncodeArgs& a, cudaStream_t s);
+// batches: per-field tables in device memory
+uint32_t range_ctas(uint64_t n);  // CTAs the range pass gives a REL field of n elements
+cudaError_t launch_range_batch(const RangeTask* d_tasks, const uint32_t* d_cta0, int nfields, uint32_t nctas,
+                               cudaStream_t s);
+cudaError_t launch_codebook_batch(const BookArgs* d_tasks, int nfields, cudaStream_t s);
+cudaError_t launch_encode_batch(const EncodeArgs* d_tasks, const uint32_t* d_tile0, int nfields, uint32_t ntiles,
+                                uint32_t* ticket, cudaStream_t s);
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);
 
