@@ -57,6 +57,10 @@ def grf(shape, beta: float, seed: int, device="cpu") -> torch.Tensor:
     shape = tuple(int(s) for s in shape)
     g = _gen(seed, device)
     noise = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+    if torch.device(device).type == "cpu":
+        # host fields go through numpy's FFT (double precision): some builds of torch's
+        # CPU FFT corrupt memory on odd 3-D shapes
+        return _grf_host(noise.numpy(), beta)
     spec = torch.fft.rfftn(noise)
     del noise
     k2 = None
@@ -79,6 +83,27 @@ def grf(shape, beta: float, seed: int, device="cpu") -> torch.Tensor:
     if float(sd) > 0:
         out = out / sd
     return out.to(torch.float32).contiguous()
+
+
+def _grf_host(noise: np.ndarray, beta: float) -> torch.Tensor:
+    shape = noise.shape
+    axes = list(range(len(shape)))
+    spec = np.fft.rfftn(noise.astype(np.float64), axes=axes)
+    k2 = np.zeros(spec.shape, dtype=np.float64)
+    for ax, s in enumerate(shape):
+        f = np.fft.rfftfreq(s, d=1.0 / s) if ax == len(shape) - 1 else np.fft.fftfreq(s, d=1.0 / s)
+        view = [1] * len(shape)
+        view[ax] = -1
+        k2 = k2 + (f ** 2).reshape(view)
+    amp = np.zeros_like(k2)
+    pos = k2 > 0
+    amp[pos] = k2[pos] ** (-beta / 4.0)
+    out = np.fft.irfftn(spec * amp, s=shape, axes=axes)
+    out = out - out.mean()
+    sd = out.std()
+    if sd > 0:
+        out = out / sd
+    return torch.from_numpy(np.ascontiguousarray(out.astype(np.float32)))
 
 
 def zero_patches(x: torch.Tensor, frac: float, seed: int, patch: int = 64) -> torch.Tensor:
@@ -106,7 +131,7 @@ def zero_patches(x: torch.Tensor, frac: float, seed: int, patch: int = 64) -> to
 
 def zero_blocks(x: torch.Tensor, frac: float, seed: int, edge: int = 16) -> torch.Tensor:
     """Set randomly chosen aligned edge^ndim blocks to exactly 0.0 until at least
-    `frac` of the cells are zero (1-, 2- or 3-D)."""
+    `frac` of the cells are zero (1-, 2- or 3-D); some cells always stay non-zero."""
     shape = x.shape
     grid = [int(math.ceil(s / edge)) for s in shape]
     nb = int(np.prod(grid))
@@ -123,6 +148,8 @@ def zero_blocks(x: torch.Tensor, frac: float, seed: int, edge: int = 16) -> torc
         cells = 1
         for d, i in enumerate(idx):
             cells *= min(edge, shape[d] - i * edge)
+        if count + cells >= total:
+            continue  # never zero a whole field (its value range would be empty)
         cellmask[b] = True
         count += cells
     m = torch.from_numpy(cellmask.reshape(grid))
