@@ -202,10 +202,14 @@ def batched_comparison(args, dev, flush):
     modes = [sp.eb_mode for sp in specs]
     n_in = sum(4 * x.numel() for x in xs)
     caps = [min(api.max_archive_bytes(tuple(x.shape)), 6 * x.numel() + (1 << 20)) for x in xs]
-    # selector weights: trained on the method's own sizes from 8 separate seeded fields
-    rows = selector.collect_rows([(lambda s=s: synth.make_field(synth.workload_selector(s, dims=(48, 160, 160)),
-                                                                 dev), 1e-3, "rel") for s in range(1000, 1008)])
-    w, _, _ = selector.train(rows, seed=0, steps=1500)
+    # selector weights: trained on the method's own sizes from separately seeded fields
+    # of the same mix (seeds 9000+, a twentieth of the size) and 3-D zero-block fields
+    train_specs = synth.workload_batch(48, seed0=9000, scale=0.05)
+    rows = selector.collect_rows(
+        [(lambda sp=sp: synth.make_field(sp, dev), sp.eb, sp.eb_mode) for sp in train_specs] +
+        [(lambda s=s: synth.make_field(synth.workload_selector(s, dims=(48, 160, 160)), dev), 1e-3, "rel")
+         for s in range(1000, 1008)])
+    w, _, _ = selector.train(rows, seed=0, steps=3000, lr=1e-2)
     stream = torch.cuda.current_stream()
     ws = api.Workspace(dev)
     arc = torch.empty(max(caps), dtype=torch.uint8, device=dev)

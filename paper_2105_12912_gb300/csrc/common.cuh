@@ -91,6 +91,7 @@ struct DevState {
   uint32_t range_done;    // CTAs finished in the range pass
   uint32_t ticket_construct;
   uint32_t ticket_encode;
+  uint32_t ticket_decode;
   uint32_t encode_done;
   uint32_t ncodec[3];
   unsigned long long n_rec;

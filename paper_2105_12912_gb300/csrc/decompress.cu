@@ -286,23 +286,26 @@ __device__ bool ihs_decode_warp(const uint16_t* __restrict__ in, uint32_t avail,
   return !__any_sync(~0u, bad);
 }
 
-constexpr int kStreamWarps = 8;
+constexpr int kStreamWarps = 16;
 
-// Entropy decoding, one warp per interleaved stream: a Huffman block's code stream
-// (warp slot 0; slot 1 idles) or an RLE+Huffman block's value (slot 0) and length
-// (slot 1) streams.  The lookup tables of the books present sit in shared memory.
-// Runs of RLE+Huffman blocks go to the workspace run arrays.
+// Entropy decoding, persistent: each CTA stages the lookup tables of the books the
+// archive uses in shared memory once, then its warps take codec blocks from a ticket;
+// a warp decodes a Huffman block's code stream, or an RLE+Huffman block's value
+// stream and then its length stream (runs go to the workspace run arrays).
 __global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_kernel(DecodeArgs a) {
-  extern __shared__ __align__(16) uint32_t s_luts[];  // [3][1 << kLutBits]
+  extern __shared__ __align__(16) uint32_t s_luts[];  // the present books' tables
   __shared__ unsigned long long s_first[kMaxLen + 1], s_limit[kMaxLen + 1];
   __shared__ uint32_t s_off[kMaxLen + 1], s_count[kMaxLen + 1];
   if (a.st->status & ERR_CORRUPT) return;
   const bool huff = (a.flags & 1u) != 0, rle = (a.flags & 2u) != 0;
+  uint32_t* lut_code = s_luts;
+  uint32_t* lut_val = s_luts + (huff ? (1 << kLutBits) : 0);
+  uint32_t* lut_len = lut_val + (1 << kLutBits);
   for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) {
-    if (huff) s_luts[i] = a.tabs[0].lut[i];
+    if (huff) lut_code[i] = a.tabs[0].lut[i];
     if (rle) {
-      s_luts[(1 << kLutBits) + i] = a.tabs[1].lut[i];
-      s_luts[2 * (1 << kLutBits) + i] = a.tabs[2].lut[i];
+      lut_val[i] = a.tabs[1].lut[i];
+      lut_len[i] = a.tabs[2].lut[i];
     }
   }
   for (int i = threadIdx.x; i <= kMaxLen; i += blockDim.x) {
@@ -312,54 +315,59 @@ __global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_kernel(Decode
     s_count[i] = a.tabs[0].count[i];
   }
   __syncthreads();
-  const uint32_t gw = blockIdx.x * kStreamWarps + (threadIdx.x >> 5);
-  const uint32_t b = gw >> 1, which = gw & 1;
-  if (b >= a.g.nblk) return;
-  const int codec = a.ar[a.off_codec + b];
-  if (codec == CODEC_RLE || (codec == CODEC_HUFF && which == 1)) return;
   const bool lane0 = (threadIdx.x & 31) == 0;
-  uint32_t org[3], w[3];
-  block_box(a.g, b, org, w);
-  const uint32_t m = w[0] * w[1] * w[2];
-  const uint64_t bytes = a.blk_off[b + 1] - a.blk_off[b];
-  const uint8_t* pay = a.ar + a.off_pay + a.blk_off[b];
-  uint32_t used = 0;
-  bool ok;
-  if (codec == CODEC_HUFF) {
-    const DecTab* t = &a.tabs[0];
-    if (!t->present) {
-      if (lane0) flag(a.st, ERR_CORRUPT);
-      return;
-    }
-    const BookView bk{s_luts, s_first, s_limit, s_count, s_off, t->sorted, (int)t->maxlen, t->fullmask};
-    ok = ihs_decode_warp(reinterpret_cast<const uint16_t*>(pay), (uint32_t)(bytes / 2), m, bk,
-                         a.codes + (uint64_t)b * kSlots, 0, &used);
-    ok = ok && ((2ull * used + 3) & ~3ull) == bytes;
-  } else {
-    const DecTab* t = &a.tabs[1 + which];
-    if (!t->present) {
-      if (lane0) flag(a.st, ERR_CORRUPT);
-      return;
-    }
-    const uint32_t* p32 = reinterpret_cast<const uint32_t*>(pay);
-    const uint32_t nr = bytes >= 8 ? p32[0] : 0u, vu = bytes >= 8 ? p32[1] : 0u;
-    if (bytes < 8 || nr > m || 8ull + 2ull * vu > bytes) {
-      if (lane0) flag(a.st, ERR_CORRUPT);
-      return;
-    }
-    const uint32_t lavail = (uint32_t)((bytes - 8) / 2 - vu);
-    const BookView bk{s_luts + (1 + which) * (1 << kLutBits), t->first, t->limit, t->count, t->off, t->sorted,
-                      (int)t->maxlen, t->fullmask};
-    const uint16_t* p16 = reinterpret_cast<const uint16_t*>(pay) + 4;
-    if (which == 0) {
-      ok = ihs_decode_warp(p16, vu, nr, bk, a.runv + (uint64_t)b * kSlots, 0, &used);
-      ok = ok && used == vu;
+  while (true) {
+    uint32_t b = 0;
+    if (lane0) b = atomicAdd(&a.st->ticket_decode, 1u);
+    b = __shfl_sync(~0u, b, 0);
+    if (b >= a.g.nblk) break;
+    const int codec = a.ar[a.off_codec + b];
+    if (codec == CODEC_RLE) continue;
+    uint32_t org[3], w[3];
+    block_box(a.g, b, org, w);
+    const uint32_t m = w[0] * w[1] * w[2];
+    const uint64_t bytes = a.blk_off[b + 1] - a.blk_off[b];
+    const uint8_t* pay = a.ar + a.off_pay + a.blk_off[b];
+    uint32_t used = 0;
+    bool ok;
+    if (codec == CODEC_HUFF) {
+      const DecTab* t = &a.tabs[0];
+      if (!t->present) {
+        if (lane0) flag(a.st, ERR_CORRUPT);
+        continue;
+      }
+      const BookView bk{lut_code, s_first, s_limit, s_count, s_off, t->sorted, (int)t->maxlen, t->fullmask};
+      ok = ihs_decode_warp(reinterpret_cast<const uint16_t*>(pay), (uint32_t)(bytes / 2), m, bk,
+                           a.codes + (uint64_t)b * kSlots, 0, &used);
+      ok = ok && ((2ull * used + 3) & ~3ull) == bytes;
     } else {
-      ok = ihs_decode_warp(p16 + vu, lavail, nr, bk, a.runl + (uint64_t)b * kSlots, 1, &used);
-      ok = ok && ((8ull + 2ull * (vu + used) + 3) & ~3ull) == bytes;
+      const DecTab* tv = &a.tabs[1];
+      const DecTab* tl = &a.tabs[2];
+      if (!tv->present || !tl->present) {
+        if (lane0) flag(a.st, ERR_CORRUPT);
+        continue;
+      }
+      const uint32_t* p32 = reinterpret_cast<const uint32_t*>(pay);
+      const uint32_t nr = bytes >= 8 ? p32[0] : 0u, vu = bytes >= 8 ? p32[1] : 0u;
+      if (bytes < 8 || nr > m || 8ull + 2ull * vu > bytes) {
+        if (lane0) flag(a.st, ERR_CORRUPT);
+        continue;
+      }
+      const uint32_t lavail = (uint32_t)((bytes - 8) / 2 - vu);
+      const uint16_t* p16 = reinterpret_cast<const uint16_t*>(pay) + 4;
+      const BookView bv{lut_val, tv->first, tv->limit, tv->count, tv->off, tv->sorted, (int)tv->maxlen,
+                        tv->fullmask};
+      ok = ihs_decode_warp(p16, vu, nr, bv, a.runv + (uint64_t)b * kSlots, 0, &used);
+      ok = ok && used == vu;
+      if (ok) {
+        const BookView bl{lut_len, tl->first, tl->limit, tl->count, tl->off, tl->sorted, (int)tl->maxlen,
+                          tl->fullmask};
+        ok = ihs_decode_warp(p16 + vu, lavail, nr, bl, a.runl + (uint64_t)b * kSlots, 1, &used);
+        ok = ok && ((8ull + 2ull * (vu + used) + 3) & ~3ull) == bytes;
+      }
     }
+    if (!ok && lane0) flag(a.st, ERR_CORRUPT);
   }
-  if (!ok && lane0) flag(a.st, ERR_CORRUPT);
 }
 
 constexpr int kRleThreads = 256;
@@ -615,11 +623,28 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
   trace_begin(K_DEC_SETUP, s);
   dec_setup_kernel<<<(unsigned)(4 + rec_ctas), 1024, 0, s>>>(a);
   trace_end(K_DEC_SETUP, s);
-  const size_t lut_bytes = 3 * (1u << kLutBits) * sizeof(uint32_t);
-  cudaFuncSetAttribute(stream_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lut_bytes);
-  trace_begin(K_STREAM_DECODE, s);
-  stream_decode_kernel<<<(2 * a.g.nblk + kStreamWarps - 1) / kStreamWarps, 32 * kStreamWarps, lut_bytes, s>>>(a);
-  trace_end(K_STREAM_DECODE, s);
+  const int nluts = ((a.flags & 1u) ? 1 : 0) + ((a.flags & 2u) ? 2 : 0);
+  if (nluts) {
+    const size_t lut_bytes = (size_t)nluts * (1u << kLutBits) * sizeof(uint32_t);
+    static int sms = 0, occ[4] = {0, 0, 0, 0};
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaFuncSetAttribute(stream_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(3 * (1u << kLutBits) * sizeof(uint32_t)));
+    }
+    if (occ[nluts] == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[nluts], stream_decode_kernel, 32 * kStreamWarps, lut_bytes);
+      if (occ[nluts] <= 0) occ[nluts] = 1;
+    }
+    const uint64_t want = ((uint64_t)a.g.nblk + kStreamWarps - 1) / kStreamWarps;
+    const uint64_t cap = (uint64_t)sms * occ[nluts];
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    trace_begin(K_STREAM_DECODE, s);
+    stream_decode_kernel<<<grid, 32 * kStreamWarps, lut_bytes, s>>>(a);
+    trace_end(K_STREAM_DECODE, s);
+  }
   trace_begin(K_RLE_EXPAND, s);
   rle_expand_kernel<<<a.g.nblk, kRleThreads, 0, s>>>(a);
   trace_end(K_RLE_EXPAND, s);
