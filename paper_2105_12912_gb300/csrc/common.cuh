@@ -577,6 +577,134 @@ __device__ inline uint32_t ihs_encode_block(const uint16_t* sym, uint32_t N, int
   return total;
 }
 
+// Faster block-wide encoder for streams whose lanes each hold at most 4064 bits.
+// Pass 1 (ihs_plan): thread (lane l, warp w) reads the lengths of lane l's steps
+// 16w..16w+15 once into registers; per-lane totals give the stream size.  Pass 2
+// (ihs_emit): each thread appends its codes to lane l's bit string in shared memory
+// (32 strings of 128 words, word index XOR-swizzled by the lane so the 32 lanes hit
+// 32 banks), then every unit is cut straight out of its lane's string and stored at
+// its decoder-order position (rounds within steps, lanes in order within a round).
+struct IhsPlan {
+  uint32_t len4[4];    // the thread's 16 code lengths, 8 bits each
+  uint32_t pre;        // bits of lane l before step 16w
+  uint32_t cum;        // bits of the thread's 16 steps
+  uint32_t lane_bits;  // bits of lane l
+};
+
+constexpr uint32_t kLaneWords = 128;               // words per lane string
+constexpr uint32_t kLaneBitsMax = 32 * (kLaneWords - 1);  // 4064: room for a 2-word read
+
+__device__ __forceinline__ uint32_t plan_len(const IhsPlan& P, int i) {
+  // selects rather than an indexed load, so the plan stays in registers
+  const uint32_t wsel = i < 8 ? (i < 4 ? P.len4[0] : P.len4[1]) : (i < 12 ? P.len4[2] : P.len4[3]);
+  return (wsel >> (8 * (i & 3))) & 0xffu;
+}
+
+// Fills P for every thread; returns (all threads) the stream's unit count and, in
+// *max_lane_bits, the largest lane total.  scratch: >= 256 + 8 u32.  Contains
+// __syncthreads.
+__device__ inline uint32_t ihs_plan(const uint16_t* sym, uint32_t N, int add, const uint8_t* __restrict__ lens,
+                                    uint32_t* scratch, IhsPlan& P, uint32_t* max_lane_bits) {
+  const uint32_t tid = threadIdx.x, l = tid & 31, w = tid >> 5;
+  const uint32_t t0 = 16 * w;
+  uint32_t cum = 0;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    uint32_t pk = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t j = 32 * (t0 + 4 * q + k) + l;
+      const uint32_t L = j < N ? (uint32_t)__ldg(&lens[sym[j] + add]) : 0u;
+      pk |= L << (8 * k);
+      cum += L;
+    }
+    P.len4[q] = pk;
+  }
+  P.cum = cum;
+  __syncthreads();
+  scratch[32 * w + l] = cum;
+  __syncthreads();
+  uint32_t pre = 0, tot = 0;
+#pragma unroll
+  for (uint32_t v = 0; v < 8; v++) {
+    const uint32_t c = scratch[32 * v + l];
+    if (v < w) pre += c;
+    tot += c;
+  }
+  P.pre = pre;
+  P.lane_bits = tot;
+  if (w == 0) {
+    uint32_t units = warp_sum((tot + 15) >> 4);
+    uint32_t mx = tot;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(~0u, mx, o));
+    if (l == 0) {
+      scratch[256] = units;
+      scratch[257] = mx;
+    }
+  }
+  __syncthreads();
+  const uint32_t units = scratch[256];
+  *max_lane_bits = scratch[257];
+  __syncthreads();
+  return units;
+}
+
+// Pass 2; requires every lane total <= kLaneBitsMax.  lanebuf: 32 * kLaneWords u32.
+// scratch: >= 8 u32.  Contains __syncthreads.
+__device__ inline void ihs_emit(const uint16_t* sym, uint32_t N, int add, const uint64_t* __restrict__ codes,
+                                const IhsPlan& P, uint32_t* lanebuf, uint16_t* out16, uint32_t* scratch) {
+  const uint32_t tid = threadIdx.x, l = tid & 31, w = tid >> 5;
+  const uint32_t t0 = 16 * w;
+  for (uint32_t i = tid; i < 32 * kLaneWords; i += blockDim.x) lanebuf[i] = 0;
+  __syncthreads();
+  uint32_t* mine = lanebuf + kLaneWords * l;
+  uint32_t p = P.pre;
+#pragma unroll 4
+  for (int i = 0; i < 16; i++) {
+    int L = (int)plan_len(P, i);
+    if (L == 0) continue;
+    const uint64_t C = __ldg(&codes[sym[32 * (t0 + i) + l] + add]);
+    while (L > 0) {
+      const uint32_t wi = p >> 5, off = p & 31;
+      const int n = min(L, 32 - (int)off);
+      const uint32_t bits = (uint32_t)((C >> (L - n)) & ((n == 32) ? 0xffffffffull : ((1ull << n) - 1ull)));
+      atomicOr(&mine[wi ^ l], bits << (32 - off - n));
+      L -= n;
+      p += n;
+    }
+  }
+  // units each warp's steps take, for the warp's first output position
+  const uint32_t u_begin = (P.pre + 15) >> 4, u_end = (P.pre + P.cum + 15) >> 4;
+  const uint32_t wtot = warp_sum(u_end - u_begin);
+  if (l == 0) scratch[w] = wtot;
+  __syncthreads();
+  uint32_t base = 0;
+  for (uint32_t v = 0; v < w; v++) base += scratch[v];
+  const uint32_t lt = (1u << l) - 1u;
+  uint32_t c = P.pre, uprev = u_begin;
+#pragma unroll 1
+  for (int i = 0; i < 16; i++) {
+    const uint32_t cn = c + plan_len(P, i);
+    const uint32_t u = (cn + 15) >> 4;
+    const uint32_t D = u - uprev;
+#pragma unroll 1
+    for (uint32_t r = 1; r <= 4; r++) {
+      const uint32_t br = __ballot_sync(~0u, D >= r);
+      if (!br) break;
+      if (D >= r) {
+        const uint32_t q = 16 * (uprev + r - 1), wi = q >> 5, off = q & 31;
+        const uint64_t two = ((uint64_t)mine[wi ^ l] << 32) | (uint64_t)mine[(wi + 1) ^ l];
+        out16[base + __popc(br & lt)] = (uint16_t)(two >> (48 - off));
+      }
+      base += __popc(br);
+    }
+    c = cn;
+    uprev = u;
+  }
+  __syncthreads();
+}
+
 // Units lane `lane` of a stream needs: ceil(bits/16), given its bit total.
 __device__ __forceinline__ uint32_t ihs_lane_units(uint32_t bits) { return (bits + 15) / 16; }
 

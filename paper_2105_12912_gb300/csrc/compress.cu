@@ -636,22 +636,13 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   };
   if (analyze || (sel != SEL_HUFF && eligible && sel != SEL_RLE)) extract_runs();
 
-  // exact sizes: Huffman units from per-lane bit totals
+  // exact sizes: Huffman units from per-lane bit totals; the plan (code lengths in
+  // registers, lane offsets) is kept for the payload
+  IhsPlan plan;
+  uint32_t plan_max = ~0u, plan_units = 0;
   auto huff_units = [&]() {
-    uint32_t bits = 0;
-#pragma unroll 4
-    for (int i = 0; i < kSlots / kEncThreads; i++) {
-      const uint32_t j = tid + kEncThreads * i;
-      if (j < m) bits += __ldg(&clen[s_c[j]]);
-    }
-    s_part[tid] = bits;
-    __syncthreads();
-    if (tid < 32) {
-      const uint32_t u = units_from_partials(s_part);
-      if (tid == 0) s_units[0] = u;
-    }
-    __syncthreads();
-    return s_units[0];
+    plan_units = ihs_plan(s_c, m, 0, clen, s_part, plan, &plan_max);
+    return plan_units;
   };
   auto rlehuff_units = [&]() {
     uint32_t vb = 0, lb = 0;
@@ -792,7 +783,13 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   // fits 16 KB unless a forced Huffman mode meets very long codes; those go direct)
   auto assemble = [&](uint16_t* out16) {
     if (codec == CODEC_HUFF) {
-      const uint32_t u = ihs_encode_block(s_c, m, 0, clen, ccode, out16, s_part);
+      uint32_t u;
+      if (plan_max <= kLaneBitsMax) {
+        ihs_emit(s_c, m, 0, ccode, plan, reinterpret_cast<uint32_t*>(s_rv), out16, s_part);
+        u = plan_units;
+      } else {
+        u = ihs_encode_block(s_c, m, 0, clen, ccode, out16, s_part);
+      }
       if ((u & 1u) && tid == 0) out16[u] = 0;
     } else if (codec == CODEC_RLE_HUFF) {
       const uint32_t vu = s_units[1], lu = s_units[2];
