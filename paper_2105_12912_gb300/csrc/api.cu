@@ -225,6 +225,7 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
   ca.counts = at<uint32_t>(d_ws, L.counts);
   ca.masks = at<uint32_t>(d_ws, L.masks);
   ca.deltas = at<int32_t>(d_ws, L.deltas);
+  ca.block_runs = at<uint16_t>(d_ws, L.runs);
   ca.spin_limit = g_spin_limit;
   ca.all_runs = (select == SEL_RLE || select == SEL_RLE_HUFF) ? 1 : 0;
   prepare_construct_task(task);
@@ -263,6 +264,7 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
   ea.radius = radius;
   ea.select = select;
   ea.codes = ca.codes;
+  ea.block_runs = ca.block_runs;
   ea.lens = ba.lens;
   ea.bcodes = ba.codes;
   ea.mlp_w = opt ? opt->selector_weights : nullptr;

@@ -56,7 +56,7 @@ static_assert(sizeof(DevState) <= kStateStride, "DevState stride");
 constexpr uint64_t kHistBytes = (kNsymCode + kNsymCode + kNsymLen) * 4;
 
 struct FieldLayout {  // offsets from the start of the per-field part
-  uint64_t lens, bcodes, codes, counts, masks, deltas, rec_off, total;
+  uint64_t lens, bcodes, codes, counts, masks, deltas, rec_off, runs, total;
 };
 
 FieldLayout field_layout(const Geom& g) {
@@ -76,6 +76,8 @@ FieldLayout field_layout(const Geom& g) {
   o += a256(4ull * kSlots * g.nblk);
   L.rec_off = o;
   o += a256(8ull * g.nblk);
+  L.runs = o;
+  o += a256(2ull * g.nblk);
   L.total = o;
   return L;
 }
@@ -249,6 +251,7 @@ csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_opti
     ca.counts = at<uint32_t>(fw, FL.counts);
     ca.masks = at<uint32_t>(fw, FL.masks);
     ca.deltas = at<int32_t>(fw, FL.deltas);
+    ca.block_runs = at<uint16_t>(fw, FL.runs);
     ca.spin_limit = kSpinLimit;
     ca.all_runs = (select == SEL_RLE || select == SEL_RLE_HUFF) ? 1 : 0;
     prepare_construct_task(ct[f]);
@@ -282,6 +285,7 @@ csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_opti
     ea.radius = radius;
     ea.select = select;
     ea.codes = ca.codes;
+    ea.block_runs = ca.block_runs;
     ea.lens = ba.lens;
     ea.bcodes = ba.codes;
     ea.mlp_w = opt ? opt->selector_weights : nullptr;

@@ -615,10 +615,13 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   const bool analyze = a.analyze != 0;
   uint32_t nr = 0;
   bool have_runs = false;
-  if (sel != SEL_HUFF || analyze) nr = block_run_heads(s_c, m, s_head, s_woff, s_next);
+  // the run count comes from construction; the run index is built only when runs
+  // are extracted
+  if (sel != SEL_HUFF || analyze) nr = a.block_runs[b];
   const bool eligible = a.all_runs || 4 * nr <= m;
   auto extract_runs = [&]() {
     if (have_runs) return;
+    block_run_heads(s_c, m, s_head, s_woff, s_next);
 #pragma unroll 4
     for (int i = 0; i < kSlots / kEncThreads; i++) {
       const uint32_t j = tid + kEncThreads * i;

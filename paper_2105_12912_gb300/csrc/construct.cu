@@ -171,6 +171,100 @@ __device__ __forceinline__ void flush_hist(const uint32_t* h, int n, uint32_t* g
   }
 }
 
+// ---- edge blocks (not inlined: keeps the full-block paths compact in the
+// instruction cache): prequantize into registers in dense order, stage k, residuals
+// from the staged neighbours.  Returns error bits.
+template <int ND>
+__device__ __noinline__ uint32_t edge_codes(const ConstructArgs& A, uint32_t b, Smem& S, float* in,
+                                            const uint32_t* w, uint32_t m, int32_t* dglob) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const float eb_f = A.st->eb_f, ebx2_f = A.st->ebx2_f, ebx2_r = A.st->ebx2_r;
+  const int32_t r = (int32_t)A.radius;
+  int32_t* s_k = reinterpret_cast<int32_t*>(in);
+  uint32_t err = 0;
+  int32_t kv[kPer];
+  uint32_t pm = 0;
+#pragma unroll
+  for (int i = 0; i < kPer; i++) {
+    const uint32_t j = tid + kThreads * i;
+    kv[i] = 0;
+    if (j < m) {
+      uint32_t zz, yy, xx;
+      if (ND == 1) {
+        zz = 0;
+        yy = 0;
+        xx = j;
+      } else if (ND == 2) {
+        zz = 0;
+        yy = j / w[2];
+        xx = j - yy * w[2];
+      } else {
+        const uint32_t p = w[1] * w[2];
+        zz = j / p;
+        const uint32_t rr = j - zz * p;
+        yy = rr / w[2];
+        xx = rr - yy * w[2];
+      }
+      const uint32_t box = ND == 1 ? xx : (ND == 2 ? yy * 64 + xx : (zz * 16 + yy) * 16 + xx);
+      bool p;
+      err |= prequant(in[box], eb_f, ebx2_f, ebx2_r, kv[i], p);
+      pm |= (uint32_t)p << i;
+    }
+  }
+  __syncthreads();  // box read: it becomes s_k (dense)
+#pragma unroll
+  for (int i = 0; i < kPer; i++) {
+    const uint32_t j = tid + kThreads * i;
+    s_k[j] = kv[i];
+    const uint32_t pb = __ballot_sync(~0u, (pm >> i) & 1u);
+    if (lane == 0) S.patch[j >> 5] = pb;
+  }
+  __syncthreads();
+  const uint32_t sy = w[2], sz = w[1] * w[2];
+#pragma unroll
+  for (int i = 0; i < kPer; i++) {
+    const uint32_t j = tid + kThreads * i;
+    int32_t delta = 0;
+    uint16_t q = 0;
+    const bool inb = j < m;
+    (void)delta;
+    if (inb) {
+      uint32_t zz = 0, yy = 0, xx = j;
+      if (ND == 2) {
+        yy = j / w[2];
+        xx = j - yy * w[2];
+      } else if (ND == 3) {
+        zz = j / sz;
+        const uint32_t rr = j - zz * sz;
+        yy = rr / w[2];
+        xx = rr - yy * w[2];
+      }
+      const bool hx = (xx % Chunk<ND>::x) != 0;
+      const bool hy = ND >= 2 && (yy % Chunk<ND>::y) != 0;
+      const bool hz = ND >= 3 && (zz % Chunk<ND>::z) != 0;
+      int32_t p;
+      if (ND == 1) {
+        p = hx ? s_k[j - 1] : 0;
+      } else if (ND == 2) {
+        p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) - ((hx && hy) ? s_k[j - sy - 1] : 0);
+      } else {
+        p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) + (hz ? s_k[j - sz] : 0) -
+            ((hx && hy) ? s_k[j - sy - 1] : 0) - ((hx && hz) ? s_k[j - sz - 1] : 0) -
+            ((hy && hz) ? s_k[j - sz - sy] : 0) + ((hx && hy && hz) ? s_k[j - sz - sy - 1] : 0);
+      }
+      delta = s_k[j] - p;
+      q = (delta > -r && delta < r) ? (uint16_t)(delta + r) : (uint16_t)0;
+      atomicAdd(&S.hc[q], 1u);
+    }
+    S.c[j] = q;  // zero beyond m
+    if (inb && q == 0) dglob[j] = delta;
+    const uint32_t ob = __ballot_sync(~0u, inb && q == 0);
+    if (lane == 0) S.outl[j >> 5] = ob;
+  }
+  __syncthreads();
+    return err;
+}
+
 // ---- one tile ------------------------------------------------------------------------
 // Codes, records and histogram updates of codec block b from the box in `in` (which
 // this call overwrites with k and outlier deltas).  Thread 0 adds the tile's record
@@ -312,88 +406,7 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, Smem& S, float*
     }
     __syncthreads();
   } else {
-    // ---- edge blocks: prequantize into registers (dense order), stage k, residuals
-    // from the staged neighbours ---------------------------------------------------
-    int32_t kv[kPer];
-    uint32_t pm = 0;
-#pragma unroll
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t j = tid + kThreads * i;
-      kv[i] = 0;
-      if (j < m) {
-        uint32_t zz, yy, xx;
-        if (ND == 1) {
-          zz = 0;
-          yy = 0;
-          xx = j;
-        } else if (ND == 2) {
-          zz = 0;
-          yy = j / w[2];
-          xx = j - yy * w[2];
-        } else {
-          const uint32_t p = w[1] * w[2];
-          zz = j / p;
-          const uint32_t rr = j - zz * p;
-          yy = rr / w[2];
-          xx = rr - yy * w[2];
-        }
-        const uint32_t box = ND == 1 ? xx : (ND == 2 ? yy * 64 + xx : (zz * 16 + yy) * 16 + xx);
-        bool p;
-        err |= prequant(in[box], eb_f, ebx2_f, ebx2_r, kv[i], p);
-        pm |= (uint32_t)p << i;
-      }
-    }
-    __syncthreads();  // box read: it becomes s_k (dense)
-#pragma unroll
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t j = tid + kThreads * i;
-      s_k[j] = kv[i];
-      const uint32_t pb = __ballot_sync(~0u, (pm >> i) & 1u);
-      if (lane == 0) S.patch[j >> 5] = pb;
-    }
-    __syncthreads();
-    const uint32_t sy = w[2], sz = w[1] * w[2];
-#pragma unroll
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t j = tid + kThreads * i;
-      int32_t delta = 0;
-      uint16_t q = 0;
-      const bool inb = j < m;
-      (void)delta;
-      if (inb) {
-        uint32_t zz = 0, yy = 0, xx = j;
-        if (ND == 2) {
-          yy = j / w[2];
-          xx = j - yy * w[2];
-        } else if (ND == 3) {
-          zz = j / sz;
-          const uint32_t rr = j - zz * sz;
-          yy = rr / w[2];
-          xx = rr - yy * w[2];
-        }
-        const bool hx = (xx % Chunk<ND>::x) != 0;
-        const bool hy = ND >= 2 && (yy % Chunk<ND>::y) != 0;
-        const bool hz = ND >= 3 && (zz % Chunk<ND>::z) != 0;
-        int32_t p;
-        if (ND == 1) {
-          p = hx ? s_k[j - 1] : 0;
-        } else if (ND == 2) {
-          p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) - ((hx && hy) ? s_k[j - sy - 1] : 0);
-        } else {
-          p = (hx ? s_k[j - 1] : 0) + (hy ? s_k[j - sy] : 0) + (hz ? s_k[j - sz] : 0) -
-              ((hx && hy) ? s_k[j - sy - 1] : 0) - ((hx && hz) ? s_k[j - sz - 1] : 0) -
-              ((hy && hz) ? s_k[j - sz - sy] : 0) + ((hx && hy && hz) ? s_k[j - sz - sy - 1] : 0);
-        }
-        delta = s_k[j] - p;
-        q = (delta > -r && delta < r) ? (uint16_t)(delta + r) : (uint16_t)0;
-        atomicAdd(&S.hc[q], 1u);
-      }
-      S.c[j] = q;  // zero beyond m
-      if (inb && q == 0) dglob[j] = delta;
-      const uint32_t ob = __ballot_sync(~0u, inb && q == 0);
-      if (lane == 0) S.outl[j >> 5] = ob;
-    }
-    __syncthreads();
+    err |= edge_codes<ND>(A, b, S, in, w, m, dglob);
   }
 
   // ---- run heads and record counts: one block reduction of packed counts -------
@@ -410,6 +423,7 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, Smem& S, float*
   const uint32_t nruns = (uint32_t)(tot & kF);
   if (tid == 0) {
     A.counts[b] = (n_out << 16) | n_patch;
+    A.block_runs[b] = (uint16_t)nruns;
     n_rec_acc += n_out + n_patch;
     n_patch_acc += n_patch;
     // codes to the block-major stream (whole 4096-slot block, zero tail) and the
@@ -469,6 +483,7 @@ __device__ __forceinline__ int find_field(const uint32_t* tile0, int nfields, ui
 // entry passes the task by value (`one`, tasks == nullptr, ntiles = its block
 // count); batches pass a device table and tile0[f], the first global tile of field
 // f (tile0[nfields] = ntiles).
+template <int ND>  // 1, 2, 3; 0 = any (batches of mixed dimensionality)
 __global__ __launch_bounds__(kThreads, 3) void construct_kernel(const __grid_constant__ ConstructTask one,
                                                              const ConstructTask* __restrict__ tasks,
                                                              const uint32_t* __restrict__ tile0, int nfields,
@@ -544,8 +559,8 @@ __global__ __launch_bounds__(kThreads, 3) void construct_kernel(const __grid_con
     }
     __syncthreads();
     if (s_fail) break;
-    if (A.g.ndim == 1) process_tile<1>(A, b, S, S.in[cur], n_rec_acc, n_patch_acc);
-    else if (A.g.ndim == 2) process_tile<2>(A, b, S, S.in[cur], n_rec_acc, n_patch_acc);
+    if (ND == 1 || (ND == 0 && A.g.ndim == 1)) process_tile<1>(A, b, S, S.in[cur], n_rec_acc, n_patch_acc);
+    else if (ND == 2 || (ND == 0 && A.g.ndim == 2)) process_tile<2>(A, b, S, S.in[cur], n_rec_acc, n_patch_acc);
     else process_tile<3>(A, b, S, S.in[cur], n_rec_acc, n_patch_acc);
     __syncthreads();
     cur ^= 1;
@@ -636,8 +651,11 @@ int construct_grid(uint32_t ntiles) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(construct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ, construct_kernel, kThreads, sizeof(Smem));
+    cudaFuncSetAttribute(construct_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    cudaFuncSetAttribute(construct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    cudaFuncSetAttribute(construct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    cudaFuncSetAttribute(construct_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ, construct_kernel<0>, kThreads, sizeof(Smem));
     if (g_sms <= 0) g_sms = 1;
     if (g_occ <= 0) g_occ = 1;
   }
@@ -648,8 +666,9 @@ int construct_grid(uint32_t ntiles) {
 cudaError_t launch_construct(const ConstructTask& one, uint32_t* ticket, cudaStream_t s) {
   const int grid = construct_grid(one.a.g.nblk);
   trace_begin(K_CONSTRUCT, s);
-  construct_kernel<<<grid, kThreads, sizeof(Smem), s>>>(one, nullptr, nullptr, 1, one.a.g.nblk, ticket,
-                                                        one.a.spin_limit);
+  const int nd = one.a.g.ndim;
+  auto k = nd == 1 ? construct_kernel<1> : (nd == 2 ? construct_kernel<2> : construct_kernel<3>);
+  k<<<grid, kThreads, sizeof(Smem), s>>>(one, nullptr, nullptr, 1, one.a.g.nblk, ticket, one.a.spin_limit);
   trace_end(K_CONSTRUCT, s);
   return cudaGetLastError();
 }
@@ -661,8 +680,8 @@ cudaError_t launch_construct_batch(const ConstructTask* d_tasks, const uint32_t*
   memset(&dummy, 0, sizeof(dummy));
   if (grid <= 0) grid = construct_grid(ntiles);
   trace_begin(K_CONSTRUCT, s);
-  construct_kernel<<<grid, kThreads, sizeof(Smem), s>>>(dummy, d_tasks, d_tile0, nfields, ntiles, ticket,
-                                                        spin_limit);
+  construct_kernel<0><<<grid, kThreads, sizeof(Smem), s>>>(dummy, d_tasks, d_tile0, nfields, ntiles, ticket,
+                                                           spin_limit);
   trace_end(K_CONSTRUCT, s);
   return cudaGetLastError();
 }

@@ -47,7 +47,7 @@ inline bool make_geom(int ndim, const uint64_t* dims, Geom& g) {
 struct Layout {
   uint64_t st, hist_code, hist_val, hist_len, lb_e, zero_end;
   uint64_t lens, bcodes, blk_off, rec_start, tabs, codes, runl, dec_total;
-  uint64_t counts, masks, deltas, rec_off, total;
+  uint64_t counts, masks, deltas, rec_off, runs, total;
 };
 
 inline Layout layout(const Geom& g) {
@@ -88,6 +88,8 @@ inline Layout layout(const Geom& g) {
   o += a256(4ull * kSlots * g.nblk);
   L.rec_off = o;
   o += a256(8ull * g.nblk);
+  L.runs = o;
+  o += a256(2ull * g.nblk);
   L.total = o;
   return L;
 }

@@ -22,6 +22,7 @@ struct ConstructArgs {
   uint32_t* counts;    // [nblk] (outliers << 16) | patches of each block
   uint32_t* masks;     // [nblk][256] patch bit words [128], then outlier bit words [128]
   int32_t* deltas;     // [nblk * 4096] outlier residuals by slot (written at outliers only)
+  uint16_t* block_runs;  // [nblk] runs of equal codes in each block
   uint32_t spin_limit;
   int all_runs;        // every block's runs feed the run books (forced run codecs)
 };
@@ -88,6 +89,7 @@ struct EncodeArgs {
   uint32_t radius;
   int select;
   const uint16_t* codes;
+  const uint16_t* block_runs;  // [nblk] runs per block (from construction)
   const uint8_t* lens;
   const uint64_t* bcodes;
   const float* mlp_w;
