@@ -562,8 +562,42 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) 
         if (y < w[1]) __stcs(&out[base + (uint64_t)y * nx], scale(v[i], ebx2));
       }
     }
+  } else if (m == (uint32_t)kSlots) {
+    // full 16^3 block: thread (x, y) takes the z column -- z sums in registers, x
+    // sums by shuffles -- then, after one exchange through shared memory, thread
+    // (x, z) takes the y column, adds along y in registers and stores its row
+    // segment (16 consecutive floats per half-warp)
+    const uint32_t x = tid & 15, y = tid >> 4;
+    int32_t v[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = s_q[(i * 16 + y) * 16 + x];
+#pragma unroll
+    for (int i = 1; i < 16; i++)
+      if (i & 7) v[i] += v[i - 1];
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        const int32_t u = __shfl_up_sync(~0u, v[i], o);
+        if ((x & 7) >= (uint32_t)o) v[i] += u;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; i++) s_q[(i * 16 + y) * 16 + x] = v[i];
+    __syncthreads();
+    const uint32_t z = tid >> 4;
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = s_q[(z * 16 + i) * 16 + x];
+#pragma unroll
+    for (int i = 1; i < 16; i++)
+      if (i & 7) v[i] += v[i - 1];
+    const uint64_t base = ((uint64_t)(org[0] + z) * ny + org[1]) * nx + org[2] + x;
+#pragma unroll
+    for (int i = 0; i < 16; i++) __stcs(&out[base + (uint64_t)i * nx], scale(v[i], ebx2));
   } else {
-    // z sums in registers, x sums by shuffles, y sums through shared memory
+    // edge block: z sums in registers, x sums by shuffles, y sums through shared
+    // memory
     const uint32_t x = tid & 15, y = tid >> 4;
     const bool in_xy = x < w[2] && y < w[1];
     int32_t v[16];
