@@ -271,6 +271,18 @@ __device__ __forceinline__ uint32_t prequant(float x, float eb_f, float ebx2_f, 
   return 0;
 }
 
+// The common case of prequant with no branches: k0 is final when |x / 2eb| < 2^23
+// and fl32(k0 * 2eb) lies strictly within eb of x (the rounded difference then
+// decides exactly).  Returns false when prequant must decide instead (non-finite
+// or out-of-range input, a tie at exactly eb, a miss needing the neighbour or a
+// patch); k then holds no meaningful value.
+__device__ __forceinline__ bool prequant_fast(float x, float eb_f, float ebx2_f, float ebx2_r, int32_t& k) {
+  const float v = __fmul_rn(x, ebx2_r);
+  k = __float2int_rn(v);
+  const float s = __fsub_rn(x, __fmul_rn(__int2float_rn(k), ebx2_f));
+  return (fabsf(v) < 8388608.0f) & (fabsf(s) < eb_f);
+}
+
 // Binary logarithm in Q16 by bit-by-bit squaring of the mantissa (integer only).
 __device__ __forceinline__ uint32_t log2_q16(uint64_t v) {
   if (v == 0) return 0;

@@ -48,7 +48,7 @@ __global__ void abs_params_kernel(DevState* st, double eb) {
 
 // Grid-stride min/max with float4 loads; non-finite values are flagged.  The last CTA
 // to finish derives the error bound.
-__device__ void range_body(const float* __restrict__ x, uint64_t n, DevState* st, int mode, double eb,
+__device__ __forceinline__ void range_body(const float* __restrict__ x, uint64_t n, DevState* st, int mode, double eb,
                            uint32_t cta, uint32_t nctas) {
   __shared__ uint32_t s_red[2][33];
   __shared__ bool s_last;

@@ -306,17 +306,24 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, Smem& S, float*
     if (ND == 1) {
       // thread t: 16 consecutive elements (a warp covers two whole 256-chunks)
       int32_t k[16];
-      uint32_t pm = 0;
+      uint32_t pm = 0, slow = 0;
       const float4* in4 = reinterpret_cast<const float4*>(in) + 4 * tid;
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         const float4 v = in4[i];
         const float f[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-          bool p;
-          err |= prequant(f[c], eb_f, ebx2_f, ebx2_r, k[4 * i + c], p);
-          pm |= (uint32_t)p << (4 * i + c);
+        for (int c = 0; c < 4; c++)
+          slow |= (uint32_t)!prequant_fast(f[c], eb_f, ebx2_f, ebx2_r, k[4 * i + c]) << (4 * i + c);
+      }
+      if (__any_sync(~0u, slow != 0)) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          if ((slow >> i) & 1u) {
+            bool p;
+            err |= prequant(in[16 * tid + i], eb_f, ebx2_f, ebx2_r, k[i], p);
+            pm |= (uint32_t)p << i;
+          }
         }
       }
       const int32_t prev = __shfl_up_sync(~0u, k[15], 1);
@@ -341,12 +348,19 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, Smem& S, float*
       // thread t: column xx = t & 63 of the 16-row chunk band t >> 6
       const uint32_t xx = tid & 63, ry = tid >> 6;
       int32_t k[16];
-      uint32_t pm = 0;
+      uint32_t pm = 0, slow = 0;
 #pragma unroll
-      for (int i = 0; i < 16; i++) {
-        bool p;
-        err |= prequant(in[(16 * ry + i) * 64 + xx], eb_f, ebx2_f, ebx2_r, k[i], p);
-        pm |= (uint32_t)p << i;
+      for (int i = 0; i < 16; i++)
+        slow |= (uint32_t)!prequant_fast(in[(16 * ry + i) * 64 + xx], eb_f, ebx2_f, ebx2_r, k[i]) << i;
+      if (__any_sync(~0u, slow != 0)) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          if ((slow >> i) & 1u) {
+            bool p;
+            err |= prequant(in[(16 * ry + i) * 64 + xx], eb_f, ebx2_f, ebx2_r, k[i], p);
+            pm |= (uint32_t)p << i;
+          }
+        }
       }
       const bool anyp = __any_sync(~0u, pm != 0);
 #pragma unroll
@@ -369,12 +383,19 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, Smem& S, float*
       // registers and shuffles, the y difference through shared memory
       const uint32_t xx = tid & 15, yy = tid >> 4;
       int32_t k[16];
-      uint32_t pm = 0;
+      uint32_t pm = 0, slow = 0;
 #pragma unroll
-      for (int i = 0; i < 16; i++) {
-        bool p;
-        err |= prequant(in[(i * 16 + yy) * 16 + xx], eb_f, ebx2_f, ebx2_r, k[i], p);
-        pm |= (uint32_t)p << i;
+      for (int i = 0; i < 16; i++)
+        slow |= (uint32_t)!prequant_fast(in[(i * 16 + yy) * 16 + xx], eb_f, ebx2_f, ebx2_r, k[i]) << i;
+      if (__any_sync(~0u, slow != 0)) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          if ((slow >> i) & 1u) {
+            bool p;
+            err |= prequant(in[(i * 16 + yy) * 16 + xx], eb_f, ebx2_f, ebx2_r, k[i], p);
+            pm |= (uint32_t)p << i;
+          }
+        }
       }
 #pragma unroll
       for (int i = 15; i > 0; i--)
