@@ -170,7 +170,38 @@ csz_status csz_batch_results(csz_batch* batch, uint64_t* h_bytes, int* h_status,
 /* The construction grid the autotuner chose and the batch times (ms) it measured
    with 1..4 resident CTAs per SM (0 where not tried). */
 csz_status csz_batch_info(const csz_batch* batch, int* construct_grid, double* tuned_ms);
-/* Where the last failing csz_batch_create call stopped and the CUDA error it met. */
+/*
+ * Batched decompression, the counterpart of the above: one launch per stage (header
+ * checks, set-up, entropy decoding, run expansion, reconstruction) for all fields,
+ * captured into a CUDA graph at csz_batch_dec_create and replayed by
+ * csz_batch_decompress.  Each field names its archive (archive_bytes readable
+ * bytes), its output (out_cap_elems floats) and the shape it must decode to; the
+ * headers are read and checked on the device at every replay, so the archives'
+ * contents may change between replays as long as each keeps its shape.  A field
+ * whose header or data fail validation gets CSZ_E_CORRUPT (CSZ_E_TIMEOUT for an
+ * expired wait) in csz_batch_dec_results without disturbing the others.  Buffers
+ * and workspace stay bound until csz_batch_dec_destroy.
+ */
+typedef struct {
+  const uint8_t* d_archive;
+  size_t archive_bytes;
+  float* d_out;
+  uint64_t out_cap_elems;
+  int ndim;
+  uint64_t dims[3];
+} csz_dfield;
+
+typedef struct csz_batch_dec csz_batch_dec;
+
+size_t csz_batch_dec_workspace_bytes(int nfields, const csz_dfield* fields);
+csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_workspace,
+                                size_t workspace_bytes, void* stream, csz_batch_dec** batch);
+csz_status csz_batch_decompress(csz_batch_dec* batch, void* stream);
+csz_status csz_batch_dec_results(csz_batch_dec* batch, int* h_status, void* stream);
+void csz_batch_dec_destroy(csz_batch_dec* batch);
+
+/* Where the last failing csz_batch_create / csz_batch_dec_create call stopped and
+   the CUDA error it met. */
 const char* csz_batch_last_error(void);
 void csz_batch_destroy(csz_batch* batch);
 

@@ -22,6 +22,11 @@ class csz_field(C.Structure):
                 ("eb", C.c_double), ("d_archive", C.c_void_p), ("archive_cap", C.c_size_t)]
 
 
+class csz_dfield(C.Structure):
+    _fields_ = [("d_archive", C.c_void_p), ("archive_bytes", C.c_size_t), ("d_out", C.c_void_p),
+                ("out_cap_elems", C.c_uint64), ("ndim", C.c_int), ("dims", C.c_uint64 * 3)]
+
+
 class CszError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
@@ -60,6 +65,12 @@ SIGNATURES = {
     "csz_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "csz_batch_destroy": (None, [C.c_void_p]),
     "csz_batch_last_error": (C.c_char_p, []),
+    "csz_batch_dec_workspace_bytes": (C.c_size_t, [C.c_int, C.POINTER(csz_dfield)]),
+    "csz_batch_dec_create": (C.c_int, [C.c_int, C.POINTER(csz_dfield), C.c_void_p, C.c_size_t, C.c_void_p,
+                                       C.POINTER(C.c_void_p)]),
+    "csz_batch_decompress": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "csz_batch_dec_results": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_void_p]),
+    "csz_batch_dec_destroy": (None, [C.c_void_p]),
     "csz_status_string": (C.c_char_p, [C.c_int]),
     "csz_kernel_count": (C.c_int, []),
     "csz_kernel_name": (C.c_char_p, [C.c_int]),

@@ -222,6 +222,61 @@ class BatchCompressor:
             self._h = None
 
 
+class BatchDecompressor:
+    """Decompresses a fixed list of archives into fields of known shapes together
+    (one launch per stage, replayed as a CUDA graph).  The archive tensors are
+    referenced: overwrite them in place (same shapes) to decompress new data."""
+
+    def __init__(self, archives, shapes, archive_bytes=None, outs=None, stream=None):
+        n = len(archives)
+        if n == 0 or len(shapes) != n:
+            raise ValueError("one shape per archive")
+        dev = archives[0].device
+        self.archives = list(archives)
+        self.outs = list(outs) if outs is not None else [torch.empty(tuple(sh), dtype=torch.float32, device=dev)
+                                                          for sh in shapes]
+        arr = (L.csz_dfield * n)()
+        for i, (a, sh, o) in enumerate(zip(self.archives, shapes, self.outs)):
+            if not (a.is_cuda and a.dtype == torch.uint8):
+                raise ValueError("archives must be uint8 CUDA tensors")
+            if not (o.is_cuda and o.dtype == torch.float32 and o.is_contiguous()):
+                raise ValueError("outputs must be contiguous float32 CUDA tensors")
+            f = arr[i]
+            f.d_archive = a.data_ptr()
+            f.archive_bytes = int(archive_bytes[i]) if archive_bytes is not None else a.numel()
+            f.d_out = o.data_ptr()
+            f.out_cap_elems = o.numel()
+            f.ndim = len(sh)
+            for k, d in enumerate(sh):
+                f.dims[k] = int(d)
+        self._arr = arr
+        wsb = int(L.lib().csz_batch_dec_workspace_bytes(n, arr))
+        if wsb == 0:
+            raise ValueError("invalid shape in batch")
+        self.workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        h = C.c_void_p()
+        st = L.lib().csz_batch_dec_create(n, arr, C.c_void_p(self.workspace.data_ptr()), wsb, _stream_ptr(stream),
+                                          C.byref(h))
+        if st != L.OK:
+            raise L.CszError(st, "csz_batch_dec_create (" + L.lib().csz_batch_last_error().decode() + ")")
+        self._h = h
+        self.n = n
+
+    def run(self, stream=None):
+        _check(L.lib().csz_batch_decompress(self._h, _stream_ptr(stream)), "csz_batch_decompress")
+
+    def results(self, stream=None):
+        stats = (C.c_int * self.n)()
+        L.lib().csz_batch_dec_results(self._h, stats, _stream_ptr(stream))
+        return [int(v) for v in stats]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            L.lib().csz_batch_dec_destroy(h)
+            self._h = None
+
+
 # ---------------------------------------------------------------------------------
 # learned selector: training rows, inference, gradient, training
 # ---------------------------------------------------------------------------------

@@ -110,6 +110,9 @@ void trace_resume(bool on) { g_trace.on = on; }
 void trace_count_batch() {
   for (int k : {K_RANGE, K_CONSTRUCT, K_CODEBOOK, K_ENCODE}) g_trace.launches[k]++;
 }
+void trace_count_decode_batch() {
+  for (int k : {K_DEC_SETUP, K_STREAM_DECODE, K_RLE_EXPAND, K_RECONSTRUCT}) g_trace.launches[k]++;
+}
 }  // namespace cszp
 
 extern "C" {
@@ -366,6 +369,7 @@ csz_status csz_decompress(const uint8_t* d_ar, size_t bytes, float* d_out, uint6
   DevState* st = at<DevState>(d_ws, L.st);
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return CSZ_E_CUDA;
   DecodeArgs da;
+  memset(&da, 0, sizeof(da));
   da.g = g;
   da.st = st;
   da.ar = d_ar;

@@ -441,6 +441,237 @@ csz_status csz_batch_info(const csz_batch* b, int* construct_grid, double* tuned
   return CSZ_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// batched decompression
+// ---------------------------------------------------------------------------------
+}  // extern "C"
+
+struct csz_batch_dec {
+  int nfields = 0;
+  unsigned char* zero_base = nullptr;
+  uint64_t zero_bytes = 0;
+  DevState* states = nullptr;
+  DecodeBatchLaunch launch{};
+  DecodeArgs* d_tasks = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+struct DecFieldLayout {
+  uint64_t blk_off, rec_start, tabs, codes, runl, total;
+};
+
+DecFieldLayout dec_field_layout(const Geom& g) {
+  DecFieldLayout L;
+  uint64_t o = 0;
+  L.blk_off = o;
+  o += a256(8ull * (g.nblk + 1));
+  L.rec_start = o;
+  o += a256(4ull * (g.nblk + 1));
+  L.tabs = o;
+  o += a256(3 * sizeof(DecTab));
+  L.codes = o;
+  o += a256(2ull * kSlots * g.nblk);
+  L.runl = o;
+  o += a256(2ull * kSlots * g.nblk);
+  L.total = o;
+  return L;
+}
+
+struct DecBatchLayout {
+  uint64_t states, zero_end, tasks, setup0, chunk0, tile0;
+  std::vector<uint64_t> field_at;
+  uint64_t total;
+};
+
+DecBatchLayout dec_batch_layout(const std::vector<Geom>& gs) {
+  const uint64_t F = gs.size();
+  DecBatchLayout B;
+  uint64_t o = 0;
+  B.states = o;
+  o += kStateStride * F;
+  B.zero_end = o;
+  o = a256(o);
+  B.tasks = o;
+  o += a256(sizeof(DecodeArgs) * F);
+  B.setup0 = o;
+  o += a256(4 * (F + 1));
+  B.chunk0 = o;
+  o += a256(4 * (F + 1));
+  B.tile0 = o;
+  o += a256(4 * (F + 1));
+  B.field_at.resize(F);
+  for (uint64_t f = 0; f < F; f++) {
+    B.field_at[f] = o;
+    o += dec_field_layout(gs[f]).total;
+  }
+  B.total = o;
+  return B;
+}
+
+csz_status check_dfields(int n, const csz_dfield* fields, std::vector<Geom>& gs) {
+  if (n <= 0 || !fields) return CSZ_E_ARG;
+  gs.resize(n);
+  uint64_t tiles = 0;
+  for (int f = 0; f < n; f++) {
+    if (!make_geom(fields[f].ndim, fields[f].dims, gs[f])) return CSZ_E_ARG;
+    tiles += gs[f].nblk;
+  }
+  if (tiles >= (1ull << 32)) return CSZ_E_ARG;
+  return CSZ_OK;
+}
+
+cudaError_t dec_enqueue(const csz_batch_dec* b, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, s);
+  if (e != cudaSuccess) return e;
+  // the header pass rewrites the tables' header-derived fields every run
+  return launch_decode_batch(b->launch, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t csz_batch_dec_workspace_bytes(int nfields, const csz_dfield* fields) {
+  std::vector<Geom> gs;
+  if (check_dfields(nfields, fields, gs) != CSZ_OK) return 0;
+  return (size_t)dec_batch_layout(gs).total;
+}
+
+csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_ws, size_t ws_bytes, void* stream,
+                                csz_batch_dec** out) {
+  if (!out || !d_ws) return CSZ_E_ARG;
+  *out = nullptr;
+  std::vector<Geom> gs;
+  csz_status r = check_dfields(nfields, fields, gs);
+  if (r != CSZ_OK) return r;
+  for (int f = 0; f < nfields; f++) {
+    if (!fields[f].d_archive || !fields[f].d_out) return CSZ_E_ARG;
+    if (fields[f].out_cap_elems < gs[f].nelem) return CSZ_E_CAPACITY;
+  }
+  const DecBatchLayout B = dec_batch_layout(gs);
+  if (ws_bytes < B.total) return CSZ_E_CAPACITY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* ws = static_cast<unsigned char*>(d_ws);
+  csz_batch_dec* b = new (std::nothrow) csz_batch_dec();
+  if (!b) return CSZ_E_ARG;
+  b->nfields = nfields;
+  b->zero_base = ws;
+  b->zero_bytes = B.zero_end;
+  b->states = at<DevState>(ws, B.states);
+  b->d_tasks = at<DecodeArgs>(ws, B.tasks);
+  std::vector<DecodeArgs> tasks(nfields);
+  std::vector<uint32_t> setup0(nfields + 1), chunk0(nfields + 1), tile0(nfields + 1);
+  uint32_t nsetup = 0, nchunks = 0, ntiles = 0;
+  for (int f = 0; f < nfields; f++) {
+    const Geom& g = gs[f];
+    const DecFieldLayout FL = dec_field_layout(g);
+    unsigned char* fw = ws + B.field_at[f];
+    DecodeArgs& a = tasks[f];
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.st = reinterpret_cast<DevState*>(ws + B.states + kStateStride * f);
+    a.ar = fields[f].d_archive;
+    a.bytes = fields[f].archive_bytes;
+    a.blk_off = at<uint64_t>(fw, FL.blk_off);
+    a.rec_start = at<uint32_t>(fw, FL.rec_start);
+    a.tabs = at<DecTab>(fw, FL.tabs);
+    a.codes = at<uint16_t>(fw, FL.codes);
+    a.runv = a.codes;
+    a.runl = at<uint16_t>(fw, FL.runl);
+    a.out = fields[f].d_out;
+    a.dead = 1;  // until the header pass accepts the field
+    setup0[f] = nsetup;
+    uint64_t rec_ctas = (g.nelem + 32767) / 32768;
+    if (rec_ctas < 1) rec_ctas = 1;
+    if (rec_ctas > 256) rec_ctas = 256;
+    nsetup += 4 + (uint32_t)rec_ctas;
+    chunk0[f] = nchunks;
+    nchunks += (g.nblk + kStreamWarpsPerCta - 1) / kStreamWarpsPerCta;
+    tile0[f] = ntiles;
+    ntiles += g.nblk;
+  }
+  setup0[nfields] = nsetup;
+  chunk0[nfields] = nchunks;
+  tile0[nfields] = ntiles;
+  cudaError_t e = upload(b->d_tasks, tasks, s);
+  if (e == cudaSuccess) e = upload(at<uint32_t>(ws, B.setup0), setup0, s);
+  if (e == cudaSuccess) e = upload(at<uint32_t>(ws, B.chunk0), chunk0, s);
+  if (e == cudaSuccess) e = upload(at<uint32_t>(ws, B.tile0), tile0, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (failed(e, "decompression table upload")) {
+    delete b;
+    return CSZ_E_CUDA;
+  }
+  b->launch = DecodeBatchLaunch{b->d_tasks, nfields, at<uint32_t>(ws, B.setup0), nsetup,
+                                at<uint32_t>(ws, B.chunk0), nchunks, at<uint32_t>(ws, B.tile0), ntiles};
+  // capture once on a private stream
+  const bool tracing = trace_suspend();
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cap = nullptr;
+  const char* step = "capture stream";
+  e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    step = "begin capture";
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  }
+  if (e == cudaSuccess) {
+    const cudaError_t e2 = dec_enqueue(b, cap);
+    e = cudaStreamEndCapture(cap, &graph);
+    step = "end capture";
+    if (e == cudaSuccess && e2 != cudaSuccess) {
+      e = e2;
+      step = "captured launches";
+    }
+  }
+  if (e == cudaSuccess) {
+    step = "instantiate";
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (cap) cudaStreamDestroy(cap);
+  trace_resume(tracing);
+  if (failed(e, step)) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    delete b;
+    return CSZ_E_CUDA;
+  }
+  *out = b;
+  return CSZ_OK;
+}
+
+csz_status csz_batch_decompress(csz_batch_dec* b, void* stream) {
+  if (!b || !b->exec) return CSZ_E_ARG;
+  if (cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return CSZ_E_CUDA;
+  trace_count_decode_batch();
+  return CSZ_OK;
+}
+
+csz_status csz_batch_dec_results(csz_batch_dec* b, int* h_status, void* stream) {
+  if (!b) return CSZ_E_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<unsigned char> buf(kStateStride * b->nfields);
+  if (cudaMemcpyAsync(buf.data(), b->states, buf.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CSZ_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  csz_status worst = CSZ_OK;
+  for (int f = 0; f < b->nfields; f++) {
+    DevState st;
+    memcpy(&st, buf.data() + kStateStride * f, sizeof(st));
+    const csz_status r = fold(st.status);
+    if (h_status) h_status[f] = (int)r;
+    if (r != CSZ_OK && worst == CSZ_OK) worst = r;
+  }
+  return worst;
+}
+
+void csz_batch_dec_destroy(csz_batch_dec* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  delete b;
+}
+
 const char* csz_batch_last_error(void) {
   static char buf[160];
   snprintf(buf, sizeof(buf), "%s: %s", g_fail_step, cudaGetErrorString(g_fail_err));

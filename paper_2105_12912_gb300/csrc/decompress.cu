@@ -20,6 +20,7 @@ __device__ __forceinline__ void flag(DevState* st, uint32_t bits) { atomicOr(&st
 // archive validation and offsets
 // =================================================================================
 __device__ void dec_prep_body(const DecodeArgs& a) {
+  if (a.dead) return;
   __shared__ uint64_t s_scan[33];
   __shared__ uint32_t s_nc[3];
   const int tid = threadIdx.x;
@@ -50,6 +51,7 @@ __device__ void dec_prep_body(const DecodeArgs& a) {
 }
 
 __device__ void dec_records_body(const DecodeArgs& a, uint32_t cta, uint32_t nctas) {
+  if (a.dead) return;
   const uint32_t* rec = reinterpret_cast<const uint32_t*>(a.ar + a.off_rec);
   const uint64_t nslots = (uint64_t)a.g.nblk * kSlots;
   const uint64_t n = a.n_rec > (uint64_t)a.g.nblk + 1 ? a.n_rec : (uint64_t)a.g.nblk + 1;
@@ -83,6 +85,7 @@ __device__ void dec_records_body(const DecodeArgs& a, uint32_t cta, uint32_t nct
 // One CTA per book: lengths from the archive, Kraft check, canonical tables and a
 // 12-bit lookup table.
 __device__ void dec_tables_body(const DecodeArgs& a, int book) {
+  if (a.dead) return;
   __shared__ uint8_t s_len[kNsymLen];
   __shared__ uint16_t s_wcnt[(kNsymLen / 32) * (kMaxLen + 1)];
   __shared__ CanonSmem cs;
@@ -286,17 +289,19 @@ __device__ bool ihs_decode_warp(const uint16_t* __restrict__ in, uint32_t avail,
   return !__any_sync(~0u, bad);
 }
 
-constexpr int kStreamWarps = 16;
+constexpr int kStreamWarps = kStreamWarpsPerCta;
 
 // Entropy decoding, persistent: each CTA stages the lookup tables of the books the
 // archive uses in shared memory once, then its warps take codec blocks from a ticket;
 // a warp decodes a Huffman block's code stream, or an RLE+Huffman block's value
 // stream and then its length stream (runs go to the workspace run arrays).
-__global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_kernel(DecodeArgs a) {
+// Blocks come from the field's ticket (b_end == 0) or, in batches, warp i of the
+// CTA takes block b_begin + i if below b_end.
+__device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32_t b_end) {
   extern __shared__ __align__(16) uint32_t s_luts[];  // the present books' tables
   __shared__ unsigned long long s_first[kMaxLen + 1], s_limit[kMaxLen + 1];
   __shared__ uint32_t s_off[kMaxLen + 1], s_count[kMaxLen + 1];
-  if (a.st->status & ERR_CORRUPT) return;
+  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
   const bool huff = (a.flags & 1u) != 0, rle = (a.flags & 2u) != 0;
   uint32_t* lut_code = s_luts;
   uint32_t* lut_val = s_luts + (huff ? (1 << kLutBits) : 0);
@@ -316,11 +321,17 @@ __global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_kernel(Decode
   }
   __syncthreads();
   const bool lane0 = (threadIdx.x & 31) == 0;
-  while (true) {
+  const bool ticketed = b_end == 0;
+  for (uint32_t round = 0;; round++) {
     uint32_t b = 0;
-    if (lane0) b = atomicAdd(&a.st->ticket_decode, 1u);
-    b = __shfl_sync(~0u, b, 0);
-    if (b >= a.g.nblk) break;
+    if (ticketed) {
+      if (lane0) b = atomicAdd(&a.st->ticket_decode, 1u);
+      b = __shfl_sync(~0u, b, 0);
+      if (b >= a.g.nblk) break;
+    } else {
+      b = b_begin + (threadIdx.x >> 5);
+      if (round > 0 || b >= b_end) break;
+    }
     const int codec = a.ar[a.off_codec + b];
     if (codec == CODEC_RLE) continue;
     uint32_t org[3], w[3];
@@ -370,18 +381,22 @@ __global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_kernel(Decode
   }
 }
 
+__global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_kernel(DecodeArgs a) {
+  stream_decode_body(a, 0, 0);
+}
+
 constexpr int kRleThreads = 256;
 
 // RLE and RLE+Huffman blocks: run starts by a block scan, then every code position
 // finds its run by binary search.
-__global__ __launch_bounds__(kRleThreads) void rle_expand_kernel(DecodeArgs a) {
+__device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
   __shared__ uint16_t s_v[kSlots];
   __shared__ uint16_t s_l[kSlots];
   __shared__ uint32_t s_start[kSlots + 1];
   __shared__ uint32_t s_scan[33];
   __shared__ uint32_t s_bad;
-  const uint32_t b = blockIdx.x;
   const int tid = threadIdx.x;
+  if (a.dead) return;
   const int codec = a.ar[a.off_codec + b];
   if (codec != CODEC_RLE && codec != CODEC_RLE_HUFF) return;
   if (a.st->status & ERR_CORRUPT) return;
@@ -479,6 +494,8 @@ __global__ __launch_bounds__(kRleThreads) void rle_expand_kernel(DecodeArgs a) {
   o4[1] = make_uint4(vals[4], vals[5], vals[6], vals[7]);
 }
 
+__global__ __launch_bounds__(kRleThreads) void rle_expand_kernel(DecodeArgs a) { rle_expand_body(a, blockIdx.x); }
+
 // =================================================================================
 // reconstruction: N-D partial sums per chunk (Sec. IV-B2), scaled by 2eb
 // =================================================================================
@@ -487,11 +504,9 @@ constexpr int kRecThreads = 256;
 __device__ __forceinline__ float scale(int32_t k, float ebx2) { return __fmul_rn(__int2float_rn(k), ebx2); }
 
 template <int ND>
-__global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) {
-  __shared__ __align__(16) int32_t s_q[kSlots];
-  const uint32_t b = blockIdx.x;
+__device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q) {
   const int tid = threadIdx.x;
-  if (a.st->status & ERR_CORRUPT) return;
+  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
   uint32_t org[3], w[3];
   block_box(a.g, b, org, w);
   const uint32_t m = w[0] * w[1] * w[2];
@@ -648,6 +663,153 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) 
       out[((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx] = __uint_as_float(kv.y);
     }
   }
+}
+
+template <int ND>
+__global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) {
+  __shared__ __align__(16) int32_t s_q[kSlots];
+  reconstruct_body<ND>(a, blockIdx.x, s_q);
+}
+
+// =================================================================================
+// batches: device-side header checks and table-driven launches
+// =================================================================================
+__device__ __forceinline__ uint64_t dev_a8(uint64_t v) { return (v + 7) & ~7ull; }
+
+// Reads field f's archive header on the device, checks it against the shape the
+// batch was planned for (the same checks the single-field entry makes on the host)
+// and completes the field's decode arguments; a failing header marks the field
+// dead (every later stage skips it) and corrupt.
+__global__ void dec_header_batch_kernel(DecodeArgs* tasks, int nfields) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nfields) return;
+  DecodeArgs& a = tasks[f];
+  const Geom& g = a.g;
+  bool ok = a.bytes >= (uint64_t)kHdr;
+  uint64_t n_rec = 0, n_out = 0, n_patch = 0, payload = 0, total = 0, nblk = 0, dims[3] = {0, 0, 0};
+  uint32_t magic = 0, radius = 0, lanes = 0, flags = 0;
+  uint16_t version = 0;
+  uint8_t ndim = 0, mode = 0;
+  float eb_f = 0.0f;
+  if (ok) {
+    const uint8_t* h = a.ar;
+    memcpy(&magic, h, 4);
+    memcpy(&version, h + 4, 2);
+    ndim = h[6];
+    mode = h[7];
+    memcpy(dims, h + 8, 24);
+    memcpy(&eb_f, h + 48, 4);
+    memcpy(&radius, h + 52, 4);
+    memcpy(&lanes, h + 56, 4);
+    memcpy(&flags, h + 60, 4);
+    memcpy(&nblk, h + 64, 8);
+    memcpy(&n_rec, h + 72, 8);
+    memcpy(&n_out, h + 80, 8);
+    memcpy(&n_patch, h + 88, 8);
+    memcpy(&payload, h + 96, 8);
+    memcpy(&total, h + 104, 8);
+    ok = magic == kMagic && version == kVersion && ndim == g.ndim && mode <= 1;
+    for (int d = 0; d < 3 && ok; d++) {
+      const uint64_t want = d < g.ndim ? (uint64_t)g.n[3 - g.ndim + d] : 0ull;
+      ok = dims[d] == want;
+    }
+    ok = ok && radius >= 1 && radius <= 512 && lanes == (uint32_t)kLanes && flags <= 3;
+    ok = ok && nblk == g.nblk && n_rec == n_out + n_patch && eb_f > 0.0f && isfinite(2.0f * eb_f);
+    ok = ok && n_rec <= 2 * g.nelem && payload <= a.bytes && (payload & 3) == 0;
+    const uint64_t off_bb = kHdr + dev_a8(g.nblk);
+    const uint64_t off_rec = off_bb + dev_a8(4ull * g.nblk);
+    const uint64_t off_books = off_rec + 8 * n_rec + dev_a8(payload);
+    const uint64_t want_total = off_books + ((flags & 1) ? kNsymCode : 0) + ((flags & 2) ? kNsymCode + kNsymLen : 0);
+    ok = ok && total == want_total && total <= a.bytes;
+    if (ok) {
+      a.off_codec = kHdr;
+      a.off_bb = off_bb;
+      a.off_rec = off_rec;
+      a.off_pay = off_rec + 8 * n_rec;
+      a.off_books = off_books;
+      a.n_rec = n_rec;
+      a.payload = payload;
+      a.flags = flags;
+      a.radius = radius;
+      a.ebx2_f = 2.0f * eb_f;
+    }
+  }
+  a.dead = ok ? 0 : 1;
+  if (!ok) atomicOr(&a.st->status, ERR_CORRUPT);
+}
+
+__device__ __forceinline__ int field_of(const uint32_t* prefix, int nfields, uint32_t c) {
+  int lo = 0, hi = nfields - 1;  // last field with prefix[f] <= c
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// set-up: per field 1 prep CTA, 3 table CTAs, then its record CTAs (setup0 prefix)
+__global__ __launch_bounds__(1024) void dec_setup_batch_kernel(const DecodeArgs* __restrict__ tasks,
+                                                               const uint32_t* __restrict__ setup0, int nfields) {
+  const int f = field_of(setup0, nfields, blockIdx.x);
+  const DecodeArgs& a = tasks[f];
+  const uint32_t role = blockIdx.x - setup0[f], nroles = setup0[f + 1] - setup0[f];
+  if (role == 0) dec_prep_body(a);
+  else if (role <= 3) dec_tables_body(a, (int)role - 1);
+  else dec_records_body(a, role - 4, nroles - 4);
+}
+
+// entropy decoding: per field ceil(nblk / kStreamWarps) CTAs, one block per warp
+__global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_batch_kernel(const DecodeArgs* __restrict__ tasks,
+                                                                                const uint32_t* __restrict__ chunk0,
+                                                                                int nfields) {
+  const int f = field_of(chunk0, nfields, blockIdx.x);
+  const DecodeArgs& a = tasks[f];
+  const uint32_t b0 = (blockIdx.x - chunk0[f]) * kStreamWarps;
+  const uint32_t b1 = min(a.g.nblk, b0 + kStreamWarps);
+  stream_decode_body(a, b0, b1);
+}
+
+__global__ __launch_bounds__(kRleThreads) void rle_expand_batch_kernel(const DecodeArgs* __restrict__ tasks,
+                                                                       const uint32_t* __restrict__ tile0, int nfields) {
+  const int f = field_of(tile0, nfields, blockIdx.x);
+  rle_expand_body(tasks[f], blockIdx.x - tile0[f]);
+}
+
+__global__ __launch_bounds__(kRecThreads) void reconstruct_batch_kernel(const DecodeArgs* __restrict__ tasks,
+                                                                        const uint32_t* __restrict__ tile0, int nfields) {
+  __shared__ __align__(16) int32_t s_q[kSlots];
+  const int f = field_of(tile0, nfields, blockIdx.x);
+  const DecodeArgs& a = tasks[f];
+  const uint32_t b = blockIdx.x - tile0[f];
+  if (a.g.ndim == 1) reconstruct_body<1>(a, b, s_q);
+  else if (a.g.ndim == 2) reconstruct_body<2>(a, b, s_q);
+  else reconstruct_body<3>(a, b, s_q);
+}
+
+cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
+  cudaError_t e;
+  dec_header_batch_kernel<<<(L.nfields + 127) / 128, 128, 0, s>>>(L.tasks, L.nfields);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  trace_begin(K_DEC_SETUP, s);
+  dec_setup_batch_kernel<<<L.nsetup, 1024, 0, s>>>(L.tasks, L.setup0, L.nfields);
+  trace_end(K_DEC_SETUP, s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t lut_bytes = 3 * (1u << kLutBits) * sizeof(uint32_t);
+  e = cudaFuncSetAttribute(stream_decode_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lut_bytes);
+  if (e != cudaSuccess) return e;
+  trace_begin(K_STREAM_DECODE, s);
+  stream_decode_batch_kernel<<<L.nchunks, 32 * kStreamWarps, lut_bytes, s>>>(L.tasks, L.chunk0, L.nfields);
+  trace_end(K_STREAM_DECODE, s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  trace_begin(K_RLE_EXPAND, s);
+  rle_expand_batch_kernel<<<L.ntiles, kRleThreads, 0, s>>>(L.tasks, L.tile0, L.nfields);
+  trace_end(K_RLE_EXPAND, s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  trace_begin(K_RECONSTRUCT, s);
+  reconstruct_batch_kernel<<<L.ntiles, kRecThreads, 0, s>>>(L.tasks, L.tile0, L.nfields);
+  trace_end(K_RECONSTRUCT, s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {

@@ -140,6 +140,7 @@ struct DecodeArgs {
   uint16_t* runv;      // decoded run values of RLE+Huffman blocks (may alias codes)
   uint16_t* runl;      // nblk * 4096 decoded run lengths
   float* out;
+  int dead;            // batches: the header failed validation, do nothing
 };
 
 // ---- per-kernel tracing (CUDA events around each launch; defined in api.cu) -------
@@ -163,6 +164,7 @@ void trace_end(int id, cudaStream_t s);
 bool trace_suspend();           // stop event tracing (stream capture); returns the old state
 void trace_resume(bool on);
 void trace_count_batch();       // one replay of a compression batch graph: count its launches
+void trace_count_decode_batch();  // the same for a decompression batch graph
 
 // ---- launchers (return cudaGetLastError of the launch) ---------------------------
 cudaError_t launch_abs_params(DevState* st, double eb, cudaStream_t s);
@@ -185,5 +187,20 @@ cudaError_t launch_encode_batch(const EncodeArgs* d_tasks, const uint32_t* d_til
                                 uint32_t* ticket, cudaStream_t s);
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);
+
+// Batched decompression: a device table of per-field decode arguments (headers are
+// read and checked on the device) and CTA prefixes per stage.
+struct DecodeBatchLaunch {
+  DecodeArgs* tasks;
+  int nfields;
+  const uint32_t* setup0;  // nfields + 1: set-up CTAs (prep, 3 tables, records)
+  uint32_t nsetup;
+  const uint32_t* chunk0;  // nfields + 1: stream-decode CTAs (kStreamWarps blocks each)
+  uint32_t nchunks;
+  const uint32_t* tile0;   // nfields + 1: codec blocks
+  uint32_t ntiles;
+};
+constexpr int kStreamWarpsPerCta = 16;
+cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s);
 
 }  // namespace cszp

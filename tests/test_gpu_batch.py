@@ -133,3 +133,50 @@ def test_batch_autotune_info(gpu):
     bc = gpu.BatchCompressor(xs, 1e-3, "abs")
     info = bc.info()
     assert info["construct_grid"] > 0 and info["tuned_ms"][0] > 0
+
+
+def test_batch_round_trip(gpu, orc):
+    """Batched compression then batched decompression: every field bit-identical to
+    the single-field decompression of the same archive, within the bound, and
+    identical again after a replay with new data in the same buffers."""
+    fields = _mixed_fields(7)
+    xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
+    bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields])
+    bd = gpu.BatchDecompressor(bc.archives, [tuple(x.shape) for x in xs])
+    for rep in range(2):
+        if rep == 1:
+            for x in xs:
+                x.mul_(-0.75).add_(3.0)
+        bc.run()
+        sizes, stats = bc.results()
+        assert all(v == 0 for v in stats)
+        bd.run()
+        assert bd.results() == [0] * len(xs)
+        for i, x in enumerate(xs):
+            y, st = gpu.decompress(bc.archives[i], sizes[i])
+            assert st == 0
+            assert torch.equal(bd.outs[i].view(torch.int32), y.view(torch.int32)), (rep, i)
+            eb_f = gpu.header(bc.archives[i])["eb_f"]
+            assert float((x.double() - bd.outs[i].double()).abs().max()) <= eb_f
+
+
+def test_batch_decompress_bad_header_isolated(gpu):
+    fields = _mixed_fields(8)[:6]
+    xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
+    bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields], autotune=False)
+    bc.run()
+    sizes, _ = bc.results()
+    bad = [a.clone() for a in bc.archives]
+    bad[2][0] ^= 0xFF           # magic
+    bad[4][64] ^= 0x01          # block count
+    shapes = [tuple(x.shape) for x in xs]
+    shapes[5] = tuple(int(d) + 1 for d in shapes[5])  # shape that does not match the header
+    outs = [torch.empty(sh, device="cuda") for sh in shapes]
+    bd = gpu.BatchDecompressor(bad, shapes, archive_bytes=sizes, outs=outs)
+    bd.run()
+    st = bd.results()
+    assert st[2] == 4 and st[4] == 4 and st[5] == 4
+    for i in (0, 1, 3):
+        assert st[i] == 0
+        y, _ = gpu.decompress(bc.archives[i], sizes[i])
+        assert torch.equal(bd.outs[i].view(torch.int32), y.view(torch.int32))
