@@ -236,6 +236,15 @@ def batched_comparison(args, dev, flush):
 
     plain_bytes = plain()
     t_plain = [t for t, _ in timed(plain, 3)]
+    # plain round trip: per-field compress + decompress
+    outs = [torch.empty_like(x) for x in xs]
+
+    def plain_rt():
+        for x, eb, m, o in zip(xs, ebs, modes, outs):
+            ar, nb, _ = api.compress(x, eb, m, select="exhaustive", out=arc[:min(arc.numel(), 6 * x.numel() + (1 << 20))],
+                                     workspace=ws)
+            api.decompress(ar, nb, out=o, dims=tuple(x.shape), workspace=ws)
+    t_plain_rt = [t for t, _ in timed(plain_rt, 3)]
     res = {}
     for sel, wt in (("learned", w), ("exhaustive", None)):
         bc = api.BatchCompressor(xs, ebs, modes, select=sel, weights=wt, archive_caps=caps)
@@ -244,22 +253,43 @@ def batched_comparison(args, dev, flush):
         if any(stats):
             raise RuntimeError(f"batched {sel}: field status {stats}")
         t_b = [t for t, _ in timed(bc.run, 5)]
+        bd = api.BatchDecompressor(bc.archives, [tuple(x.shape) for x in xs], archive_bytes=caps, outs=outs)
+        bd.run()
+        dstats = bd.results()
+        if any(dstats):
+            raise RuntimeError(f"batched decompression: field status {dstats}")
+
+        def rt():
+            bc.run()
+            bd.run()
+        t_rt = [t for t, _ in timed(rt, 5)]
+        ok = all(float((x.double() - o.double()).abs().max()) <= api.header(a)["eb_f"]
+                 for x, o, a in zip(xs, outs, bc.archives))
+        if not ok:
+            raise RuntimeError("batched round trip outside the error bound")
         res[sel] = {"gbs": n_in / (np.mean(t_b) * 1e-3) / 1e9, "ms": float(np.mean(t_b)),
+                    "rt_gbs": n_in / (np.mean(t_rt) * 1e-3) / 1e9,
                     "bytes": int(sum(sizes)), "tuning": bc.info()}
-        del bc
+        del bd, bc
     plain_gbs = n_in / (np.mean(t_plain) * 1e-3) / 1e9
+    plain_rt_gbs = n_in / (np.mean(t_plain_rt) * 1e-3) / 1e9
     return {
         "workload": "batch256_mixed_1d2d3d", "fields": len(xs), "input_bytes": n_in,
         "plain_per_field_gbs": plain_gbs, "plain_ms": float(np.mean(t_plain)), "plain_cr": n_in / plain_bytes,
+        "plain_round_trip_gbs": plain_rt_gbs,
         "batched_learned_gbs": res["learned"]["gbs"], "batched_learned_ms": res["learned"]["ms"],
         "batched_learned_cr": n_in / res["learned"]["bytes"],
+        "batched_learned_round_trip_gbs": res["learned"]["rt_gbs"],
         "batched_exhaustive_gbs": res["exhaustive"]["gbs"], "batched_exhaustive_cr": n_in / res["exhaustive"]["bytes"],
+        "batched_exhaustive_round_trip_gbs": res["exhaustive"]["rt_gbs"],
         "speedup_learned_batched_vs_plain": res["learned"]["gbs"] / plain_gbs,
+        "speedup_round_trip_learned_batched_vs_plain": res["learned"]["rt_gbs"] / plain_rt_gbs,
         "cr_loss_learned_vs_plain": res["learned"]["bytes"] / plain_bytes - 1.0,
         "construct_grid": res["learned"]["tuning"]["construct_grid"],
         "autotune_ms": res["learned"]["tuning"]["tuned_ms"],
-        "note": "compression only; every timed pass is preceded by a 256 MiB L2 flush; the plain path "
-                "synchronises once per field (it returns each size to the host)",
+        "note": "GB/s of FP32 input; every timed pass is preceded by a 256 MiB L2 flush; the plain path "
+                "synchronises once per call (it returns each size / status to the host); round trips "
+                "are compression then decompression",
     }
 
 

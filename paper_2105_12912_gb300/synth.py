@@ -78,6 +78,9 @@ def grf(shape, beta: float, seed: int, device="cpu") -> torch.Tensor:
     del amp, k2
     out = torch.fft.irfftn(spec, s=shape)
     del spec
+    # cuFFT plans keep their own work areas outside PyTorch's allocator; fields of
+    # many distinct shapes would otherwise pin tens of GB
+    torch.backends.cuda.cufft_plan_cache[out.device.index].clear()
     out = out - out.mean()
     sd = out.std()
     if float(sd) > 0:
