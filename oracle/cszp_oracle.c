@@ -34,7 +34,7 @@
 #define SLOTS 4096       /* code-stream slots per codec block */
 #define HDR 128
 #define MAGIC 0x2B5A5343u /* "CSZ+" */
-#define VERSION 1
+#define VERSION 2
 #define MAXLEN 64
 
 /* ------------------------------------------------------------------------------- */
@@ -636,15 +636,26 @@ static int64_t ihs_decode(const uint16_t* in, uint64_t avail, uint64_t N, const 
 
 /* ------------------------------------------------------------------------------- */
 /* per-block payloads                                                               */
-/*   HUFF      : interleaved stream of the block's codes (u16 units, padded to 4 B)  */
+/*   HUFF      : u16 unit count of stream A, then two interleaved streams: A holds  */
+/*               the block's first h codes, B the rest (h = the multiple of 32 at or */
+/*               above m/2, at most m), padded to 4 B                                */
 /*   RLE       : u16 value[nr], u16 length[nr]                                       */
 /*   RLE_HUFF  : u32 nr, u32 value units, value stream, length stream (length-1      */
 /*               coded), padded to 4 B                                               */
 /* ------------------------------------------------------------------------------- */
 
+/* codes in stream A of a Huffman block of m codes */
+static uint64_t huff_split(uint64_t m) {
+  const uint64_t h = 32 * ceil_div(m, 64);
+  return h < m ? h : m;
+}
+
 static uint64_t huff_size(const uint16_t* c, uint64_t m, const uint8_t* len, const uint64_t* code,
                           int* missing) {
-  return align4(2 * ihs_encode(c, m, 0, len, code, NULL, missing));
+  const uint64_t h = huff_split(m);
+  const uint64_t na = ihs_encode(c, h, 0, len, code, NULL, missing);
+  const uint64_t nb = ihs_encode(c + h, m - h, 0, len, code, NULL, missing);
+  return align4(2 * (1 + na + nb));
 }
 
 static void run_streams(const run_t* runs, uint64_t nr, uint16_t* v, uint16_t* l) {
@@ -669,11 +680,15 @@ static uint64_t rlehuff_size(const run_t* runs, uint64_t nr, const uint8_t* vlen
 static void huff_write(const uint16_t* c, uint64_t m, const uint8_t* len, const uint64_t* code,
                        uint8_t* out) {
   int missing = 0;
-  uint64_t nu = ihs_encode(c, m, 0, len, code, NULL, &missing);
-  uint16_t* u = (uint16_t*)calloc(nu + 2, sizeof(uint16_t));
-  ihs_encode(c, m, 0, len, code, u, &missing);
-  memset(out, 0, align4(2 * nu));
-  memcpy(out, u, 2 * nu);
+  const uint64_t h = huff_split(m);
+  const uint64_t na = ihs_encode(c, h, 0, len, code, NULL, &missing);
+  const uint64_t nb = ihs_encode(c + h, m - h, 0, len, code, NULL, &missing);
+  uint16_t* u = (uint16_t*)calloc(1 + na + nb + 2, sizeof(uint16_t));
+  u[0] = (uint16_t)na;
+  ihs_encode(c, h, 0, len, code, u + 1, &missing);
+  ihs_encode(c + h, m - h, 0, len, code, u + 1 + na, &missing);
+  memset(out, 0, align4(2 * (1 + na + nb)));
+  memcpy(out, u, 2 * (1 + na + nb));
   free(u);
 }
 
@@ -1289,11 +1304,17 @@ static int decode_block(const parsed_t* P, const uint8_t* pay, uint64_t bytes, i
   const uint32_t nsym = 2 * P->h.radius;
   if (codec == ORC_CODEC_HUFF) {
     uint64_t nu = bytes / 2;
+    if (nu < 1) return ORC_E_CORRUPT;
     uint16_t* u = (uint16_t*)malloc((nu + 1) * sizeof(uint16_t));
     memcpy(u, pay, 2 * nu);
-    int64_t used = ihs_decode(u, nu, m, tc, c);
+    const uint64_t h = huff_split(m), na = u[0];
+    int64_t ua = -1, ub = -1;
+    if (na <= nu - 1) {
+      ua = ihs_decode(u + 1, na, h, tc, c);
+      if (ua == (int64_t)na) ub = ihs_decode(u + 1 + na, nu - 1 - na, m - h, tc, c + h);
+    }
     free(u);
-    if (used < 0 || align4(2 * (uint64_t)used) != bytes) return ORC_E_CORRUPT;
+    if (ua != (int64_t)na || ub < 0 || align4(2 * (1 + na + (uint64_t)ub)) != bytes) return ORC_E_CORRUPT;
     for (uint64_t i = 0; i < m; i++)
       if (c[i] >= nsym) return ORC_E_CORRUPT;
     return ORC_OK;

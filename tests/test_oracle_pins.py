@@ -517,7 +517,9 @@ def test_learned_mode_reduces_to_other_selectors(orc):
 # ---------------------------------------------------------------------------------
 # interleaved Huffman stream layout, closed form: with a two-symbol book every code
 # is one bit, so each of the 32 lanes tops up one 16-bit unit at steps 0, 16, 32, ...
-# and the stream is lane 0..31's unit 0, then their unit 1, and so on
+# and a stream is lane 0..31's unit 0, then their unit 1, and so on.  A Huffman
+# block is a u16 unit count of stream A (the first 2048 codes), stream A, stream B
+# (the other 2048), padded to 4 bytes.
 # ---------------------------------------------------------------------------------
 def test_interleaved_stream_layout_one_bit_codes(orc):
     rng = np.random.default_rng(12)
@@ -531,15 +533,20 @@ def test_interleaved_stream_layout_one_bit_codes(orc):
     books = sec["books"]
     assert books[512] == 1 and books[513] == 1 and books[:1024].sum() == 2
     units = sec["payload"].view(np.uint16)
-    assert units.size == 32 * 8                # 128 bits per lane -> 8 units each
-    expect = np.zeros((8, 32), np.uint16)
-    for lane in range(32):
-        bits = d[lane::32]                     # the lane's symbols, one bit each
-        for k in range(8):
-            v = 0
-            for b in bits[16 * k:16 * k + 16]:
-                v = (v << 1) | int(b)
-            expect[k, lane] = v
-    assert np.array_equal(units, expect.ravel())
+    assert units.size == 1 + 2 * 32 * 4 + 1    # count, 2 streams x 64 bits per lane, pad
+    assert units[0] == 128 and units[-1] == 0
+
+    def stream(sym):
+        expect = np.zeros((4, 32), np.uint16)
+        for lane in range(32):
+            bits = sym[lane::32]               # the lane's symbols, one bit each
+            for k in range(4):
+                v = 0
+                for b in bits[16 * k:16 * k + 16]:
+                    v = (v << 1) | int(b)
+                expect[k, lane] = v
+        return expect.ravel()
+    assert np.array_equal(units[1:129], stream(d[:2048]))
+    assert np.array_equal(units[129:257], stream(d[2048:]))
     st, y = orc.decompress(ar, n)
     assert np.array_equal(y, x)
