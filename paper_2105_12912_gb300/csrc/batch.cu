@@ -588,7 +588,7 @@ csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_w
     if (rec_ctas > 256) rec_ctas = 256;
     nsetup += 4 + (uint32_t)rec_ctas;
     chunk0[f] = nchunks;
-    nchunks += (g.nblk + kStreamWarpsPerCta - 1) / kStreamWarpsPerCta;
+    nchunks += (g.nblk + kStreamWarpsPerCta / 2 - 1) / (kStreamWarpsPerCta / 2);
     tile0[f] = ntiles;
     ntiles += g.nblk;
   }

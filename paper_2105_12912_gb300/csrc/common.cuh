@@ -27,7 +27,7 @@ constexpr int kNsymCode = 1024;
 constexpr int kNsymLen = 4096;
 constexpr int kHdr = 128;
 constexpr uint32_t kMagic = 0x2B5A5343u;  // "CSZ+"
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr int kLanes = 32;  // interleave width of Huffman streams (header field)
 constexpr int kMaxLen = 64;
 constexpr int kLutBits = 12;
@@ -589,22 +589,30 @@ __device__ inline uint32_t ihs_encode_block(const uint16_t* sym, uint32_t N, int
   return total;
 }
 
-// Faster block-wide encoder for streams whose lanes each hold at most 4064 bits.
-// Pass 1 (ihs_plan): thread (lane l, warp w) reads the lengths of lane l's steps
-// 16w..16w+15 once into registers; per-lane totals give the stream size.  Pass 2
-// (ihs_emit): each thread appends its codes to lane l's bit string in shared memory
-// (32 strings of 128 words, word index XOR-swizzled by the lane so the 32 lanes hit
-// 32 banks), then every unit is cut straight out of its lane's string and stored at
-// its decoder-order position (rounds within steps, lanes in order within a round).
+// A Huffman codec block is a u16 unit count of stream A, then two interleaved
+// streams: A codes the block's first huff_split(m) symbols, B the rest.
+__host__ __device__ __forceinline__ uint32_t huff_split(uint32_t m) {
+  const uint32_t h = 32u * ((m + 63u) / 64u);
+  return h < m ? h : m;
+}
+
+// Block-wide encoder of one Huffman block's two streams (256 threads).  Pass 1
+// (ihs_plan2): thread (lane l, warp w) reads the lengths of lane l's steps
+// 16(w&3)..16(w&3)+15 of stream w>>2 once into registers; per-lane totals give both
+// streams' sizes.  Pass 2 (ihs_emit2): each thread appends its codes to its lane's
+// bit string in shared memory (64 strings of 64 words, word index XOR-swizzled by
+// the lane so a warp's 32 lanes hit 32 banks), then every unit is cut straight out
+// of its lane's string and stored at its decoder-order position (rounds within
+// steps, lanes in order within a round).  Lanes above 2016 bits take the gather
+// encoder instead.
 struct IhsPlan {
   uint32_t len4[4];    // the thread's 16 code lengths, 8 bits each
-  uint32_t pre;        // bits of lane l before step 16w
+  uint32_t pre;        // bits of the lane before the thread's first step
   uint32_t cum;        // bits of the thread's 16 steps
-  uint32_t lane_bits;  // bits of lane l
 };
 
-constexpr uint32_t kLaneWords = 128;               // words per lane string
-constexpr uint32_t kLaneBitsMax = 32 * (kLaneWords - 1);  // 4064: room for a 2-word read
+constexpr uint32_t kLaneWords = 64;                       // words per lane string
+constexpr uint32_t kLaneBitsMax = 32 * (kLaneWords - 1);  // 2016: room for a 2-word read
 
 __device__ __forceinline__ uint32_t plan_len(const IhsPlan& P, int i) {
   // selects rather than an indexed load, so the plan stays in registers
@@ -612,13 +620,20 @@ __device__ __forceinline__ uint32_t plan_len(const IhsPlan& P, int i) {
   return (wsel >> (8 * (i & 3))) & 0xffu;
 }
 
-// Fills P for every thread; returns (all threads) the stream's unit count and, in
-// *max_lane_bits, the largest lane total.  scratch: >= 256 + 8 u32.  Contains
-// __syncthreads.
-__device__ inline uint32_t ihs_plan(const uint16_t* sym, uint32_t N, int add, const uint8_t* __restrict__ lens,
-                                    uint32_t* scratch, IhsPlan& P, uint32_t* max_lane_bits) {
-  const uint32_t tid = threadIdx.x, l = tid & 31, w = tid >> 5;
-  const uint32_t t0 = 16 * w;
+struct IhsPlan2Out {
+  uint32_t units_a, units_b;  // units of each stream
+  uint32_t max_lane_bits;     // over both streams
+};
+
+// Fills P; returns the units of both streams and the largest lane total.  scratch:
+// >= 256 + 4 u32.  Contains __syncthreads.
+__device__ inline IhsPlan2Out ihs_plan2(const uint16_t* sym, uint32_t m, const uint8_t* __restrict__ lens,
+                                       uint32_t* scratch, IhsPlan& P) {
+  const uint32_t tid = threadIdx.x, l = tid & 31, w = tid >> 5, sidx = w >> 2, wl = w & 3;
+  const uint32_t h = huff_split(m);
+  const uint32_t N = sidx ? m - h : h;
+  const uint16_t* ss = sym + (sidx ? h : 0);
+  const uint32_t t0 = 16 * wl;
   uint32_t cum = 0;
 #pragma unroll
   for (int q = 0; q < 4; q++) {
@@ -626,7 +641,7 @@ __device__ inline uint32_t ihs_plan(const uint16_t* sym, uint32_t N, int add, co
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       const uint32_t j = 32 * (t0 + 4 * q + k) + l;
-      const uint32_t L = j < N ? (uint32_t)__ldg(&lens[sym[j] + add]) : 0u;
+      const uint32_t L = j < N ? (uint32_t)__ldg(&lens[ss[j]]) : 0u;
       pk |= L << (8 * k);
       cum += L;
     }
@@ -638,45 +653,50 @@ __device__ inline uint32_t ihs_plan(const uint16_t* sym, uint32_t N, int add, co
   __syncthreads();
   uint32_t pre = 0, tot = 0;
 #pragma unroll
-  for (uint32_t v = 0; v < 8; v++) {
-    const uint32_t c = scratch[32 * v + l];
-    if (v < w) pre += c;
+  for (uint32_t v = 0; v < 4; v++) {
+    const uint32_t c = scratch[32 * (4 * sidx + v) + l];
+    if (v < wl) pre += c;
     tot += c;
   }
   P.pre = pre;
-  P.lane_bits = tot;
-  if (w == 0) {
-    uint32_t units = warp_sum((tot + 15) >> 4);
+  if (wl == 0) {  // warps 0 and 4 total their stream
+    const uint32_t units = warp_sum((tot + 15) >> 4);
     uint32_t mx = tot;
 #pragma unroll
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(~0u, mx, o));
     if (l == 0) {
-      scratch[256] = units;
-      scratch[257] = mx;
+      scratch[256 + sidx] = units;
+      scratch[258 + sidx] = mx;
     }
   }
   __syncthreads();
-  const uint32_t units = scratch[256];
-  *max_lane_bits = scratch[257];
+  IhsPlan2Out r;
+  r.units_a = scratch[256];
+  r.units_b = scratch[257];
+  r.max_lane_bits = max(scratch[258], scratch[259]);
   __syncthreads();
-  return units;
+  return r;
 }
 
-// Pass 2; requires every lane total <= kLaneBitsMax.  lanebuf: 32 * kLaneWords u32.
-// scratch: >= 8 u32.  Contains __syncthreads.
-__device__ inline void ihs_emit(const uint16_t* sym, uint32_t N, int add, const uint64_t* __restrict__ codes,
-                                const IhsPlan& P, uint32_t* lanebuf, uint16_t* out16, uint32_t* scratch) {
-  const uint32_t tid = threadIdx.x, l = tid & 31, w = tid >> 5;
-  const uint32_t t0 = 16 * w;
-  for (uint32_t i = tid; i < 32 * kLaneWords; i += blockDim.x) lanebuf[i] = 0;
+// Pass 2; requires every lane total <= kLaneBitsMax.  out16[0] receives units_a,
+// stream A starts at out16[1], stream B at out16[1 + units_a].  lanebuf: 64 *
+// kLaneWords u32.  scratch: >= 8 u32.  Contains __syncthreads.
+__device__ inline void ihs_emit2(const uint16_t* sym, uint32_t m, const uint64_t* __restrict__ codes,
+                                 const IhsPlan& P, uint32_t units_a, uint32_t* lanebuf, uint16_t* out16,
+                                 uint32_t* scratch) {
+  const uint32_t tid = threadIdx.x, l = tid & 31, w = tid >> 5, sidx = w >> 2, wl = w & 3;
+  const uint32_t h = huff_split(m);
+  const uint16_t* ss = sym + (sidx ? h : 0);
+  const uint32_t t0 = 16 * wl;
+  for (uint32_t i = tid; i < 64 * kLaneWords; i += blockDim.x) lanebuf[i] = 0;
   __syncthreads();
-  uint32_t* mine = lanebuf + kLaneWords * l;
+  uint32_t* mine = lanebuf + kLaneWords * (32 * sidx + l);
   uint32_t p = P.pre;
 #pragma unroll 4
   for (int i = 0; i < 16; i++) {
     int L = (int)plan_len(P, i);
     if (L == 0) continue;
-    const uint64_t C = __ldg(&codes[sym[32 * (t0 + i) + l] + add]);
+    const uint64_t C = __ldg(&codes[ss[32 * (t0 + i) + l]]);
     while (L > 0) {
       const uint32_t wi = p >> 5, off = p & 31;
       const int n = min(L, 32 - (int)off);
@@ -686,13 +706,14 @@ __device__ inline void ihs_emit(const uint16_t* sym, uint32_t N, int add, const 
       p += n;
     }
   }
-  // units each warp's steps take, for the warp's first output position
+  // units each warp's steps take, for the warp's first output position in its stream
   const uint32_t u_begin = (P.pre + 15) >> 4, u_end = (P.pre + P.cum + 15) >> 4;
   const uint32_t wtot = warp_sum(u_end - u_begin);
   if (l == 0) scratch[w] = wtot;
   __syncthreads();
-  uint32_t base = 0;
-  for (uint32_t v = 0; v < w; v++) base += scratch[v];
+  uint32_t base = 1 + (sidx ? units_a : 0);
+  for (uint32_t v = 0; v < wl; v++) base += scratch[4 * sidx + v];
+  if (tid == 0) out16[0] = (uint16_t)units_a;
   const uint32_t lt = (1u << l) - 1u;
   uint32_t c = P.pre, uprev = u_begin;
 #pragma unroll 1

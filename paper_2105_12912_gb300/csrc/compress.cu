@@ -642,10 +642,10 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   // exact sizes: Huffman units from per-lane bit totals; the plan (code lengths in
   // registers, lane offsets) is kept for the payload
   IhsPlan plan;
-  uint32_t plan_max = ~0u, plan_units = 0;
-  auto huff_units = [&]() {
-    plan_units = ihs_plan(s_c, m, 0, clen, s_part, plan, &plan_max);
-    return plan_units;
+  IhsPlan2Out plan_out{0u, 0u, ~0u};
+  auto huff_units = [&]() {  // u16 count + both streams
+    plan_out = ihs_plan2(s_c, m, clen, s_part, plan);
+    return 1u + plan_out.units_a + plan_out.units_b;
   };
   auto rlehuff_units = [&]() {
     uint32_t vb = 0, lb = 0;
@@ -786,12 +786,14 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   // fits 16 KB unless a forced Huffman mode meets very long codes; those go direct)
   auto assemble = [&](uint16_t* out16) {
     if (codec == CODEC_HUFF) {
-      uint32_t u;
-      if (plan_max <= kLaneBitsMax) {
-        ihs_emit(s_c, m, 0, ccode, plan, reinterpret_cast<uint32_t*>(s_rv), out16, s_part);
-        u = plan_units;
+      const uint32_t u = 1u + plan_out.units_a + plan_out.units_b;
+      if (plan_out.max_lane_bits <= kLaneBitsMax) {
+        ihs_emit2(s_c, m, ccode, plan, plan_out.units_a, reinterpret_cast<uint32_t*>(s_rv), out16, s_part);
       } else {
-        u = ihs_encode_block(s_c, m, 0, clen, ccode, out16, s_part);
+        const uint32_t h = huff_split(m);
+        if (tid == 0) out16[0] = (uint16_t)plan_out.units_a;
+        ihs_encode_block(s_c, h, 0, clen, ccode, out16 + 1, s_part);
+        ihs_encode_block(s_c + h, m - h, 0, clen, ccode, out16 + 1 + plan_out.units_a, s_part);
       }
       if ((u & 1u) && tid == 0) out16[u] = 0;
     } else if (codec == CODEC_RLE_HUFF) {
@@ -855,7 +857,7 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
 
 // Blocks are taken in ticket order, so the payload look-back only ever waits on
 // blocks that CTAs already hold.
-__global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
+__global__ __launch_bounds__(kEncThreads, 5) void encode_kernel(EncodeArgs a) {
   __shared__ uint32_t s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(&a.st->ticket_encode, 1u);
   __syncthreads();
@@ -864,7 +866,7 @@ __global__ __launch_bounds__(kEncThreads) void encode_kernel(EncodeArgs a) {
 
 // Batch: one CTA per codec block of every field; the ticket runs over the blocks of
 // all fields in order (tile0[f] = first block of field f).
-__global__ __launch_bounds__(kEncThreads) void encode_batch_kernel(const EncodeArgs* __restrict__ tasks,
+__global__ __launch_bounds__(kEncThreads, 5) void encode_batch_kernel(const EncodeArgs* __restrict__ tasks,
                                                                    const uint32_t* __restrict__ tile0, int nfields,
                                                                    uint32_t* ticket) {
   __shared__ uint32_t s_tile;

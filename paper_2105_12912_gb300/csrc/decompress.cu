@@ -322,16 +322,19 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
   __syncthreads();
   const bool lane0 = (threadIdx.x & 31) == 0;
   const bool ticketed = b_end == 0;
+  // work items are (block, stream) slots: a Huffman block's streams A and B, an
+  // RLE+Huffman block's value and length streams
   for (uint32_t round = 0;; round++) {
-    uint32_t b = 0;
+    uint32_t slot = 0;
     if (ticketed) {
-      if (lane0) b = atomicAdd(&a.st->ticket_decode, 1u);
-      b = __shfl_sync(~0u, b, 0);
-      if (b >= a.g.nblk) break;
+      if (lane0) slot = atomicAdd(&a.st->ticket_decode, 1u);
+      slot = __shfl_sync(~0u, slot, 0);
+      if (slot >= 2 * a.g.nblk) break;
     } else {
-      b = b_begin + (threadIdx.x >> 5);
-      if (round > 0 || b >= b_end) break;
+      slot = 2 * b_begin + (threadIdx.x >> 5);
+      if (round > 0 || slot >= 2 * b_end) break;
     }
+    const uint32_t b = slot >> 1, which = slot & 1;
     const int codec = a.ar[a.off_codec + b];
     if (codec == CODEC_RLE) continue;
     uint32_t org[3], w[3];
@@ -343,14 +346,22 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
     bool ok;
     if (codec == CODEC_HUFF) {
       const DecTab* t = &a.tabs[0];
-      if (!t->present) {
+      const uint16_t* u = reinterpret_cast<const uint16_t*>(pay);
+      const uint32_t nu = (uint32_t)(bytes / 2);
+      const uint32_t na = nu >= 1 ? u[0] : 0u;
+      if (!t->present || nu < 1 || na > nu - 1) {
         if (lane0) flag(a.st, ERR_CORRUPT);
         continue;
       }
+      const uint32_t h = huff_split(m);
       const BookView bk{lut_code, s_first, s_limit, s_count, s_off, t->sorted, (int)t->maxlen, t->fullmask};
-      ok = ihs_decode_warp(reinterpret_cast<const uint16_t*>(pay), (uint32_t)(bytes / 2), m, bk,
-                           a.codes + (uint64_t)b * kSlots, 0, &used);
-      ok = ok && ((2ull * used + 3) & ~3ull) == bytes;
+      if (which == 0) {
+        ok = ihs_decode_warp(u + 1, na, h, bk, a.codes + (uint64_t)b * kSlots, 0, &used);
+        ok = ok && used == na;
+      } else {
+        ok = ihs_decode_warp(u + 1 + na, nu - 1 - na, m - h, bk, a.codes + (uint64_t)b * kSlots + h, 0, &used);
+        ok = ok && ((2ull * (1ull + na + used) + 3) & ~3ull) == bytes;
+      }
     } else {
       const DecTab* tv = &a.tabs[1];
       const DecTab* tl = &a.tabs[2];
@@ -366,11 +377,12 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
       }
       const uint32_t lavail = (uint32_t)((bytes - 8) / 2 - vu);
       const uint16_t* p16 = reinterpret_cast<const uint16_t*>(pay) + 4;
-      const BookView bv{lut_val, tv->first, tv->limit, tv->count, tv->off, tv->sorted, (int)tv->maxlen,
-                        tv->fullmask};
-      ok = ihs_decode_warp(p16, vu, nr, bv, a.runv + (uint64_t)b * kSlots, 0, &used);
-      ok = ok && used == vu;
-      if (ok) {
+      if (which == 0) {
+        const BookView bv{lut_val, tv->first, tv->limit, tv->count, tv->off, tv->sorted, (int)tv->maxlen,
+                          tv->fullmask};
+        ok = ihs_decode_warp(p16, vu, nr, bv, a.runv + (uint64_t)b * kSlots, 0, &used);
+        ok = ok && used == vu;
+      } else {
         const BookView bl{lut_len, tl->first, tl->limit, tl->count, tl->off, tl->sorted, (int)tl->maxlen,
                           tl->fullmask};
         ok = ihs_decode_warp(p16 + vu, lavail, nr, bl, a.runl + (uint64_t)b * kSlots, 1, &used);
@@ -759,14 +771,14 @@ __global__ __launch_bounds__(1024) void dec_setup_batch_kernel(const DecodeArgs*
   else dec_records_body(a, role - 4, nroles - 4);
 }
 
-// entropy decoding: per field ceil(nblk / kStreamWarps) CTAs, one block per warp
+// entropy decoding: per field ceil(nblk / (kStreamWarps / 2)) CTAs, one stream per warp
 __global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_batch_kernel(const DecodeArgs* __restrict__ tasks,
                                                                                 const uint32_t* __restrict__ chunk0,
                                                                                 int nfields) {
   const int f = field_of(chunk0, nfields, blockIdx.x);
   const DecodeArgs& a = tasks[f];
-  const uint32_t b0 = (blockIdx.x - chunk0[f]) * kStreamWarps;
-  const uint32_t b1 = min(a.g.nblk, b0 + kStreamWarps);
+  const uint32_t b0 = (blockIdx.x - chunk0[f]) * (kStreamWarps / 2);
+  const uint32_t b1 = min(a.g.nblk, b0 + kStreamWarps / 2);
   stream_decode_body(a, b0, b1);
 }
 
@@ -834,7 +846,7 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[nluts], stream_decode_kernel, 32 * kStreamWarps, lut_bytes);
       if (occ[nluts] <= 0) occ[nluts] = 1;
     }
-    const uint64_t want = ((uint64_t)a.g.nblk + kStreamWarps - 1) / kStreamWarps;
+    const uint64_t want = (2ull * a.g.nblk + kStreamWarps - 1) / kStreamWarps;
     const uint64_t cap = (uint64_t)sms * occ[nluts];
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     trace_begin(K_STREAM_DECODE, s);

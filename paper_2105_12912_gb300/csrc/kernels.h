@@ -195,7 +195,7 @@ struct DecodeBatchLaunch {
   int nfields;
   const uint32_t* setup0;  // nfields + 1: set-up CTAs (prep, 3 tables, records)
   uint32_t nsetup;
-  const uint32_t* chunk0;  // nfields + 1: stream-decode CTAs (kStreamWarps blocks each)
+  const uint32_t* chunk0;  // nfields + 1: stream-decode CTAs (kStreamWarpsPerCta / 2 blocks each)
   uint32_t nchunks;
   const uint32_t* tile0;   // nfields + 1: codec blocks
   uint32_t ntiles;
