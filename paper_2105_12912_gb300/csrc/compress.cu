@@ -58,20 +58,30 @@ __device__ __forceinline__ void range_body(const float* __restrict__ x, uint64_t
   const bool vec = (((uintptr_t)x) & 15) == 0;
   uint64_t nvec = vec ? n / 4 : 0;
   const float4* x4 = reinterpret_cast<const float4*>(x);
-  for (uint64_t i = tid; i < nvec; i += nth) {
-    float4 v = __ldcs(&x4[i]);
-    float a[4] = {v.x, v.y, v.z, v.w};
+  auto take = [&](float4 v) {
+    const float a[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       if (!isfinite(a[k])) {
         bad = 1;
       } else {
-        uint32_t key = order_key(a[k]);
+        const uint32_t key = order_key(a[k]);
         lo_inv = max(lo_inv, ~key);
         hi = max(hi, key);
       }
     }
+  };
+  // four independent 16-byte loads in flight per thread per iteration
+  uint64_t i = tid;
+  for (; i + 3 * nth < nvec; i += 4 * nth) {
+    const float4 v0 = __ldcs(&x4[i]), v1 = __ldcs(&x4[i + nth]), v2 = __ldcs(&x4[i + 2 * nth]),
+                 v3 = __ldcs(&x4[i + 3 * nth]);
+    take(v0);
+    take(v1);
+    take(v2);
+    take(v3);
   }
+  for (; i < nvec; i += nth) take(__ldcs(&x4[i]));
   for (uint64_t i = nvec * 4 + tid; i < n; i += nth) {
     float a = x[i];
     if (!isfinite(a)) {
