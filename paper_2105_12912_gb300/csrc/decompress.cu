@@ -515,8 +515,9 @@ constexpr int kRecThreads = 256;
 
 __device__ __forceinline__ float scale(int32_t k, float ebx2) { return __fmul_rn(__int2float_rn(k), ebx2); }
 
+// codes: the block's 4096 code slots (global memory, or a shared-memory copy)
 template <int ND>
-__device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q) {
+__device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, const uint16_t* codes) {
   const int tid = threadIdx.x;
   if (a.dead || (a.st->status & ERR_CORRUPT)) return;
   uint32_t org[3], w[3];
@@ -524,11 +525,15 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q) 
   const uint32_t m = w[0] * w[1] * w[2];
   const int32_t r = (int32_t)a.radius;
   const float ebx2 = a.ebx2_f;
-  // codes -> q' = q - r
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(a.codes + (uint64_t)b * kSlots);
+  const uint32_t rs = a.rec_start[b], re = a.rec_start[b + 1];
+  const uint2* rec = reinterpret_cast<const uint2*>(a.ar + a.off_rec);
+  // a full 3-D block without records reads its codes directly; otherwise
+  // codes -> q' = q - r in s_q, then the outliers' deltas
+  const bool direct = ND == 3 && m == (uint32_t)kSlots && rs == re;
+  if (!direct) {
+    const uint4* src = reinterpret_cast<const uint4*>(codes);
     for (uint32_t i = tid; i < (m + 7) / 8; i += kRecThreads) {
-      const uint4 v = __ldcs(&src[i]);
+      const uint4 v = src[i];
       const uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int k = 0; k < 4; k++) {
@@ -536,15 +541,13 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q) 
         s_q[8 * i + 2 * k + 1] = (int32_t)(u[k] >> 16) - r;
       }
     }
+    __syncthreads();
+    for (uint32_t i = rs + tid; i < re; i += kRecThreads) {
+      const uint2 kv = rec[i];
+      if ((kv.x & 1u) == 0) s_q[(kv.x >> 1) % kSlots] = (int32_t)kv.y;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const uint32_t rs = a.rec_start[b], re = a.rec_start[b + 1];
-  const uint2* rec = reinterpret_cast<const uint2*>(a.ar + a.off_rec);
-  for (uint32_t i = rs + tid; i < re; i += kRecThreads) {
-    const uint2 kv = rec[i];
-    if ((kv.x & 1u) == 0) s_q[(kv.x >> 1) % kSlots] = (int32_t)kv.y;
-  }
-  __syncthreads();
   const uint64_t ny = a.g.n[1], nx = a.g.n[2];
   float* __restrict__ out = a.out;
   if (ND == 1) {
@@ -597,7 +600,8 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q) 
     const uint32_t x = tid & 15, y = tid >> 4;
     int32_t v[16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = s_q[(i * 16 + y) * 16 + x];
+    for (int i = 0; i < 16; i++)
+      v[i] = direct ? (int32_t)codes[(i * 16 + y) * 16 + x] - r : s_q[(i * 16 + y) * 16 + x];
 #pragma unroll
     for (int i = 1; i < 16; i++)
       if (i & 7) v[i] += v[i - 1];
@@ -677,10 +681,50 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q) 
   }
 }
 
+// Persistent: CTA c takes blocks c, c + grid, ...; while it reconstructs one, a bulk
+// copy is already bringing the next block's 8 KB of codes into shared memory.
 template <int ND>
 __global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) {
+  __shared__ __align__(128) uint16_t s_codes[2][kSlots];
   __shared__ __align__(16) int32_t s_q[kSlots];
-  reconstruct_body<ND>(a, blockIdx.x, s_q);
+  __shared__ unsigned long long s_bar[2];
+  __shared__ uint32_t s_fail;
+  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
+  const int tid = threadIdx.x;
+  const uint32_t grid = gridDim.x;
+  auto issue = [&](uint32_t b, int buf) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&s_bar[buf], kSlots * 2);
+    bulk_load(s_codes[buf], a.codes + (uint64_t)b * kSlots, kSlots * 2, &s_bar[buf]);
+  };
+  if (tid == 0) {
+    mbar_init(&s_bar[0]);
+    mbar_init(&s_bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+    if (blockIdx.x < a.g.nblk) issue(blockIdx.x, 0);
+  }
+  __syncthreads();
+  uint32_t it = 0, b = blockIdx.x;
+  bool next_issued = false;
+  for (; b < a.g.nblk; b += grid, it++) {
+    const int cur = it & 1;
+    next_issued = b + grid < a.g.nblk;
+    if (tid == 0 && next_issued) issue(b + grid, cur ^ 1);
+    if (!mbar_wait(&s_bar[cur], (it >> 1) & 1u, kSpinLimit)) {
+      atomicOr(&a.st->status, ERR_TIMEOUT);
+      s_fail = 1;
+    }
+    __syncthreads();
+    if (s_fail) break;
+    reconstruct_body<ND>(a, b, s_q, s_codes[cur]);
+    __syncthreads();
+  }
+  if (s_fail && tid == 0) {
+    // wait once more (bounded) for this block's copy and the next one in flight
+    mbar_wait(&s_bar[it & 1], (it >> 1) & 1u, kSpinLimit);
+    if (next_issued) mbar_wait(&s_bar[(it + 1) & 1], ((it + 1) >> 1) & 1u, kSpinLimit);
+  }
 }
 
 // =================================================================================
@@ -794,9 +838,10 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_batch_kernel(const De
   const int f = field_of(tile0, nfields, blockIdx.x);
   const DecodeArgs& a = tasks[f];
   const uint32_t b = blockIdx.x - tile0[f];
-  if (a.g.ndim == 1) reconstruct_body<1>(a, b, s_q);
-  else if (a.g.ndim == 2) reconstruct_body<2>(a, b, s_q);
-  else reconstruct_body<3>(a, b, s_q);
+  const uint16_t* codes = a.codes + (uint64_t)b * kSlots;
+  if (a.g.ndim == 1) reconstruct_body<1>(a, b, s_q, codes);
+  else if (a.g.ndim == 2) reconstruct_body<2>(a, b, s_q, codes);
+  else reconstruct_body<3>(a, b, s_q, codes);
 }
 
 cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
@@ -856,14 +901,25 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
   trace_begin(K_RLE_EXPAND, s);
   rle_expand_kernel<<<a.g.nblk, kRleThreads, 0, s>>>(a);
   trace_end(K_RLE_EXPAND, s);
-  trace_begin(K_RECONSTRUCT, s);
-  if (a.g.ndim == 1)
-    reconstruct_kernel<1><<<a.g.nblk, kRecThreads, 0, s>>>(a);
-  else if (a.g.ndim == 2)
-    reconstruct_kernel<2><<<a.g.nblk, kRecThreads, 0, s>>>(a);
-  else
-    reconstruct_kernel<3><<<a.g.nblk, kRecThreads, 0, s>>>(a);
-  trace_end(K_RECONSTRUCT, s);
+  {
+    static int sms = 0, occ[4] = {0, 0, 0, 0};
+    auto k = a.g.ndim == 1 ? reconstruct_kernel<1> : (a.g.ndim == 2 ? reconstruct_kernel<2> : reconstruct_kernel<3>);
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (occ[a.g.ndim] == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[a.g.ndim], k, kRecThreads, 0);
+      if (occ[a.g.ndim] <= 0) occ[a.g.ndim] = 1;
+    }
+    // persistent only when every CTA gets several blocks to prefetch
+    const uint64_t cap = (uint64_t)sms * occ[a.g.ndim];
+    const unsigned grid = (unsigned)(a.g.nblk <= 3 * cap ? a.g.nblk : cap);
+    trace_begin(K_RECONSTRUCT, s);
+    k<<<grid, kRecThreads, 0, s>>>(a);
+    trace_end(K_RECONSTRUCT, s);
+  }
   return cudaGetLastError();
 }
 
