@@ -293,6 +293,20 @@ def batched_comparison(args, dev, flush):
     }
 
 
+def kernel_source_rev():
+    """Hash of the CUDA sources: DRAM counters taken from an ncu capture are reported
+    only while the kernels they measured are unchanged."""
+    import hashlib
+    root = os.path.join(ROOT, "paper_2105_12912_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(root)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(root, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def run_ours(args):
     from paper_2105_12912_gb300 import api, synth
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -391,8 +405,8 @@ def run_ours(args):
     if os.path.exists(tpath):
         try:
             tj = json.load(open(tpath))
-            ent = tj.get(f"{args.workload}:{dom}")
-            if ent and ent.get("source_rev") == tj.get("kernel_rev"):
+            ent = tj.get("entries", {}).get(f"{args.workload}:{dom}")
+            if ent and tj.get("source_rev") == kernel_source_rev():
                 traffic = ent.get("bytes_per_launch")
         except Exception:
             traffic = None
