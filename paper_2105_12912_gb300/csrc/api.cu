@@ -42,6 +42,7 @@ struct Header {
   float eb_f;
   uint32_t radius, lanes, flags;
   uint64_t nblk, n_rec, n_out, n_patch, payload, total;
+  uint32_t n_codec[3];
 };
 
 // Header checks that need no device data (magic, shape, bound, section sizes).  With
@@ -66,6 +67,7 @@ csz_status parse_header(const uint8_t* h, size_t bytes, Header& H, Geom& g, bool
   memcpy(&H.n_patch, h + 88, 8);
   memcpy(&H.payload, h + 96, 8);
   memcpy(&H.total, h + 104, 8);
+  memcpy(H.n_codec, h + 116, 12);
   if (H.magic != kMagic || H.version != kVersion) return CSZ_E_CORRUPT;
   if (H.ndim < 1 || H.ndim > 3 || H.eb_mode > 1) return CSZ_E_CORRUPT;
   if (!make_geom(H.ndim, H.dims, g)) return CSZ_E_CORRUPT;
@@ -382,6 +384,7 @@ csz_status csz_decompress(const uint8_t* d_ar, size_t bytes, float* d_out, uint6
   da.n_rec = H.n_rec;
   da.payload = H.payload;
   da.flags = H.flags;
+  for (int i = 0; i < 3; i++) da.n_codec[i] = H.n_codec[i];
   da.radius = H.radius;
   da.ebx2_f = 2.0f * H.eb_f;
   da.blk_off = at<uint64_t>(d_ws, L.blk_off);

@@ -688,9 +688,14 @@ __device__ inline void ihs_emit2(const uint16_t* sym, uint32_t m, const uint64_t
   const uint32_t h = huff_split(m);
   const uint16_t* ss = sym + (sidx ? h : 0);
   const uint32_t t0 = 16 * wl;
-  for (uint32_t i = tid; i < 64 * kLaneWords; i += blockDim.x) lanebuf[i] = 0;
-  __syncthreads();
   uint32_t* mine = lanebuf + kLaneWords * (32 * sidx + l);
+  // each thread clears the words its bits land in, plus the next one (a unit read
+  // takes two words); together the threads of a lane clear every word that is read
+  {
+    const uint32_t w0 = P.pre >> 5, w1 = min((P.pre + P.cum + 31) >> 5, kLaneWords - 1);
+    for (uint32_t wi = w0; wi <= w1; wi++) mine[wi ^ l] = 0;
+  }
+  __syncthreads();
   uint32_t p = P.pre;
 #pragma unroll 4
   for (int i = 0; i < 16; i++) {

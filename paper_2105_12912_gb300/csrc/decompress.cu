@@ -46,6 +46,8 @@ __device__ void dec_prep_body(const DecodeArgs& a) {
     a.blk_off[a.g.nblk] = carry;
     if (carry != a.payload) bad = true;
     if ((s_nc[CODEC_HUFF] && !(a.flags & 1u)) || (s_nc[CODEC_RLE_HUFF] && !(a.flags & 2u))) bad = true;
+    for (int c = 0; c < 3; c++)
+      if (s_nc[c] != a.n_codec[c]) bad = true;  // the header's counts decide which kernels run
   }
   if (bad) flag(a.st, ERR_CORRUPT);
 }
@@ -764,6 +766,7 @@ __global__ void dec_header_batch_kernel(DecodeArgs* tasks, int nfields) {
     memcpy(&n_patch, h + 88, 8);
     memcpy(&payload, h + 96, 8);
     memcpy(&total, h + 104, 8);
+    memcpy(a.n_codec, h + 116, 12);
     ok = magic == kMagic && version == kVersion && ndim == g.ndim && mode <= 1;
     for (int d = 0; d < 3 && ok; d++) {
       const uint64_t want = d < g.ndim ? (uint64_t)g.n[3 - g.ndim + d] : 0ull;
@@ -898,9 +901,11 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
     stream_decode_kernel<<<grid, 32 * kStreamWarps, lut_bytes, s>>>(a);
     trace_end(K_STREAM_DECODE, s);
   }
-  trace_begin(K_RLE_EXPAND, s);
-  rle_expand_kernel<<<a.g.nblk, kRleThreads, 0, s>>>(a);
-  trace_end(K_RLE_EXPAND, s);
+  if (a.n_codec[CODEC_RLE] + a.n_codec[CODEC_RLE_HUFF]) {  // run blocks present
+    trace_begin(K_RLE_EXPAND, s);
+    rle_expand_kernel<<<a.g.nblk, kRleThreads, 0, s>>>(a);
+    trace_end(K_RLE_EXPAND, s);
+  }
   {
     static int sms = 0, occ[4] = {0, 0, 0, 0};
     auto k = a.g.ndim == 1 ? reconstruct_kernel<1> : (a.g.ndim == 2 ? reconstruct_kernel<2> : reconstruct_kernel<3>);

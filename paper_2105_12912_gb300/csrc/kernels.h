@@ -132,6 +132,7 @@ struct DecodeArgs {
   uint64_t off_codec, off_bb, off_rec, off_pay, off_books;
   uint64_t n_rec, payload;
   uint32_t flags, radius;
+  uint32_t n_codec[3];  // blocks per codec, as the header states (checked against the codec bytes)
   float ebx2_f;
   uint64_t* blk_off;   // [nblk+1]
   uint32_t* rec_start; // [nblk+1]
