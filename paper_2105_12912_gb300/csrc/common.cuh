@@ -720,25 +720,50 @@ __device__ inline void ihs_emit2(const uint16_t* sym, uint32_t m, const uint64_t
   for (uint32_t v = 0; v < wl; v++) base += scratch[4 * sidx + v];
   if (tid == 0) out16[0] = (uint16_t)units_a;
   const uint32_t lt = (1u << l) - 1u;
+  auto unit_at = [&](uint32_t k) -> uint16_t {  // unit k of this lane's string
+    const uint32_t q = 16 * k, wi = q >> 5, off = q & 31;
+    const uint64_t two = ((uint64_t)mine[wi ^ l] << 32) | (uint64_t)mine[(wi + 1) ^ l];
+    return (uint16_t)(two >> (48 - off));
+  };
   uint32_t c = P.pre, uprev = u_begin;
-#pragma unroll 1
-  for (int i = 0; i < 16; i++) {
-    const uint32_t cn = c + plan_len(P, i);
-    const uint32_t u = (cn + 15) >> 4;
-    const uint32_t D = u - uprev;
-#pragma unroll 1
-    for (uint32_t r = 1; r <= 4; r++) {
-      const uint32_t br = __ballot_sync(~0u, D >= r);
-      if (!br) break;
-      if (D >= r) {
-        const uint32_t q = 16 * (uprev + r - 1), wi = q >> 5, off = q & 31;
-        const uint64_t two = ((uint64_t)mine[wi ^ l] << 32) | (uint64_t)mine[(wi + 1) ^ l];
-        out16[base + __popc(br & lt)] = (uint16_t)(two >> (48 - off));
-      }
-      base += __popc(br);
+  // four steps at a time; a lane takes two or more units in one step only for a code
+  // longer than 16 bits, so usually one ballot per step gives every position
+#pragma unroll
+  for (int i0 = 0; i0 < 16; i0 += 4) {
+    uint32_t D[4], up[4];
+    bool multi = false;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t cn = c + plan_len(P, i0 + k);
+      const uint32_t u = (cn + 15) >> 4;
+      D[k] = u - uprev;
+      up[k] = uprev;
+      multi |= D[k] >= 2;
+      c = cn;
+      uprev = u;
     }
-    c = cn;
-    uprev = u;
+    if (!__any_sync(~0u, multi)) {
+      uint32_t b1[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) b1[k] = __ballot_sync(~0u, D[k] != 0);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        if (D[k]) out16[base + __popc(b1[k] & lt)] = unit_at(up[k]);
+        base += __popc(b1[k]);
+      }
+    } else {
+      // rounds, as the decoder takes them
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+#pragma unroll 1
+        for (uint32_t r = 1; r <= 4; r++) {
+          const uint32_t br = __ballot_sync(~0u, D[k] >= r);
+          if (!br) break;
+          if (D[k] >= r) out16[base + __popc(br & lt)] = unit_at(up[k] + r - 1);
+          base += __popc(br);
+        }
+      }
+    }
   }
   __syncthreads();
 }
