@@ -284,9 +284,12 @@ __device__ __forceinline__ bool prequant_fast(float x, float eb_f, float ebx2_f,
 }
 
 // Binary logarithm in Q16 by bit-by-bit squaring of the mantissa (integer only).
-__device__ __forceinline__ uint32_t log2_q16(uint64_t v) {
+// constexpr so that the same routine also fills the table of small arguments below.
+__host__ __device__ constexpr uint32_t log2_q16(uint64_t v) {
   if (v == 0) return 0;
-  uint32_t e = 63 - __clzll((long long)v);
+  uint32_t e = 0;
+  for (uint32_t s = 32; s; s >>= 1)
+    if (v >> (e + s)) e += s;
   uint64_t m = e >= 31 ? (v >> (e - 31)) : (v << (31 - e));
   uint32_t frac = 0;
 #pragma unroll 1
@@ -300,6 +303,23 @@ __device__ __forceinline__ uint32_t log2_q16(uint64_t v) {
   }
   return e * 65536u + frac;
 }
+
+// log2_q16 of 0..4096 (every count a codec block can hold), evaluated at compile
+// time: block statistics look their per-bin terms up instead of squaring 16 times.
+struct Log2Table {
+  uint32_t v[kSlots + 1];
+};
+constexpr Log2Table make_log2_table() {
+  Log2Table t{};
+  for (uint32_t i = 0; i <= (uint32_t)kSlots; i++) t.v[i] = log2_q16(i);
+  return t;
+}
+static_assert(make_log2_table().v[1] == 0u && make_log2_table().v[2] == 65536u &&
+                  make_log2_table().v[kSlots] == 12u * 65536u,
+              "log2 table: exact powers of two");
+__device__ const Log2Table kLog2Table = make_log2_table();
+
+__device__ __forceinline__ uint32_t log2_q16_small(uint32_t v) { return __ldg(&kLog2Table.v[v]); }
 
 // ---------------------------------------------------------------------------------
 // canonical Huffman codes from lengths (block-wide).  Codes are ordered by

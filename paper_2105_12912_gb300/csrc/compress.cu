@@ -698,37 +698,58 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
     __syncthreads();
     for (uint32_t i = tid; i < nr; i += kEncThreads) atomicAdd(&s_hist[s_rv[i]], (uint32_t)s_rl[i]);
     __syncthreads();
+    // block statistics in one pass and one reduction: entropy sum, |delta| sum, top
+    // count, and (selector) code changes at distance 8
     uint64_t S_ = 0, absd = 0;
-    uint32_t f1 = 0;
+    uint32_t f1 = 0, var8 = 0;
     for (int c = tid; c < kNsymCode; c += kEncThreads) {
       const uint32_t h = s_hist[c];
       if (h) {
-        S_ += (uint64_t)h * log2_q16(h);
+        S_ += (uint64_t)h * log2_q16_small(h);
         f1 = max(f1, h);
         if (c != 0) absd += (uint64_t)h * (uint64_t)abs((int)c - (int)r);
       }
     }
-    S_ = block_sum<uint64_t>(S_, s_scan64);
-    absd = block_sum<uint64_t>(absd, s_scan64);
-    f1 = block_max_u32(f1, s_scan);
-    const int64_t Lm = log2_q16(m);
-    const int64_t NH = (int64_t)m * Lm - (int64_t)S_;
+    const bool want_var8 = !(sel == SEL_HEURISTIC && !analyze);
+    if (want_var8)
+      for (uint32_t j = tid; j + 8 < m; j += kEncThreads) var8 += s_c[j] != s_c[j + 8];
+    S_ = warp_sum(S_);
+    absd = warp_sum(absd);
+    var8 = warp_sum(var8);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) f1 = max(f1, __shfl_xor_sync(~0u, f1, o));
+    if ((tid & 31) == 0) {
+      s_scan64[4 * wid + 0] = S_;
+      s_scan64[4 * wid + 1] = absd;
+      s_scan64[4 * wid + 2] = f1;
+      s_scan64[4 * wid + 3] = var8;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      S_ = absd = 0;
+      f1 = var8 = 0;
+      for (int v = 0; v < kEncThreads / 32; v++) {
+        S_ += s_scan64[4 * v + 0];
+        absd += s_scan64[4 * v + 1];
+        f1 = max(f1, (uint32_t)s_scan64[4 * v + 2]);
+        var8 += (uint32_t)s_scan64[4 * v + 3];
+      }
+    }
+    const int64_t Lm = log2_q16_small(m);
+    const int64_t NH = (int64_t)m * Lm - (int64_t)S_;  // meaningful in thread 0
     if (sel == SEL_HEURISTIC && !analyze) {
       if (tid == 0) {
         int64_t Rm = 0;
         if (10ll * f1 > 4ll * m) {
           const int64_t rest = (int64_t)m - f1;
-          Rm = (int64_t)m * 65536 + (int64_t)f1 * log2_q16(f1) +
-               (rest > 0 ? rest * (int64_t)log2_q16((uint64_t)rest) : 0) - (int64_t)m * Lm;
+          Rm = (int64_t)m * 65536 + (int64_t)f1 * log2_q16_small(f1) +
+               (rest > 0 ? rest * (int64_t)log2_q16_small((uint32_t)rest) : 0) - (int64_t)m * Lm;
           if (Rm < 0) Rm = 0;
         }
         const int64_t est = NH + Rm;
         s_codec = (100 * est <= 109ll * (int64_t)m * 65536) ? CODEC_RLE_HUFF : CODEC_HUFF;
       }
     } else {
-      uint32_t var8 = 0;
-      for (uint32_t j = tid; j + 8 < m; j += kEncThreads) var8 += s_c[j] != s_c[j + 8];
-      var8 = block_sum<uint32_t>(var8, s_scan);
       if (tid == 0) {
         const uint32_t zero = s_hist[r];
         const uint32_t outl = s_hist[0];

@@ -58,6 +58,7 @@ struct Smem {
   uint32_t next[kSlots / 32];
   unsigned long long scan[33];
   unsigned long long bar[2];    // mbarriers of the two buffers
+  uint32_t box[2][6];           // origin and extent of each buffer's tile (thread 0 writes)
 };
 
 // One TMA tile copy (box at element coordinates c0 (x), c1, c2) into shared memory.
@@ -88,10 +89,8 @@ __device__ __forceinline__ void tma_load(int rank, void* dst, const CUtensorMap*
 
 // Start fetching tile b of task T into buffer `buf` (thread 0 only).  The buffer was
 // last touched by ordinary loads and stores, hence the proxy fence.
-__device__ void issue_tile(const ConstructTask* T, uint32_t b, float* buf, unsigned long long* bar) {
+__device__ void issue_tile(const ConstructTask* T, const uint32_t* org, float* buf, unsigned long long* bar) {
   const Geom& g = T->a.g;
-  uint32_t org[3], w[3];
-  block_box(g, b, org, w);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   mbar_expect_tx(bar, kTileBytes);
   if (g.ndim == 1) {
@@ -235,37 +234,48 @@ __device__ __noinline__ uint32_t edge_codes(const ConstructArgs& A, uint32_t b, 
 }
 
 // ---- one tile ------------------------------------------------------------------------
-// Codes, records and histogram updates of codec block b from the box in `in` (which
-// this call overwrites with k and outlier deltas).  Thread 0 adds the tile's record
-// and patch counts to n_rec_acc / n_patch_acc.
+// Codes, records and histogram updates of codec block b (origin box[0..2], extent
+// box[3..5]) from the box in `in` (which this call overwrites with k and outlier
+// deltas).  Thread 0 adds the tile's record and patch counts to n_rec_acc /
+// n_patch_acc.
 template <int ND>
-__device__ void process_tile(const ConstructArgs& A, uint32_t b, Smem& S, float* in, uint32_t& n_rec_acc,
-                             uint32_t& n_patch_acc) {
+__device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t* box, Smem& S, float* in,
+                             uint32_t& n_rec_acc, uint32_t& n_patch_acc) {
   const int tid = threadIdx.x, lane = tid & 31;
-  const Geom& g = A.g;
-  uint32_t org[3], w[3];
-  block_box(g, b, org, w);
+  const uint32_t w[3] = {box[3], box[4], box[5]};
   const uint32_t m = w[0] * w[1] * w[2];
   const float eb_f = A.st->eb_f, ebx2_f = A.st->ebx2_f, ebx2_r = A.st->ebx2_r;
   const int32_t r = (int32_t)A.radius;
+  const Geom& g = A.g;
   const bool full = w[0] == g.blk[0] && w[1] == g.blk[1] && w[2] == g.blk[2];
   int32_t* s_k = reinterpret_cast<int32_t*>(in);
   int32_t* dglob = A.deltas + (uint64_t)b * kSlots;  // outlier residuals of this block, by slot
   uint32_t err = 0;
 
-  // postquantization of a full warp step: code, outlier delta, code histogram (one
-  // add for the whole warp when all 32 codes agree, as in zero regions)
-  auto post = [&](int32_t delta, uint32_t j) -> uint16_t {
-    const uint16_t q = (delta > -r && delta < r) ? (uint16_t)(delta + r) : (uint16_t)0;
-    S.c[j] = q;
+  // Postquantization of one warp step over the 32 consecutive slots of word j >> 5:
+  // code, outlier delta, the word's outlier / patch / run-head bits, and the code
+  // histogram (one add for the whole step when its 32 codes agree, as in zero
+  // regions).  Head bit 0 compares with the previous word, written by another warp:
+  // it is left clear here and set after the tile.
+  auto post = [&](int32_t delta, uint32_t j, bool patch_step, bool patch_bit) {
+    const uint32_t u = (uint32_t)(delta + r);
+    const uint32_t q = u - 1u < (uint32_t)(2 * r - 1) ? u : 0u;  // |delta| < r
+    S.c[j] = (uint16_t)q;
     if (q == 0) dglob[j] = delta;
-    const uint32_t q0 = __shfl_sync(~0u, (uint32_t)q, 0);
-    if (__all_sync(~0u, q == q0)) {
-      if (lane == 0) atomicAdd(&S.hc[q0], 32u);
+    const uint32_t left = __shfl_up_sync(~0u, q, 1);
+    const uint32_t hd = __ballot_sync(~0u, lane != 0 && q != left);
+    const uint32_t ob = __ballot_sync(~0u, q == 0);
+    const uint32_t pb = patch_step ? __ballot_sync(~0u, patch_bit) : 0u;
+    if (hd == 0) {
+      if (lane == 0) atomicAdd(&S.hc[q], 32u);
     } else {
       atomicAdd(&S.hc[q], 1u);
     }
-    return q;
+    if (lane == 0) {
+      S.head[j >> 5] = hd;
+      S.outl[j >> 5] = ob;
+      S.patch[j >> 5] = pb;
+    }
   };
 
   // ---- prequantization, Lorenzo residual (Sec. IV-B2), postquantization ----------
@@ -296,22 +306,32 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, Smem& S, float*
         }
       }
       const int32_t prev = __shfl_up_sync(~0u, k[15], 1);
-      uint32_t om = 0;
+      uint32_t om = 0, hm = 0, qprev = 0, qfirst = 0;
 #pragma unroll
       for (int i = 0; i < 16; i++) {
         const uint32_t j = 16 * tid + i;
         const int32_t left = i ? k[i - 1] : prev;
         const int32_t delta = (j & 255) ? k[i] - left : k[i];
-        const uint16_t q = (delta > -r && delta < r) ? (uint16_t)(delta + r) : (uint16_t)0;
-        S.c[j] = q;
+        const uint32_t u = (uint32_t)(delta + r);
+        const uint32_t q = u - 1u < (uint32_t)(2 * r - 1) ? u : 0u;  // |delta| < r
+        S.c[j] = (uint16_t)q;
         if (q == 0) dglob[j] = delta;
         atomicAdd(&S.hc[q], 1u);
         om |= (uint32_t)(q == 0) << i;
+        if (i == 0) qfirst = q;
+        else hm |= (uint32_t)(q != qprev) << i;
+        qprev = q;
       }
-      const uint32_t om2 = __shfl_down_sync(~0u, om, 1), pm2 = __shfl_down_sync(~0u, pm, 1);
+      // the first slot's left neighbour is the last slot of the lane below (lane 0:
+      // another warp's, set after the tile)
+      const uint32_t qbelow = __shfl_up_sync(~0u, qprev, 1);
+      if (lane != 0 && qfirst != qbelow) hm |= 1u;
+      const uint32_t om2 = __shfl_down_sync(~0u, om, 1), pm2 = __shfl_down_sync(~0u, pm, 1),
+                     hm2 = __shfl_down_sync(~0u, hm, 1);
       if ((lane & 1) == 0) {
         S.outl[tid >> 1] = om | (om2 << 16);
         S.patch[tid >> 1] = pm | (pm2 << 16);
+        S.head[tid >> 1] = hm | (hm2 << 16);
       }
     } else if (ND == 2) {
       // thread t: column xx = t & 63 of the 16-row chunk band t >> 6
@@ -339,13 +359,7 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, Smem& S, float*
         const int32_t left = __shfl_up_sync(~0u, k[i], 1);
         const int32_t delta = (xx & 15) ? k[i] - left : k[i];  // x difference
         const uint32_t j = (16 * ry + i) * 64 + xx;
-        const uint16_t q = post(delta, j);
-        const uint32_t ob = __ballot_sync(~0u, q == 0);
-        const uint32_t pb = anyp ? __ballot_sync(~0u, (pm >> i) & 1u) : 0u;
-        if (lane == 0) {
-          S.outl[j >> 5] = ob;
-          S.patch[j >> 5] = pb;
-        }
+        post(delta, j, anyp, (pm >> i) & 1u);
       }
     } else {
       // thread t: z column of (xx, yy) = (t & 15, t >> 4); z and x differences in
@@ -385,30 +399,33 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, Smem& S, float*
 #pragma unroll
       for (int i = 0; i < 16; i++) {
         const uint32_t j = (i * 16 + yy) * 16 + xx;
-        const uint16_t q = post(k[i] - below[i], j);
-        const uint32_t ob = __ballot_sync(~0u, q == 0);
-        const uint32_t pb = anyp ? __ballot_sync(~0u, (pm >> i) & 1u) : 0u;
-        if (lane == 0) {
-          S.outl[j >> 5] = ob;
-          S.patch[j >> 5] = pb;
-        }
+        post(k[i] - below[i], j, anyp, (pm >> i) & 1u);
       }
     }
     __syncthreads();
   } else {
     err |= edge_codes<ND>(A, b, S, in, w, m, dglob);
+    run_head_words(S.c, m, S.head);
+    __syncthreads();
   }
 
-  // ---- run heads and record counts: one block reduction of packed counts -------
+  // ---- head bit 0 of every word, then the tile's counts from the bit words -------
   // (outliers << 42 | patches << 21 | runs; each count is at most 4096)
-  const uint32_t my_runs = run_head_words(S.c, m, S.head);
-  const uint32_t lo = tid * kPer;
-  const uint32_t ob = (S.outl[lo >> 5] >> (lo & 31)) & 0xffffu;
-  const uint32_t pb = (S.patch[lo >> 5] >> (lo & 31)) & 0xffffu;
+  if (tid < kSlots / 32) {
+    uint32_t hw = S.head[tid];
+    if (full) {
+      const uint32_t j0 = 32u * tid;
+      hw |= (uint32_t)(tid == 0 || S.c[j0] != S.c[j0 - 1]);
+      S.head[tid] = hw;
+    }
+    const unsigned long long v = ((unsigned long long)__popc(S.outl[tid]) << 42) |
+                                 ((unsigned long long)__popc(S.patch[tid]) << 21) | (unsigned long long)__popc(hw);
+    const unsigned long long ws = warp_sum(v);
+    if (lane == 0) S.scan[tid >> 5] = ws;
+  }
+  __syncthreads();
+  const unsigned long long tot = S.scan[0] + S.scan[1] + S.scan[2] + S.scan[3];
   constexpr uint64_t kF = (1ull << 21) - 1;
-  unsigned long long tot;
-  block_excl_scan<unsigned long long>(
-      ((unsigned long long)__popc(ob) << 42) | ((unsigned long long)__popc(pb) << 21) | my_runs, S.scan, &tot);
   const uint32_t n_out = (uint32_t)(tot >> 42), n_patch = (uint32_t)((tot >> 21) & kF);
   const uint32_t nruns = (uint32_t)(tot & kF);
   if (tid == 0) {
@@ -487,20 +504,28 @@ __global__ __launch_bounds__(kThreads, 3) void construct_kernel(const __grid_con
   const int tid = threadIdx.x;
   auto task = [&](int f) -> const ConstructTask* { return tasks ? &tasks[f] : &one; };
   auto base = [&](int f) -> uint32_t { return tasks ? tile0[f] : 0u; };
-  auto claim = [&](int slot, int hint) {  // thread 0: next ticket, its field, start its fetch
-    const uint32_t t = atomicAdd(ticket, 1u);
+  // thread 0: ticket t goes to buffer `slot`: its field, its box, and its fetch.
+  // Tickets are drawn one tile ahead of the fetches (`pending`), so the counter's
+  // round trip overlaps the work on the current tile.
+  auto claim = [&](int slot, uint32_t t, int hint) {
     const int f = t < ntiles ? (tasks ? find_field(tile0, nfields, t, hint) : 0) : -1;
     s_t[slot] = t;
     s_f[slot] = f;
-    if (f >= 0 && task(f)->use_tma) issue_tile(task(f), t - base(f), S.in[slot], &S.bar[slot]);
+    if (f >= 0) {
+      uint32_t* bx = S.box[slot];
+      block_box(task(f)->a.g, t - base(f), bx, bx + 3);
+      if (task(f)->use_tma) issue_tile(task(f), bx, S.in[slot], &S.bar[slot]);
+    }
   };
+  uint32_t pending = 0;
 
   if (tid == 0) {
     mbar_init(&S.bar[0]);
     mbar_init(&S.bar[1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
-    claim(0, 0);
+    claim(0, atomicAdd(ticket, 1u), 0);
+    pending = atomicAdd(ticket, 1u);
   }
   for (int i = tid; i < kNsymCode + kNsymCode + kNsymLen; i += kThreads) S.hc[i] = 0;  // hc, hv, hl
   __syncthreads();
@@ -525,7 +550,10 @@ __global__ __launch_bounds__(kThreads, 3) void construct_kernel(const __grid_con
     if (f < 0) break;
     const ConstructTask* T = task(f);
     // claim the next tile and start its fetch before working on this one
-    if (tid == 0) claim(cur ^ 1, f);
+    if (tid == 0) {
+      claim(cur ^ 1, pending, f);
+      pending = atomicAdd(ticket, 1u);
+    }
     if (f != field) {
       // moving to another field: the previous one's histograms and counters go out
       if (field >= 0) {
@@ -549,9 +577,10 @@ __global__ __launch_bounds__(kThreads, 3) void construct_kernel(const __grid_con
     }
     __syncthreads();
     if (s_fail) break;
-    if (ND == 1 || (ND == 0 && A.g.ndim == 1)) process_tile<1>(A, b, S, S.in[cur], n_rec_acc, n_patch_acc);
-    else if (ND == 2 || (ND == 0 && A.g.ndim == 2)) process_tile<2>(A, b, S, S.in[cur], n_rec_acc, n_patch_acc);
-    else process_tile<3>(A, b, S, S.in[cur], n_rec_acc, n_patch_acc);
+    const uint32_t* bx = S.box[cur];
+    if (ND == 1 || (ND == 0 && A.g.ndim == 1)) process_tile<1>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
+    else if (ND == 2 || (ND == 0 && A.g.ndim == 2)) process_tile<2>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
+    else process_tile<3>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
     __syncthreads();
     cur ^= 1;
   }
