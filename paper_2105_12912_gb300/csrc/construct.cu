@@ -27,6 +27,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPer = kSlots / kThreads;  // 16 elements per thread
 constexpr uint32_t kTileBytes = kSlots * 4;
+constexpr int kHlShared = 256;  // run lengths counted in shared memory; longer runs go to the field's
+                                // histogram directly (they are rare: one per long constant stretch)
 
 template <int ND>
 struct Chunk;
@@ -50,7 +52,7 @@ struct Smem {
   uint16_t c[kSlots];           // codes of the current tile (dense order)
   uint32_t hc[kNsymCode];       // code histogram (per CTA, current field)
   uint32_t hv[kNsymCode];       // run-value histogram
-  uint32_t hl[kNsymLen];        // run-length histogram (length - 1)
+  uint32_t hl[kHlShared];       // run-length histogram (length - 1), short runs
   uint32_t patch[kSlots / 32];  // verbatim-patch positions
   uint32_t outl[kSlots / 32];   // outlier positions
   uint32_t head[kSlots / 32];   // run heads
@@ -393,13 +395,11 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t*
 #pragma unroll
       for (int i = 0; i < 16; i++) s_k[(i * 16 + yy) * 16 + xx] = k[i];
       __syncthreads();
-      int32_t below[16];
-#pragma unroll
-      for (int i = 0; i < 16; i++) below[i] = (yy & 7) ? s_k[(i * 16 + yy - 1) * 16 + xx] : 0;
 #pragma unroll
       for (int i = 0; i < 16; i++) {
         const uint32_t j = (i * 16 + yy) * 16 + xx;
-        post(k[i] - below[i], j, anyp, (pm >> i) & 1u);
+        const int32_t below = (yy & 7) ? s_k[(i * 16 + yy - 1) * 16 + xx] : 0;
+        post(k[i] - below, j, anyp, (pm >> i) & 1u);
       }
     }
     __syncthreads();
@@ -461,8 +461,10 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t*
         atomicAdd(&S.hv[v], 1u);
         if (len == 1)
           ones++;
-        else
+        else if (len <= (uint32_t)kHlShared)
           atomicAdd(&S.hl[len - 1], 1u);
+        else
+          atomicAdd(&A.hist_len[len - 1], 1u);
       }
     }
     ones = warp_sum(ones);
@@ -491,7 +493,7 @@ __device__ __forceinline__ int find_field(const uint32_t* tile0, int nfields, ui
 // count); batches pass a device table and tile0[f], the first global tile of field
 // f (tile0[nfields] = ntiles).
 template <int ND>  // 1, 2, 3; 0 = any (batches of mixed dimensionality)
-__global__ __launch_bounds__(kThreads, 3) void construct_kernel(const __grid_constant__ ConstructTask one,
+__global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_constant__ ConstructTask one,
                                                              const ConstructTask* __restrict__ tasks,
                                                              const uint32_t* __restrict__ tile0, int nfields,
                                                              uint32_t ntiles, uint32_t* ticket,
@@ -527,7 +529,7 @@ __global__ __launch_bounds__(kThreads, 3) void construct_kernel(const __grid_con
     claim(0, atomicAdd(ticket, 1u), 0);
     pending = atomicAdd(ticket, 1u);
   }
-  for (int i = tid; i < kNsymCode + kNsymCode + kNsymLen; i += kThreads) S.hc[i] = 0;  // hc, hv, hl
+  for (int i = tid; i < kNsymCode + kNsymCode + kHlShared; i += kThreads) S.hc[i] = 0;  // hc, hv, hl
   __syncthreads();
 
   int cur = 0, field = -1;
@@ -537,7 +539,7 @@ __global__ __launch_bounds__(kThreads, 3) void construct_kernel(const __grid_con
     const ConstructArgs& P = task(f)->a;
     flush_hist(S.hc, kNsymCode, P.hist_code);
     flush_hist(S.hv, kNsymCode, P.hist_val);
-    flush_hist(S.hl, kNsymLen, P.hist_len);
+    flush_hist(S.hl, kHlShared, P.hist_len);
     if (tid == 0) {
       if (n_rec_acc) atomicAdd(&P.st->n_rec, (unsigned long long)n_rec_acc);
       if (n_patch_acc) atomicAdd(&P.st->n_patch, (unsigned long long)n_patch_acc);
@@ -559,7 +561,7 @@ __global__ __launch_bounds__(kThreads, 3) void construct_kernel(const __grid_con
       if (field >= 0) {
         flush_field(field);
         __syncthreads();
-        for (int i = tid; i < kNsymCode + kNsymCode + kNsymLen; i += kThreads) S.hc[i] = 0;
+        for (int i = tid; i < kNsymCode + kNsymCode + kHlShared; i += kThreads) S.hc[i] = 0;
       }
       field = f;
     }
