@@ -716,20 +716,43 @@ __device__ inline void ihs_emit2(const uint16_t* sym, uint32_t m, const uint64_t
     for (uint32_t wi = w0; wi <= w1; wi++) mine[wi ^ l] = 0;
   }
   __syncthreads();
-  uint32_t p = P.pre;
+  // codes gather in a 64-bit window (left-aligned, `fill` bits used, < 32 between
+  // codes); each completed word is stored.  Only the thread's first and last words
+  // can be shared with the neighbouring steps of the lane: those two are OR-ed in.
+  {
+    uint32_t wi = P.pre >> 5;
+    int fill = (int)(P.pre & 31);
+    uint64_t win = 0;
+    bool first = true;
+    auto flush = [&]() {
+      const uint32_t word = (uint32_t)(win >> 32);
+      if (first) atomicOr(&mine[wi ^ l], word);
+      else mine[wi ^ l] = word;
+      first = false;
+      win <<= 32;
+      fill -= 32;
+      wi++;
+    };
 #pragma unroll 4
-  for (int i = 0; i < 16; i++) {
-    int L = (int)plan_len(P, i);
-    if (L == 0) continue;
-    const uint64_t C = __ldg(&codes[ss[32 * (t0 + i) + l]]);
-    while (L > 0) {
-      const uint32_t wi = p >> 5, off = p & 31;
-      const int n = min(L, 32 - (int)off);
-      const uint32_t bits = (uint32_t)((C >> (L - n)) & ((n == 32) ? 0xffffffffull : ((1ull << n) - 1ull)));
-      atomicOr(&mine[wi ^ l], bits << (32 - off - n));
-      L -= n;
-      p += n;
+    for (int i = 0; i < 16; i++) {
+      const int L = (int)plan_len(P, i);
+      if (L == 0) continue;
+      const uint64_t C = __ldg(&codes[ss[32 * (t0 + i) + l]]);
+      if (L <= 32) {
+        win |= C << (64 - fill - L);
+        fill += L;
+        if (fill >= 32) flush();
+      } else {  // a code longer than 32 bits: its top L - 32 bits, then the low 32
+        const int hl = L - 32;
+        win |= (C >> 32) << (64 - fill - hl);
+        fill += hl;
+        if (fill >= 32) flush();
+        win |= (C & 0xffffffffull) << (32 - fill);
+        fill += 32;
+        flush();
+      }
     }
+    if (fill > 0) atomicOr(&mine[wi ^ l], (uint32_t)(win >> 32));
   }
   // units each warp's steps take, for the warp's first output position in its stream
   const uint32_t u_begin = (P.pre + 15) >> 4, u_end = (P.pre + P.cum + 15) >> 4;
