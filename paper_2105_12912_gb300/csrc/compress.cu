@@ -438,7 +438,7 @@ static size_t codebook_smem_bytes() { return 94208 + kNsymLen * 8; }
 // =================================================================================
 __device__ void finalize_body(const FinalizeArgs& a) {
   __shared__ uint32_t s_hdr[kHdr / 4];
-  __shared__ uint64_t s_total, s_off_books;
+  __shared__ uint64_t s_total, s_off_books, s_pay_end;
   __shared__ uint32_t s_flags;
   DevState* st = a.st;
   const int tid = threadIdx.x;
@@ -450,6 +450,7 @@ __device__ void finalize_body(const FinalizeArgs& a) {
     const uint64_t total = off_books + ((flags & 1) ? kNsymCode : 0) + ((flags & 2) ? kNsymCode + kNsymLen : 0);
     s_total = total;
     s_off_books = off_books;
+    s_pay_end = off_pay + payload;
     s_flags = flags;
     st->total = total;
     if (total > a.cap) atomicOr(&st->status, ERR_CAPACITY);
@@ -487,8 +488,7 @@ __device__ void finalize_body(const FinalizeArgs& a) {
   // zero padding: codec section, blk_bytes section, payload tail
   for (uint64_t i = kHdr + a.nblk + tid; i < a.off_bb; i += blockDim.x) ar[i] = 0;
   for (uint64_t i = a.off_bb + 4ull * a.nblk + tid; i < a.off_rec; i += blockDim.x) ar[i] = 0;
-  const uint64_t pay_end = a.off_rec + 8 * st->n_rec + st->payload;
-  for (uint64_t i = pay_end + tid; i < s_off_books; i += blockDim.x) ar[i] = 0;
+  for (uint64_t i = s_pay_end + tid; i < s_off_books; i += blockDim.x) ar[i] = 0;
   uint64_t o = s_off_books;
   if (s_flags & 1) {
     for (int i = tid; i < kNsymCode; i += blockDim.x) ar[o + i] = a.lens[i];
@@ -807,10 +807,17 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   if (codec == CODEC_RLE || codec == CODEC_RLE_HUFF) extract_runs();
   exact_sizes(codec == CODEC_HUFF, codec == CODEC_RLE, codec == CODEC_RLE_HUFF);
   const uint64_t size = codec == CODEC_HUFF ? size_h : (codec == CODEC_RLE ? 4ull * nr : size_rh);
+  // The block's codec and size are counted, then the block counts itself done with
+  // release semantics: the block that takes the last count (acquire) writes the
+  // header from complete totals once its own payload is out.  No other block's
+  // payload bytes are needed for that, so the count need not wait for them.
+  __shared__ bool s_last;
+  uint32_t done = 0;
   if (tid == 0) {
     lookback_publish(a.lb, b, size);
     atomicAdd(&a.st->ncodec[codec], 1u);
     atomicAdd(&a.st->payload, (unsigned long long)size);
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(done) : "l"(&a.st->encode_done) : "memory");
   }
 
   // payload assembly in shared memory while predecessors publish (every chosen size
@@ -841,6 +848,7 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   };
   const bool in_smem = size <= (uint64_t)kBufBytes;
   if (in_smem) assemble(reinterpret_cast<uint16_t*>(s_buf));
+  if (tid == 0) s_last = done == a.g.nblk - 1;
   __syncthreads();
 
   // placement
@@ -872,18 +880,8 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   } else {
     assemble(reinterpret_cast<uint16_t*>(dst));
   }
-  // the last block to finish writes the header, section padding and books
-  __shared__ bool s_last;
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    s_last = atomicAdd(&a.st->encode_done, 1u) == a.g.nblk - 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    finalize_body(a.fin);
-  }
+  // the block that counted last writes the header, section padding and books
+  if (s_last) finalize_body(a.fin);
 }
 
 // Blocks are taken in ticket order, so the payload look-back only ever waits on
