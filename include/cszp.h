@@ -92,6 +92,16 @@ csz_status csz_compress(const float* d_field, int ndim, const uint64_t* dims, in
                         size_t workspace_bytes, uint8_t* d_archive, size_t archive_cap,
                         size_t* h_archive_bytes, void* stream);
 
+/*
+ * csz_compress that also copies the archive's 128-byte header to h_header (host
+ * memory, 128 bytes) within its one synchronisation, for csz_decompress_async.
+ * h_header is written only when the call returns CSZ_OK; NULL is CSZ_E_ARG.
+ */
+csz_status csz_compress_with_header(const float* d_field, int ndim, const uint64_t* dims, int eb_mode,
+                                    double eb, const csz_options* opt, void* d_workspace,
+                                    size_t workspace_bytes, uint8_t* d_archive, size_t archive_cap,
+                                    size_t* h_archive_bytes, uint8_t* h_header, void* stream);
+
 /* Read shape and bound from an archive header held in host memory (first 128
    bytes suffice). */
 csz_status csz_archive_info(const uint8_t* h_archive, size_t bytes, int* ndim, uint64_t* dims,
@@ -107,6 +117,22 @@ csz_status csz_archive_info(const uint8_t* h_archive, size_t bytes, int* ndim, u
 csz_status csz_decompress(const uint8_t* d_archive, size_t bytes, float* d_out,
                           uint64_t out_cap_elems, void* d_workspace, size_t workspace_bytes,
                           void* stream);
+
+/*
+ * csz_decompress without any host synchronisation.  The caller passes the archive's
+ * 128-byte header as a host copy (h_header: e.g. from csz_compress_with_header, or
+ * read once and kept), so nothing is read back before the launches; the device
+ * compares the archive's own header with that copy and reports a mismatch as
+ * CSZ_E_CORRUPT.  The decompression's status (a csz_status value) is written to the
+ * device word *d_status when the work completes in stream order.  The call returns
+ * CSZ_OK once everything is enqueued, or an error it finds on the host before any
+ * launch (a header copy that does not parse against `bytes`: CSZ_E_CORRUPT;
+ * capacities: CSZ_E_CAPACITY; NULL pointers: CSZ_E_ARG).  d_out and the workspace
+ * must stay untouched until the status is read.
+ */
+csz_status csz_decompress_async(const uint8_t* d_archive, size_t bytes, const uint8_t* h_header,
+                                float* d_out, uint64_t out_cap_elems, void* d_workspace,
+                                size_t workspace_bytes, uint32_t* d_status, void* stream);
 
 /*
  * Decompression that allocates nothing and takes no workspace.  Some callers cannot

@@ -124,6 +124,54 @@ def decompress(archive: torch.Tensor, nbytes: int | None = None, out: torch.Tens
     return out, st
 
 
+def compress_with_header(field: torch.Tensor, eb: float, eb_mode: str = "rel", radius: int = 512,
+                         select: str = "exhaustive", weights: torch.Tensor | None = None,
+                         out: torch.Tensor | None = None, workspace: Workspace | None = None, stream=None):
+    """compress() that also returns the archive's 128-byte header as bytes (copied in
+    the same synchronisation), for decompress_async.  Returns (archive, nbytes, header)."""
+    if not (field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()):
+        raise ValueError("field must be a contiguous float32 CUDA tensor")
+    dims = tuple(field.shape)
+    if out is None:
+        out = torch.empty(max_archive_bytes(dims) or 1, dtype=torch.uint8, device=field.device)
+    ws = _ws(field.device, workspace).get(workspace_bytes(dims) or 256)
+    opt = L.csz_options()
+    opt.radius = int(radius)
+    opt.select = SELECT[select] if isinstance(select, str) else int(select)
+    if weights is not None:
+        if not (weights.is_cuda and weights.dtype == torch.float32 and weights.numel() == MLP_PARAMS):
+            raise ValueError("weights must be a float32 CUDA tensor of 1443 parameters")
+        opt.selector_weights = C.c_void_p(weights.data_ptr())
+    nbytes = C.c_size_t(0)
+    hdr = (C.c_uint8 * 128)()
+    st = L.lib().csz_compress_with_header(
+        C.c_void_p(field.data_ptr()), len(dims), L.dims_array(dims),
+        EB_MODES[eb_mode] if isinstance(eb_mode, str) else int(eb_mode), float(eb), C.byref(opt),
+        C.c_void_p(ws.data_ptr()), ws.numel(), C.c_void_p(out.data_ptr()), out.numel(), C.byref(nbytes), hdr,
+        _stream_ptr(stream))
+    _check(st, "csz_compress_with_header")
+    return out, int(nbytes.value), bytes(hdr)
+
+
+def decompress_async(archive: torch.Tensor, nbytes: int, header_bytes: bytes, out: torch.Tensor,
+                     status: torch.Tensor, workspace: Workspace | None = None, stream=None) -> None:
+    """Decompress without host synchronisation: the archive's header comes from the
+    host copy `header_bytes` (128 bytes), the outcome lands in `status` (an int32 CUDA
+    tensor of one element, a csz_status value) when the stream reaches it."""
+    if not (archive.is_cuda and archive.dtype == torch.uint8):
+        raise ValueError("archive must be a uint8 CUDA tensor")
+    if not (status.is_cuda and status.dtype == torch.int32 and status.numel() >= 1):
+        raise ValueError("status must be an int32 CUDA tensor")
+    if len(header_bytes) < 128:
+        raise ValueError("header_bytes must hold the archive's 128-byte header")
+    hb = (C.c_uint8 * 128).from_buffer_copy(bytes(header_bytes[:128]))
+    ws = _ws(archive.device, workspace).get(workspace_bytes(tuple(out.shape)) or 256)
+    st = L.lib().csz_decompress_async(C.c_void_p(archive.data_ptr()), int(nbytes), hb, C.c_void_p(out.data_ptr()),
+                                      out.numel(), C.c_void_p(ws.data_ptr()), ws.numel(),
+                                      C.c_void_p(status.data_ptr()), _stream_ptr(stream))
+    _check(st, "csz_decompress_async")
+
+
 def header(archive) -> dict:
     """Parsed 128-byte archive header (from a CUDA/CPU uint8 tensor or bytes)."""
     import struct

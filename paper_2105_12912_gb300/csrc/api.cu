@@ -121,7 +121,7 @@ extern "C" {
 
 static const char* const kKernelNames[K_COUNT] = {
     "range", "abs_params", "construct", "codebook", "encode", "dec_setup",
-    "stream_decode", "rle_expand", "reconstruct", "mlp_predict", "mlp_grad", "mlp_update"};
+    "stream_decode", "rle_expand", "reconstruct", "mlp_predict", "mlp_grad", "mlp_update", "dec_status"};
 
 int csz_kernel_count(void) { return K_COUNT; }
 
@@ -190,7 +190,7 @@ struct Analysis {
 // of every block), then one synchronisation to read the device status and size.
 csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
                         const csz_options* opt, void* d_ws, size_t ws_bytes, uint8_t* d_ar, size_t cap,
-                        size_t* h_bytes, const Analysis* an, void* stream) {
+                        size_t* h_bytes, const Analysis* an, void* stream, uint8_t* h_header = nullptr) {
   Geom g;
   if (!d_field || !d_ws) return CSZ_E_ARG;
   if (!an && (!d_ar || !h_bytes)) return CSZ_E_ARG;
@@ -308,11 +308,58 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
 
   DevState hs;
   if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
+  if (h_header && cudaMemcpyAsync(h_header, d_ar, kHdr, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CSZ_E_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
   trace_collect();
   const csz_status r = fold(hs.status);
   if (r != CSZ_OK) return r;
   if (h_bytes) *h_bytes = an ? 0 : (size_t)hs.total;
+  return CSZ_OK;
+}
+
+// Decode set-up from a parsed header h (read back from the device, or a host copy
+// the caller kept: then check_hdr makes the device compare it with the archive) and
+// the decode launches.  *st_out: the decompression's device state.
+csz_status enqueue_decode(const uint8_t* d_ar, size_t bytes, const uint8_t* h, bool check_hdr, float* d_out,
+                          uint64_t out_cap, void* d_ws, size_t ws_bytes, cudaStream_t s, DevState** st_out) {
+  Header H;
+  Geom g;
+  csz_status r = parse_header(h, bytes, H, g);
+  if (r != CSZ_OK) return r;
+  if (out_cap < g.nelem) return CSZ_E_CAPACITY;
+  const Layout L = layout(g);
+  if (ws_bytes < L.dec_total) return CSZ_E_CAPACITY;
+  DevState* st = at<DevState>(d_ws, L.st);
+  if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return CSZ_E_CUDA;
+  DecodeArgs da;
+  memset(&da, 0, sizeof(da));
+  da.g = g;
+  da.st = st;
+  da.ar = d_ar;
+  da.bytes = bytes;
+  da.off_codec = kHdr;
+  da.off_bb = kHdr + a8(g.nblk);
+  da.off_rec = da.off_bb + a8(4ull * g.nblk);
+  da.off_pay = da.off_rec + 8 * H.n_rec;
+  da.off_books = da.off_pay + a8(H.payload);
+  da.n_rec = H.n_rec;
+  da.payload = H.payload;
+  da.flags = H.flags;
+  for (int i = 0; i < 3; i++) da.n_codec[i] = H.n_codec[i];
+  da.radius = H.radius;
+  da.ebx2_f = 2.0f * H.eb_f;
+  da.blk_off = at<uint64_t>(d_ws, L.blk_off);
+  da.rec_start = at<uint32_t>(d_ws, L.rec_start);
+  da.tabs = at<DecTab>(d_ws, L.tabs);
+  da.codes = at<uint16_t>(d_ws, L.codes);
+  da.runv = da.codes;  // run values of an RLE+Huffman block wait in its own code slots
+  da.runl = at<uint16_t>(d_ws, L.runl);
+  da.out = d_out;
+  da.check_hdr = check_hdr ? 1 : 0;
+  memcpy(da.hdr, h, kHdr);
+  if (launch_decode(da, s) != cudaSuccess) return CSZ_E_CUDA;
+  *st_out = st;
   return CSZ_OK;
 }
 
@@ -361,45 +408,35 @@ csz_status csz_decompress(const uint8_t* d_ar, size_t bytes, float* d_out, uint6
   uint8_t h[kHdr];
   if (cudaMemcpyAsync(h, d_ar, kHdr, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
-  Header H;
-  Geom g;
-  csz_status r = parse_header(h, bytes, H, g);
+  DevState* st = nullptr;
+  const csz_status r = enqueue_decode(d_ar, bytes, h, false, d_out, out_cap, d_ws, ws_bytes, s, &st);
   if (r != CSZ_OK) return r;
-  if (out_cap < g.nelem) return CSZ_E_CAPACITY;
-  const Layout L = layout(g);
-  if (ws_bytes < L.dec_total) return CSZ_E_CAPACITY;
-  DevState* st = at<DevState>(d_ws, L.st);
-  if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return CSZ_E_CUDA;
-  DecodeArgs da;
-  memset(&da, 0, sizeof(da));
-  da.g = g;
-  da.st = st;
-  da.ar = d_ar;
-  da.bytes = bytes;
-  da.off_codec = kHdr;
-  da.off_bb = kHdr + a8(g.nblk);
-  da.off_rec = da.off_bb + a8(4ull * g.nblk);
-  da.off_pay = da.off_rec + 8 * H.n_rec;
-  da.off_books = da.off_pay + a8(H.payload);
-  da.n_rec = H.n_rec;
-  da.payload = H.payload;
-  da.flags = H.flags;
-  for (int i = 0; i < 3; i++) da.n_codec[i] = H.n_codec[i];
-  da.radius = H.radius;
-  da.ebx2_f = 2.0f * H.eb_f;
-  da.blk_off = at<uint64_t>(d_ws, L.blk_off);
-  da.rec_start = at<uint32_t>(d_ws, L.rec_start);
-  da.tabs = at<DecTab>(d_ws, L.tabs);
-  da.codes = at<uint16_t>(d_ws, L.codes);
-  da.runv = da.codes;  // run values of an RLE+Huffman block wait in its own code slots
-  da.runl = at<uint16_t>(d_ws, L.runl);
-  da.out = d_out;
-  if (launch_decode(da, s) != cudaSuccess) return CSZ_E_CUDA;
   DevState hs;
   if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
   trace_collect();
   return fold(hs.status);
+}
+
+csz_status csz_decompress_async(const uint8_t* d_ar, size_t bytes, const uint8_t* h_header, float* d_out,
+                                uint64_t out_cap, void* d_ws, size_t ws_bytes, uint32_t* d_status,
+                                void* stream) {
+  if (!d_ar || !h_header || !d_out || !d_ws || !d_status) return CSZ_E_ARG;
+  if (bytes < (size_t)kHdr) return CSZ_E_CORRUPT;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevState* st = nullptr;
+  const csz_status r = enqueue_decode(d_ar, bytes, h_header, true, d_out, out_cap, d_ws, ws_bytes, s, &st);
+  if (r != CSZ_OK) return r;
+  if (launch_dec_status(st, d_status, s) != cudaSuccess) return CSZ_E_CUDA;
+  return CSZ_OK;
+}
+
+csz_status csz_compress_with_header(const float* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
+                                    const csz_options* opt, void* d_ws, size_t ws_bytes, uint8_t* d_ar, size_t cap,
+                                    size_t* h_bytes, uint8_t* h_header, void* stream) {
+  if (!h_header) return CSZ_E_ARG;
+  return run_pipeline(d_field, ndim, dims, eb_mode, eb, opt, d_ws, ws_bytes, d_ar, cap, h_bytes, nullptr, stream,
+                      h_header);
 }
 
 }  // extern "C"

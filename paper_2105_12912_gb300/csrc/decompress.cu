@@ -10,6 +10,7 @@
 //                          per chunk (Alg. 1 l.9-13, Sec. IV-B2), scale by 2eb,
 //                          verbatim patches
 #include "common.cuh"
+#include "host.h"
 #include "kernels.h"
 
 namespace cszp {
@@ -24,6 +25,12 @@ __device__ void dec_prep_body(const DecodeArgs& a) {
   __shared__ uint64_t s_scan[33];
   __shared__ uint32_t s_nc[3];
   const int tid = threadIdx.x;
+  if (a.check_hdr && tid < 32) {
+    // the launch was set up from a host copy of the header: it must be this archive's
+    const uint8_t* h = a.ar + 4 * tid;
+    const uint32_t v = (uint32_t)h[0] | ((uint32_t)h[1] << 8) | ((uint32_t)h[2] << 16) | ((uint32_t)h[3] << 24);
+    if (__any_sync(~0u, v != a.hdr[tid]) && tid == 0) flag(a.st, ERR_CORRUPT);
+  }
   if (tid < 3) s_nc[tid] = 0;
   __syncthreads();
   uint64_t carry = 0;
@@ -869,6 +876,17 @@ cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
   trace_begin(K_RECONSTRUCT, s);
   reconstruct_batch_kernel<<<L.ntiles, kRecThreads, 0, s>>>(L.tasks, L.tile0, L.nfields);
   trace_end(K_RECONSTRUCT, s);
+  return cudaGetLastError();
+}
+
+__global__ void dec_status_kernel(const DevState* st, uint32_t* d_status) {
+  *d_status = (uint32_t)fold(st->status);
+}
+
+cudaError_t launch_dec_status(const DevState* st, uint32_t* d_status, cudaStream_t s) {
+  trace_begin(K_DEC_STATUS, s);
+  dec_status_kernel<<<1, 1, 0, s>>>(st, d_status);
+  trace_end(K_DEC_STATUS, s);
   return cudaGetLastError();
 }
 

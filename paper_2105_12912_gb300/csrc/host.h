@@ -99,7 +99,7 @@ inline T* at(void* base, uint64_t off) {
   return reinterpret_cast<T*>(static_cast<unsigned char*>(base) + off);
 }
 
-inline csz_status fold(uint32_t bits) {
+__host__ __device__ inline csz_status fold(uint32_t bits) {
   if (bits & ERR_NONFINITE) return CSZ_E_NONFINITE;
   if (bits & ERR_ARG) return CSZ_E_ARG;
   if (bits & ERR_RANGE) return CSZ_E_RANGE;

@@ -142,6 +142,8 @@ struct DecodeArgs {
   uint16_t* runl;      // nblk * 4096 decoded run lengths
   float* out;
   int dead;            // batches: the header failed validation, do nothing
+  int check_hdr;       // the arguments come from a host copy of the header (hdr): the
+  uint32_t hdr[32];    // set-up compares the device archive's header with it
 };
 
 // ---- per-kernel tracing (CUDA events around each launch; defined in api.cu) -------
@@ -158,6 +160,7 @@ enum KernelId : int {
   K_MLP_PREDICT,
   K_MLP_GRAD,
   K_MLP_UPDATE,
+  K_DEC_STATUS,
   K_COUNT
 };
 void trace_begin(int id, cudaStream_t s);
@@ -188,6 +191,8 @@ cudaError_t launch_encode_batch(const EncodeArgs* d_tasks, const uint32_t* d_til
                                 uint32_t* ticket, cudaStream_t s);
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);
+// the decompression's csz_status into a device word (asynchronous decompression)
+cudaError_t launch_dec_status(const DevState* st, uint32_t* d_status, cudaStream_t s);
 
 // Batched decompression: a device table of per-field decode arguments (headers are
 // read and checked on the device) and CTA prefixes per stage.
