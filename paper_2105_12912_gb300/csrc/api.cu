@@ -355,6 +355,7 @@ csz_status enqueue_decode(const uint8_t* d_ar, size_t bytes, const uint8_t* h, b
   da.codes = at<uint16_t>(d_ws, L.codes);
   da.runv = da.codes;  // run values of an RLE+Huffman block wait in its own code slots
   da.runl = at<uint16_t>(d_ws, L.runl);
+  da.runblk = at<uint32_t>(d_ws, L.runblk);
   da.out = d_out;
   da.check_hdr = check_hdr ? 1 : 0;
   memcpy(da.hdr, h, kHdr);

@@ -391,13 +391,16 @@ __device__ void codebook_body(const BookArgs& a, int role) {
       s_dep[i] = (i == nn - 1) ? 0 : 1;
     }
     __syncthreads();
+    // (done once every node's ancestor is the root: the depths no longer change)
     for (int step = 1; step < nn; step <<= 1) {
       uint16_t na[8], nd[8];
       int c = 0;
+      bool open = false;
       for (int i = tid; i < nn; i += blockDim.x) {
         const uint16_t an = s_anc[i];
         nd[c] = s_dep[i] + s_dep[an];
         na[c] = s_anc[an];
+        open |= na[c] != (uint16_t)(nn - 1);
         c++;
       }
       __syncthreads();
@@ -407,7 +410,7 @@ __device__ void codebook_body(const BookArgs& a, int role) {
         s_anc[i] = na[c];
         c++;
       }
-      __syncthreads();
+      if (!__syncthreads_or(open)) break;
     }
     for (int i = tid; i < L; i += blockDim.x) {
       const uint16_t d = s_dep[i];

@@ -33,21 +33,27 @@ __device__ void dec_prep_body(const DecodeArgs& a) {
   }
   if (tid < 3) s_nc[tid] = 0;
   __syncthreads();
-  uint64_t carry = 0;
+  // payload offsets and, packed above bit 48 of the same scan, the list of run blocks
+  constexpr uint64_t kLow = (1ull << 48) - 1;
+  uint64_t carry = 0, rcarry = 0;
   bool bad = false;
   for (uint32_t base = 0; base < a.g.nblk; base += blockDim.x) {
     const uint32_t b = base + tid;
     uint64_t bb = 0;
+    bool run = false;
     if (b < a.g.nblk) {
       const uint32_t c = a.ar[a.off_codec + b];
       bb = reinterpret_cast<const uint32_t*>(a.ar + a.off_bb)[b];
       if (c > 2 || (bb & 3)) bad = true;
       else atomicAdd(&s_nc[c], 1u);
+      run = c == CODEC_RLE || c == CODEC_RLE_HUFF;
     }
     uint64_t tot;
-    const uint64_t ex = block_excl_scan<uint64_t>(bb, s_scan, &tot);
-    if (b < a.g.nblk) a.blk_off[b] = carry + ex;
-    carry += tot;
+    const uint64_t ex = block_excl_scan<uint64_t>(bb | ((uint64_t)run << 48), s_scan, &tot);
+    if (b < a.g.nblk) a.blk_off[b] = carry + (ex & kLow);
+    if (run && a.runblk) a.runblk[rcarry + (ex >> 48)] = b;
+    carry += tot & kLow;
+    rcarry += tot >> 48;
   }
   if (tid == 0) {
     a.blk_off[a.g.nblk] = carry;
@@ -515,7 +521,14 @@ __device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
   o4[1] = make_uint4(vals[4], vals[5], vals[6], vals[7]);
 }
 
-__global__ __launch_bounds__(kRleThreads) void rle_expand_kernel(DecodeArgs a) { rle_expand_body(a, blockIdx.x); }
+// One CTA per listed run block (the list the set-up wrote; it holds exactly the
+// header's count unless the archive is corrupt, which the set-up has flagged).
+__global__ __launch_bounds__(kRleThreads) void rle_expand_kernel(DecodeArgs a) {
+  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
+  const uint32_t b = a.runblk[blockIdx.x];
+  if (b >= a.g.nblk) return;
+  rle_expand_body(a, b);
+}
 
 // =================================================================================
 // reconstruction: N-D partial sums per chunk (Sec. IV-B2), scaled by 2eb
@@ -921,7 +934,7 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
   }
   if (a.n_codec[CODEC_RLE] + a.n_codec[CODEC_RLE_HUFF]) {  // run blocks present
     trace_begin(K_RLE_EXPAND, s);
-    rle_expand_kernel<<<a.g.nblk, kRleThreads, 0, s>>>(a);
+    rle_expand_kernel<<<a.n_codec[CODEC_RLE] + a.n_codec[CODEC_RLE_HUFF], kRleThreads, 0, s>>>(a);
     trace_end(K_RLE_EXPAND, s);
   }
   {

@@ -46,7 +46,7 @@ inline bool make_geom(int ndim, const uint64_t* dims, Geom& g) {
 // offsets.
 struct Layout {
   uint64_t st, hist_code, hist_val, hist_len, lb_e, zero_end;
-  uint64_t lens, bcodes, blk_off, rec_start, tabs, codes, runl, dec_total;
+  uint64_t lens, bcodes, blk_off, rec_start, tabs, codes, runl, runblk, dec_total;
   uint64_t counts, masks, deltas, rec_off, runs, total;
 };
 
@@ -79,6 +79,8 @@ inline Layout layout(const Geom& g) {
   o += a256(2ull * kSlots * g.nblk);
   L.runl = o;
   o += a256(2ull * kSlots * g.nblk);
+  L.runblk = o;
+  o += a256(4ull * g.nblk);
   L.dec_total = o;
   L.counts = o;
   o += a256(4ull * g.nblk);

@@ -140,6 +140,7 @@ struct DecodeArgs {
   uint16_t* codes;     // nblk * 4096
   uint16_t* runv;      // decoded run values of RLE+Huffman blocks (may alias codes)
   uint16_t* runl;      // nblk * 4096 decoded run lengths
+  uint32_t* runblk;    // indices of the RLE / RLE+Huffman blocks, ascending (null: not listed)
   float* out;
   int dead;            // batches: the header failed validation, do nothing
   int check_hdr;       // the arguments come from a host copy of the header (hdr): the
