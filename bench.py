@@ -449,15 +449,17 @@ def run_ours(args):
 
         def e2e_step():
             xd.copy_(xh, non_blocking=True)
-            ar, nbe, _ = api.compress(xd, spec.eb, spec.eb_mode, select=args.select, out=arc, workspace=ws)
+            ar, nbe, hb = api.compress_with_header(xd, spec.eb, spec.eb_mode, select=args.select, out=arc,
+                                                   workspace=ws)
             arh[:nbe].copy_(ar[:nbe], non_blocking=True)
             ard[:nbe].copy_(arh[:nbe], non_blocking=True)
-            api.decompress(ard, nbe, out=rec, dims=dims, workspace=ws)
+            api.decompress_async(ard, nbe, hb, rec, dstatus, workspace=ws)
             outh.copy_(rec, non_blocking=True)
             nb_box[0] = nbe
 
         t_e = timed(e2e_step, max(10, args.steps // 2))
         torch.cuda.synchronize()
+        assert int(dstatus.item()) == 0
         assert torch.equal(outh, rec.cpu())
         e2e = {"value": world * bytes_in / (np.mean(t_e) * 1e-3) / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": bytes_in + nb_box[0], "d2h_bytes_per_step": nb_box[0] + bytes_in}

@@ -6,6 +6,7 @@ decompression runs in the library's CUDA kernels.
 from __future__ import annotations
 
 import ctypes as C
+from functools import lru_cache
 
 import torch
 
@@ -27,12 +28,48 @@ def _stream_ptr(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+# per-shape values and marshalled argument blocks are kept, so a call on a shape seen
+# before spends no time on them (the C side only reads them)
+@lru_cache(maxsize=1024)
+def _dims_c(dims: tuple):
+    return L.dims_array(dims)
+
+
+@lru_cache(maxsize=1024)
+def _max_archive_bytes(dims: tuple) -> int:
+    return int(L.lib().csz_max_archive_bytes(len(dims), _dims_c(dims)))
+
+
+@lru_cache(maxsize=1024)
+def _workspace_bytes(dims: tuple) -> int:
+    return int(L.lib().csz_workspace_bytes(len(dims), _dims_c(dims)))
+
+
 def max_archive_bytes(dims) -> int:
-    return int(L.lib().csz_max_archive_bytes(len(dims), L.dims_array(dims)))
+    return _max_archive_bytes(tuple(int(d) for d in dims))
 
 
 def workspace_bytes(dims) -> int:
-    return int(L.lib().csz_workspace_bytes(len(dims), L.dims_array(dims)))
+    return _workspace_bytes(tuple(int(d) for d in dims))
+
+
+_opt_cache = {}
+
+
+def _options(radius, select, weights):
+    if weights is not None:
+        if not (weights.is_cuda and weights.dtype == torch.float32 and weights.numel() == MLP_PARAMS):
+            raise ValueError("weights must be a float32 CUDA tensor of 1443 parameters")
+    key = (int(radius), SELECT[select] if isinstance(select, str) else int(select),
+           weights.data_ptr() if weights is not None else 0)
+    opt = _opt_cache.get(key)
+    if opt is None:
+        opt = L.csz_options()
+        opt.radius, opt.select = key[0], key[1]
+        if weights is not None:
+            opt.selector_weights = C.c_void_p(key[2])
+        _opt_cache[key] = opt
+    return opt
 
 
 class Workspace:
@@ -71,15 +108,9 @@ def compress(field: torch.Tensor, eb: float, eb_mode: str = "rel", radius: int =
     if out is None:
         out = torch.empty(max_archive_bytes(dims) or 1, dtype=torch.uint8, device=field.device)
     ws = _ws(field.device, workspace).get(workspace_bytes(dims) or 256)
-    opt = L.csz_options()
-    opt.radius = int(radius)
-    opt.select = SELECT[select] if isinstance(select, str) else int(select)
-    if weights is not None:
-        if not (weights.is_cuda and weights.dtype == torch.float32 and weights.numel() == MLP_PARAMS):
-            raise ValueError("weights must be a float32 CUDA tensor of 1443 parameters")
-        opt.selector_weights = C.c_void_p(weights.data_ptr())
+    opt = _options(radius, select, weights)
     nbytes = C.c_size_t(0)
-    st = L.lib().csz_compress(C.c_void_p(field.data_ptr()), len(dims), L.dims_array(dims),
+    st = L.lib().csz_compress(C.c_void_p(field.data_ptr()), len(dims), _dims_c(dims),
                               EB_MODES[eb_mode] if isinstance(eb_mode, str) else int(eb_mode), float(eb),
                               C.byref(opt), C.c_void_p(ws.data_ptr()), ws.numel(), C.c_void_p(out.data_ptr()),
                               out.numel(), C.byref(nbytes), _stream_ptr(stream))
@@ -135,17 +166,11 @@ def compress_with_header(field: torch.Tensor, eb: float, eb_mode: str = "rel", r
     if out is None:
         out = torch.empty(max_archive_bytes(dims) or 1, dtype=torch.uint8, device=field.device)
     ws = _ws(field.device, workspace).get(workspace_bytes(dims) or 256)
-    opt = L.csz_options()
-    opt.radius = int(radius)
-    opt.select = SELECT[select] if isinstance(select, str) else int(select)
-    if weights is not None:
-        if not (weights.is_cuda and weights.dtype == torch.float32 and weights.numel() == MLP_PARAMS):
-            raise ValueError("weights must be a float32 CUDA tensor of 1443 parameters")
-        opt.selector_weights = C.c_void_p(weights.data_ptr())
+    opt = _options(radius, select, weights)
     nbytes = C.c_size_t(0)
     hdr = (C.c_uint8 * 128)()
     st = L.lib().csz_compress_with_header(
-        C.c_void_p(field.data_ptr()), len(dims), L.dims_array(dims),
+        C.c_void_p(field.data_ptr()), len(dims), _dims_c(dims),
         EB_MODES[eb_mode] if isinstance(eb_mode, str) else int(eb_mode), float(eb), C.byref(opt),
         C.c_void_p(ws.data_ptr()), ws.numel(), C.c_void_p(out.data_ptr()), out.numel(), C.byref(nbytes), hdr,
         _stream_ptr(stream))
