@@ -113,7 +113,7 @@ void trace_count_batch() {
   for (int k : {K_RANGE, K_CONSTRUCT, K_CODEBOOK, K_ENCODE}) g_trace.launches[k]++;
 }
 void trace_count_decode_batch() {
-  for (int k : {K_DEC_SETUP, K_STREAM_DECODE, K_RLE_EXPAND, K_RECONSTRUCT}) g_trace.launches[k]++;
+  for (int k : {K_DEC_HEADER, K_DEC_SETUP, K_STREAM_DECODE, K_RLE_EXPAND, K_RECONSTRUCT}) g_trace.launches[k]++;
 }
 }  // namespace cszp
 
@@ -121,7 +121,8 @@ extern "C" {
 
 static const char* const kKernelNames[K_COUNT] = {
     "range", "abs_params", "construct", "codebook", "encode", "dec_setup",
-    "stream_decode", "rle_expand", "reconstruct", "mlp_predict", "mlp_grad", "mlp_update", "dec_status"};
+    "stream_decode", "rle_expand", "reconstruct", "mlp_predict", "mlp_grad", "mlp_update", "dec_status",
+    "dec_header"};
 
 int csz_kernel_count(void) { return K_COUNT; }
 

@@ -426,7 +426,6 @@ __device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
   if (a.dead) return;
   const int codec = a.ar[a.off_codec + b];
   if (codec != CODEC_RLE && codec != CODEC_RLE_HUFF) return;
-  if (a.st->status & ERR_CORRUPT) return;
   uint32_t org[3], w[3];
   block_box(a.g, b, org, w);
   const uint32_t m = w[0] * w[1] * w[2];
@@ -448,8 +447,11 @@ __device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
     if (tid == 0) flag(a.st, ERR_CORRUPT);
     return;
   }
-  if (tid == 0) s_bad = 0;
+  // the status is read once, by thread 0, and acted on after the barrier, so that a
+  // corruption flagged by another CTA meanwhile cannot split this CTA's threads
+  if (tid == 0) s_bad = (a.st->status & ERR_CORRUPT) ? 2u : 0u;
   __syncthreads();
+  if (s_bad == 2u) return;
   for (uint32_t i = tid; i < nr; i += blockDim.x) {
     s_v[i] = v[i];
     s_l[i] = l[i];
@@ -522,9 +524,10 @@ __device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
 }
 
 // One CTA per listed run block (the list the set-up wrote; it holds exactly the
-// header's count unless the archive is corrupt, which the set-up has flagged).
+// header's count unless the archive is corrupt, which the set-up has flagged and
+// the body checks).
 __global__ __launch_bounds__(kRleThreads) void rle_expand_kernel(DecodeArgs a) {
-  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
+  if (a.dead) return;
   const uint32_t b = a.runblk[blockIdx.x];
   if (b >= a.g.nblk) return;
   rle_expand_body(a, b);
@@ -869,7 +872,9 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_batch_kernel(const De
 
 cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
   cudaError_t e;
+  trace_begin(K_DEC_HEADER, s);
   dec_header_batch_kernel<<<(L.nfields + 127) / 128, 128, 0, s>>>(L.tasks, L.nfields);
+  trace_end(K_DEC_HEADER, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   trace_begin(K_DEC_SETUP, s);
   dec_setup_batch_kernel<<<L.nsetup, 1024, 0, s>>>(L.tasks, L.setup0, L.nfields);

@@ -162,6 +162,7 @@ enum KernelId : int {
   K_MLP_GRAD,
   K_MLP_UPDATE,
   K_DEC_STATUS,
+  K_DEC_HEADER,
   K_COUNT
 };
 void trace_begin(int id, cudaStream_t s);
