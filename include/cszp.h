@@ -291,8 +291,11 @@ const char* csz_status_string(int status);
  * csz_kernel_count() kernels are numbered 0..count-1 and named by csz_kernel_name().
  * Launch counts are always kept.  While tracing is enabled every launch is bracketed
  * by CUDA events on the caller's stream and the elapsed milliseconds are added to the
- * kernel's total at the call's synchronisation.  csz_trace_read fills ms[count] and
- * launches[count] (either may be NULL) and optionally resets both.
+ * kernel's total at the call's synchronisation.  While tracing is enabled,
+ * csz_batch_compress and csz_batch_decompress launch their kernels one by one instead
+ * of replaying the graph, so that each gets its events, and synchronise `stream`
+ * before returning.  csz_trace_read fills ms[count] and launches[count] (either may
+ * be NULL) and optionally resets both.
  */
 int csz_kernel_count(void);
 const char* csz_kernel_name(int id);

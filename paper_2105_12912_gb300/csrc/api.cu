@@ -109,6 +109,8 @@ bool trace_suspend() {
   return on;
 }
 void trace_resume(bool on) { g_trace.on = on; }
+bool trace_on() { return g_trace.on; }
+void trace_fold() { trace_collect(); }
 void trace_count_batch() {
   for (int k : {K_RANGE, K_CONSTRUCT, K_CODEBOOK, K_ENCODE}) g_trace.launches[k]++;
 }

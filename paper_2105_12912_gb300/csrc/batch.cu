@@ -409,6 +409,14 @@ csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_opti
 csz_status csz_batch_compress(csz_batch* b, void* stream) {
   if (!b || !b->exec) return CSZ_E_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (trace_on()) {
+    // with tracing on, the graph's launches run one by one so that each gets its
+    // events, and the call waits for them (tracing is a diagnostic mode)
+    if (enqueue(b, b->construct_grid, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      return CSZ_E_CUDA;
+    trace_fold();
+    return CSZ_OK;
+  }
   if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return CSZ_E_CUDA;
   trace_count_batch();
   return CSZ_OK;
@@ -643,6 +651,12 @@ csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_w
 
 csz_status csz_batch_decompress(csz_batch_dec* b, void* stream) {
   if (!b || !b->exec) return CSZ_E_ARG;
+  if (trace_on()) {  // as for compression: launches one by one, each with its events
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dec_enqueue(b, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+    trace_fold();
+    return CSZ_OK;
+  }
   if (cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return CSZ_E_CUDA;
   trace_count_decode_batch();
   return CSZ_OK;

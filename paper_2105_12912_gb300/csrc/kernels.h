@@ -168,6 +168,8 @@ enum KernelId : int {
 void trace_begin(int id, cudaStream_t s);
 void trace_end(int id, cudaStream_t s);
 bool trace_suspend();           // stop event tracing (stream capture); returns the old state
+bool trace_on();                // event tracing is enabled
+void trace_fold();              // fold the recorded events into the totals (after a synchronisation)
 void trace_resume(bool on);
 void trace_count_batch();       // one replay of a compression batch graph: count its launches
 void trace_count_decode_batch();  // the same for a decompression batch graph

@@ -180,3 +180,35 @@ def test_batch_decompress_bad_header_isolated(gpu):
         assert st[i] == 0
         y, _ = gpu.decompress(bc.archives[i], sizes[i])
         assert torch.equal(bd.outs[i].view(torch.int32), y.view(torch.int32))
+
+
+def test_batch_traced_launches_match_graph(gpu):
+    """With tracing on, batch calls launch their kernels one by one (each with CUDA
+    events); archives and reconstructions must equal the graph replays'."""
+    fields = _mixed_fields(9)[:8]
+    xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
+    bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields], autotune=False)
+    bd = gpu.BatchDecompressor(bc.archives, [tuple(x.shape) for x in xs])
+    bc.run()
+    bd.run()
+    sizes, stats = bc.results()
+    assert stats == [0] * len(xs) and bd.results() == [0] * len(xs)
+    ref_ar = [a[:n].clone() for a, n in zip(bc.archives, sizes)]
+    ref_out = [o.clone() for o in bd.outs]
+    gpu.trace_enable(True)
+    try:
+        gpu.trace_read(reset=True)
+        bc.run()
+        bd.run()
+        torch.cuda.synchronize()
+        tr = gpu.trace_read(reset=True)
+    finally:
+        gpu.trace_enable(False)
+    sizes2, stats2 = bc.results()
+    assert sizes2 == sizes and stats2 == stats and bd.results() == [0] * len(xs)
+    for i in range(len(xs)):
+        assert torch.equal(bc.archives[i][:sizes[i]], ref_ar[i])
+        assert torch.equal(bd.outs[i].view(torch.int32), ref_out[i].view(torch.int32))
+    for k in ("range", "construct", "codebook", "encode", "dec_header", "dec_setup", "stream_decode", "reconstruct"):
+        ms, cnt = tr[k]
+        assert cnt == 1 and ms > 0, (k, tr[k])
