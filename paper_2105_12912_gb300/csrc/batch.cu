@@ -33,6 +33,7 @@ struct csz_batch {
   EncodeArgs* etasks = nullptr;
   uint32_t ntiles = 0, nrange = 0;
   int construct_grid = 0;  // 0 = default (all resident CTAs)
+  int common_nd = 0;       // the fields' dimensionality when they all share it, else 0
   int tuned_grid = 0;
   double tuned_ms[4] = {0, 0, 0, 0};
   cudaGraphExec_t exec = nullptr;
@@ -156,7 +157,7 @@ cudaError_t enqueue(const csz_batch* b, int construct_grid, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   if ((e = launch_range_batch(b->rtasks, b->cta0, b->nfields, b->nrange, s)) != cudaSuccess) return e;
   if ((e = launch_construct_batch(b->ctasks, b->tile0, b->nfields, b->ntiles, &b->tickets[0], kSpinLimit,
-                                  construct_grid, s)) != cudaSuccess)
+                                  construct_grid, b->common_nd, s)) != cudaSuccess)
     return e;
   if ((e = launch_codebook_batch(b->btasks, b->nfields, s)) != cudaSuccess) return e;
   return launch_encode_batch(b->etasks, b->tile0, b->nfields, b->ntiles, &b->tickets[1], s);
@@ -317,6 +318,9 @@ csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_opti
   tile0[nfields] = tiles;
   cta0[nfields] = ctas;
   b->ntiles = tiles;
+  b->common_nd = fields[0].ndim;
+  for (int f = 1; f < nfields; f++)
+    if (fields[f].ndim != b->common_nd) b->common_nd = 0;
   b->nrange = ctas;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = upload(b->ctasks, ct, s);

@@ -695,14 +695,16 @@ cudaError_t launch_construct(const ConstructTask& one, uint32_t* ticket, cudaStr
 }
 
 cudaError_t launch_construct_batch(const ConstructTask* d_tasks, const uint32_t* d_tile0, int nfields,
-                                   uint32_t ntiles, uint32_t* ticket, uint32_t spin_limit, int grid,
+                                   uint32_t ntiles, uint32_t* ticket, uint32_t spin_limit, int grid, int nd,
                                    cudaStream_t s) {
   ConstructTask dummy;
   memset(&dummy, 0, sizeof(dummy));
   if (grid <= 0) grid = construct_grid(ntiles);
+  // the specialised kernel when every field has the same dimensionality
+  auto k = nd == 1 ? construct_kernel<1>
+                   : (nd == 2 ? construct_kernel<2> : (nd == 3 ? construct_kernel<3> : construct_kernel<0>));
   trace_begin(K_CONSTRUCT, s);
-  construct_kernel<0><<<grid, kThreads, sizeof(Smem), s>>>(dummy, d_tasks, d_tile0, nfields, ntiles, ticket,
-                                                           spin_limit);
+  k<<<grid, kThreads, sizeof(Smem), s>>>(dummy, d_tasks, d_tile0, nfields, ntiles, ticket, spin_limit);
   trace_end(K_CONSTRUCT, s);
   return cudaGetLastError();
 }

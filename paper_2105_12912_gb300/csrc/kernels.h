@@ -182,8 +182,8 @@ size_t construct_smem_bytes();
 int construct_grid(uint32_t ntiles);  // persistent grid: all resident CTAs, at most ntiles
 cudaError_t launch_construct(const ConstructTask& one, uint32_t* ticket, cudaStream_t s);
 cudaError_t launch_construct_batch(const ConstructTask* d_tasks, const uint32_t* d_tile0, int nfields,
-                                   uint32_t ntiles, uint32_t* ticket, uint32_t spin_limit, int grid,
-                                   cudaStream_t s);
+                                   uint32_t ntiles, uint32_t* ticket, uint32_t spin_limit, int grid, int nd,
+                                   cudaStream_t s);  // nd: the fields' common dimensionality, 0 if mixed
 cudaError_t launch_codebook(const BookArgs& a, cudaStream_t s);
 cudaError_t launch_encode(const EncodeArgs& a, cudaStream_t s);
 // batches: per-field tables in device memory

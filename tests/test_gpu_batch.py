@@ -212,3 +212,25 @@ def test_batch_traced_launches_match_graph(gpu):
     for k in ("range", "construct", "codebook", "encode", "dec_header", "dec_setup", "stream_decode", "reconstruct"):
         ms, cnt = tr[k]
         assert cnt == 1 and ms > 0, (k, tr[k])
+
+
+@pytest.mark.parametrize("nd", [1, 2, 3])
+def test_batch_of_one_dimensionality(gpu, nd):
+    """A batch whose fields share their dimensionality runs the specialised
+    construction kernel; archives must still equal the single-field calls'."""
+    shapes = {1: [(5000,), (70001,), (4096,)], 2: [(70, 131), (64, 64), (300, 301)],
+              3: [(19, 23, 37), (16, 16, 16), (40, 64, 64)]}[nd]
+    rng = np.random.default_rng(10 + nd)
+    xs = []
+    for sh in shapes:
+        x = rng.standard_normal(sh).astype(np.float32)
+        for ax in range(len(sh)):
+            x = np.cumsum(x, axis=ax).astype(np.float32)
+        xs.append(torch.from_numpy(x).cuda())
+    bc = gpu.BatchCompressor(xs, 1e-3, "rel", autotune=False)
+    bc.run()
+    sizes, stats = bc.results()
+    for i, x in enumerate(xs):
+        st, ref = _single(gpu, x, 1e-3, "rel")
+        assert stats[i] == 0 and st == 0
+        assert np.array_equal(bc.archives[i][:sizes[i]].cpu().numpy(), ref), i
