@@ -321,9 +321,17 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
   uint32_t* lut_code = s_luts;
   uint32_t* lut_val = s_luts + (huff ? (1 << kLutBits) : 0);
   uint32_t* lut_len = lut_val + (1 << kLutBits);
+  // a chunk of blocks (batches) copies only the tables its own blocks use
+  bool need_code = huff, need_runs = rle;
+  if (b_end != 0) {
+    const uint32_t b = b_begin + threadIdx.x;
+    const int c = (b < b_end) ? a.ar[a.off_codec + b] : -1;
+    need_code = __syncthreads_or(huff && c == CODEC_HUFF) != 0;
+    need_runs = __syncthreads_or(rle && c == CODEC_RLE_HUFF) != 0;
+  }
   for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) {
-    if (huff) lut_code[i] = a.tabs[0].lut[i];
-    if (rle) {
+    if (need_code) lut_code[i] = a.tabs[0].lut[i];
+    if (need_runs) {
       lut_val[i] = a.tabs[1].lut[i];
       lut_len[i] = a.tabs[2].lut[i];
     }
