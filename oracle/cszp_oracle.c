@@ -194,7 +194,7 @@ static int exceeds(float x, float y, float eb) {
 }
 
 /*
- * Prequantization (Sec. IV-A1, Alg. 1 l.2): d° = round(d / 2eb), so that
+ * Prequantization (Sec. IV-A1, Alg. 1 prequantization step): d° = round(d / 2eb), so that
  * |d - d°*2eb| < eb in exact arithmetic.  In FP32 the product d*(1/2eb) and the
  * reconstruction fl32(d°*2eb) both round, so:
  *   k0 = nearest integer to fl32(x * ebx2_r), ties to even;
@@ -262,10 +262,11 @@ static int cmp_u64(const void* a, const void* b) {
 }
 
 /*
- * Dual-quantization construction (Sec. IV-A1, Alg. 1 l.1-8, modified scheme of
- * Sec. IV-B1):  k = prequant(x);  delta = k - p(k)  (Alg. 1 l.3 prints p - d; the
- * text, "delta = d° - p°", and the reconstruction d = p + q' fix the sign as d - p);
- * in range iff |delta| < radius (Alg. 1 l.4 omits the absolute value): q = delta +
+ * Dual-quantization construction (Sec. IV-A1, Alg. 1 compression part, modified
+ * scheme of Sec. IV-B1):  k = prequant(x);  delta = k - p(k)  (Alg. 1's residual step
+ * prints p - d; the text, "delta = d° - p°", and the reconstruction d = p + q' fix
+ * the sign as d - p); in range iff |delta| < radius (Alg. 1's range test omits the
+ * absolute value): q = delta +
  * radius; otherwise q = 0 and delta itself is the outlier (the cuSZ+ change).
  * Codes go to the block-major code stream; records are sorted by key.
  */
@@ -1403,7 +1404,7 @@ int orc_decode_codes(const uint8_t* ar, size_t bytes, uint16_t* codes, uint64_t 
 }
 
 /*
- * Decompression (Alg. 1 l.9-13 read through the recurrence it replaces):
+ * Decompression (Alg. 1 decompression part, read through the recurrence it replaces):
  * fuse q' = q - r, or delta at an outlier slot (Sec. IV-B1), then rebuild each
  * prequantized integer sequentially, k = p(k) + q', in raster order (every
  * predictor neighbour precedes its element), scale by 2eb, and put back the

@@ -3,11 +3,13 @@
 // Pipeline (one stream, no host round trip until the end):
 //   range_kernel / abs_params_kernel  value range (REL) and the FP32 error bound
 //   construct_kernel (construct.cu)   prequant + chunk-local Lorenzo + postquant,
-//                                     records, histograms
-//   codebook_kernel                   three canonical Huffman books
-//   encode_kernel                     per block: exact sizes or heuristic / MLP pick,
-//                                     payload placement by decoupled look-back, payload
-//   (the last encode block)           header, padding, books
+//                                     record counts, bit words, residuals, histograms
+//   codebook_kernel                   three canonical Huffman books; a fourth CTA
+//                                     scans the blocks' record counts
+//   encode_kernel                     per block: its records, exact sizes or heuristic /
+//                                     MLP pick, payload placement by decoupled
+//                                     look-back, payload
+//   (the block counted last)          header, padding, books
 #include "common.cuh"
 #include "kernels.h"
 

@@ -13,8 +13,9 @@
 //
 // Histograms are accumulated per CTA in shared memory (32-bit counters) over all its
 // tiles of one field and added to the field's global histograms when the CTA moves
-// to another field or finishes.  Records are placed in slot order with a decoupled
-// look-back over the field's tiles.
+// to another field or finishes.  Records are not placed here: each tile leaves its
+// outlier / patch counts, bit words and outlier residuals; the codebook launch scans
+// the counts and the encode CTAs write the records in slot order.
 #include <cuda.h>
 
 #include "common.cuh"

@@ -5,10 +5,13 @@
 //                          validation and each block's first record
 //   stream_decode_kernel   one warp per interleaved 32-lane stream (Huffman code
 //                          streams, RLE+Huffman value and length streams)
-//   rle_expand_kernel      one CTA per RLE / RLE+Huffman block: runs to codes
+//   rle_expand_kernel      one CTA per listed RLE / RLE+Huffman block: runs to codes
 //   reconstruct_kernel<ND> fuse outliers (q' = q - r, or delta), N-D partial sums
-//                          per chunk (Alg. 1 l.9-13, Sec. IV-B2), scale by 2eb,
-//                          verbatim patches
+//                          per chunk (Alg. 1, Sec. IV-B2), scale by 2eb, verbatim
+//                          patches
+//   dec_status_kernel      the status word of an asynchronous decompression
+// and their batch forms (per-field tables in device memory, headers read and checked
+// on the device by dec_header_batch_kernel).
 #include "common.cuh"
 #include "host.h"
 #include "kernels.h"
