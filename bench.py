@@ -317,6 +317,18 @@ def kernel_source_rev():
     return h.hexdigest()[:16]
 
 
+def whole_job(step_ms, world, bytes_per_rank_step, dist=None, device=None):
+    """Whole-job throughput of `world` replicas: each rank's timed steps (ms) are
+    summed, the slowest rank's total bounds the job (max over ranks), and the value
+    counts the bytes all ranks processed.  Returns (GB/s, total ms of the slowest)."""
+    total_ms = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * len(step_ms) * bytes_per_rank_step / (total_ms * 1e-3) / 1e9, total_ms
+
+
 def run_ours(args):
     from paper_2105_12912_gb300 import api, synth
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -408,12 +420,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ms_step = float(np.mean(t_round))
-    total_ms = float(np.sum(t_round))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * bytes_in / (total_ms * 1e-3) / 1e9
+    value, total_ms = whole_job(t_round, world, bytes_in, dist, dev)
 
     # compress-only and decompress-only throughput, on the timed step's path, and on
     # the plain calls
