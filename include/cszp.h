@@ -283,6 +283,18 @@ csz_status csz_selector_train(float* d_weights, const float* d_feat, const float
                               void* d_workspace, size_t workspace_bytes, double* h_loss,
                               void* stream);
 
+/*
+ * Failure-path self-test (a test aid).  Runs one bounded wait that nothing
+ * satisfies, with the same code the pipeline uses: which = 0, the decoupled
+ * look-back of a tile whose predecessor never publishes; which = 1, an mbarrier
+ * phase that no copy or arrival completes.  The wait gives up after spin_limit
+ * tries, the kernel sets the timeout bit and returns, and the call reports
+ * CSZ_E_TIMEOUT.  The context stays usable.  d_scratch: device memory, at least
+ * 512 bytes, overwritten.  Synchronises `stream`.
+ */
+csz_status csz_wait_selftest(int which, uint32_t spin_limit, void* d_scratch, size_t scratch_bytes,
+                             void* stream);
+
 /* Human-readable name of a status. */
 const char* csz_status_string(int status);
 

@@ -52,6 +52,7 @@ SIGNATURES = {
                                            C.POINTER(C.c_size_t), C.c_void_p, C.c_void_p]),
     "csz_decompress_async": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
                                        C.c_size_t, C.c_void_p, C.c_void_p]),
+    "csz_wait_selftest": (C.c_int, [C.c_int, C.c_uint32, C.c_void_p, C.c_size_t, C.c_void_p]),
     "csz_decompress_static": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint64, C.c_void_p]),
     "csz_selector_rows": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint64), C.c_int, C.c_double, C.c_uint32,
                                     C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,

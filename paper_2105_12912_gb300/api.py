@@ -197,6 +197,14 @@ def decompress_async(archive: torch.Tensor, nbytes: int, header_bytes: bytes, ou
     _check(st, "csz_decompress_async")
 
 
+def wait_selftest(which: int, spin_limit: int = 1000, stream=None) -> int:
+    """Run one bounded wait that nothing satisfies (0: look-back, 1: mbarrier) and
+    return the resulting status (CSZ_E_TIMEOUT = 7 when the wait gave up)."""
+    scratch = torch.empty(512, dtype=torch.uint8, device="cuda")
+    return int(L.lib().csz_wait_selftest(int(which), int(spin_limit), C.c_void_p(scratch.data_ptr()),
+                                         scratch.numel(), _stream_ptr(stream)))
+
+
 def header(archive) -> dict:
     """Parsed 128-byte archive header (from a CUDA/CPU uint8 tensor or bytes)."""
     import struct

@@ -908,6 +908,26 @@ cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One bounded wait that nothing satisfies (a test aid for the failure path): which 0,
+// the payload look-back of tile 1 behind a tile 0 that never publishes; which 1, an
+// mbarrier phase no copy or arrival completes.  Either gives up after `spin_limit`
+// tries and leaves ERR_TIMEOUT in the status, and the kernel returns normally.
+__global__ void wait_selftest_kernel(int which, uint32_t spin_limit, uint64_t* lb, DevState* st) {
+  __shared__ unsigned long long s_bar;
+  if (which == 0) {
+    if (threadIdx.x < 32) lookback_warp(lb, 1, 5, &st->status, spin_limit);
+  } else if (threadIdx.x == 0) {
+    mbar_init(&s_bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&s_bar, 0, spin_limit)) atomicOr(&st->status, ERR_TIMEOUT);
+  }
+}
+
+cudaError_t launch_wait_selftest(int which, uint32_t spin_limit, uint64_t* lb, DevState* st, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(which, spin_limit, lb, st);
+  return cudaGetLastError();
+}
+
 __global__ void dec_status_kernel(const DevState* st, uint32_t* d_status) {
   *d_status = (uint32_t)fold(st->status);
 }

@@ -197,6 +197,8 @@ cudaError_t launch_encode_batch(const EncodeArgs* d_tasks, const uint32_t* d_til
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);
 // the decompression's csz_status into a device word (asynchronous decompression)
 cudaError_t launch_dec_status(const DevState* st, uint32_t* d_status, cudaStream_t s);
+// one bounded wait nothing satisfies (0: look-back, 1: mbarrier): ERR_TIMEOUT in st
+cudaError_t launch_wait_selftest(int which, uint32_t spin_limit, uint64_t* lb, DevState* st, cudaStream_t s);
 
 // Batched decompression: a device table of per-field decode arguments (headers are
 // read and checked on the device) and CTA prefixes per stage.
