@@ -319,7 +319,11 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
   extern __shared__ __align__(16) uint32_t s_luts[];  // the present books' tables
   __shared__ unsigned long long s_first[kMaxLen + 1], s_limit[kMaxLen + 1];
   __shared__ uint32_t s_off[kMaxLen + 1], s_count[kMaxLen + 1];
-  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
+  __shared__ int s_go;
+  if (a.dead) return;
+  // the status is read once, by thread 0, and acted on after the staging barrier, so
+  // that a corruption flagged by another CTA meanwhile cannot split this CTA
+  if (threadIdx.x == 0) s_go = !(a.st->status & ERR_CORRUPT);
   const bool huff = (a.flags & 1u) != 0, rle = (a.flags & 2u) != 0;
   uint32_t* lut_code = s_luts;
   uint32_t* lut_val = s_luts + (huff ? (1 << kLutBits) : 0);
@@ -346,6 +350,7 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
     s_count[i] = a.tabs[0].count[i];
   }
   __syncthreads();
+  if (!s_go) return;
   const bool lane0 = (threadIdx.x & 31) == 0;
   const bool ticketed = b_end == 0;
   // work items are (block, stream) slots: a Huffman block's streams A and B, an
