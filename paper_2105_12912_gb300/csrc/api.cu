@@ -115,7 +115,7 @@ void trace_count_batch() {
   for (int k : {K_RANGE, K_CONSTRUCT, K_CODEBOOK, K_ENCODE}) g_trace.launches[k]++;
 }
 void trace_count_decode_batch() {
-  for (int k : {K_DEC_HEADER, K_DEC_SETUP, K_STREAM_DECODE, K_RLE_EXPAND, K_RECONSTRUCT}) g_trace.launches[k]++;
+  for (int k : {K_DEC_HEADER, K_DEC_SETUP, K_STREAM_DECODE, K_RECONSTRUCT}) g_trace.launches[k]++;
 }
 }  // namespace cszp
 

@@ -432,16 +432,18 @@ constexpr int kRleThreads = 256;
 
 // RLE and RLE+Huffman blocks: run starts by a block scan, then every code position
 // finds its run by binary search.
-__device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
-  __shared__ uint16_t s_v[kSlots];
-  __shared__ uint16_t s_l[kSlots];
-  __shared__ uint32_t s_start[kSlots + 1];
+// Runs of run block b to its 4096 codes at `out` (global or shared memory, 16-byte
+// aligned), with shared scratch s_v, s_l (kSlots each) and s_start (kSlots + 1).
+// Returns false (the same in every thread) when the block is not expanded: not a run
+// block, corrupt (flagged), or its field already flagged corrupt.
+__device__ bool rle_expand_into(const DecodeArgs& a, uint32_t b, uint16_t* out, uint16_t* s_v, uint16_t* s_l,
+                                uint32_t* s_start) {
   __shared__ uint32_t s_scan[33];
   __shared__ uint32_t s_bad;
   const int tid = threadIdx.x;
-  if (a.dead) return;
+  if (a.dead) return false;
   const int codec = a.ar[a.off_codec + b];
-  if (codec != CODEC_RLE && codec != CODEC_RLE_HUFF) return;
+  if (codec != CODEC_RLE && codec != CODEC_RLE_HUFF) return false;
   uint32_t org[3], w[3];
   block_box(a.g, b, org, w);
   const uint32_t m = w[0] * w[1] * w[2];
@@ -461,13 +463,13 @@ __device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
   }
   if (nr > m) {
     if (tid == 0) flag(a.st, ERR_CORRUPT);
-    return;
+    return false;
   }
   // the status is read once, by thread 0, and acted on after the barrier, so that a
   // corruption flagged by another CTA meanwhile cannot split this CTA's threads
   if (tid == 0) s_bad = (a.st->status & ERR_CORRUPT) ? 2u : 0u;
   __syncthreads();
-  if (s_bad == 2u) return;
+  if (s_bad == 2u) return false;
   for (uint32_t i = tid; i < nr; i += blockDim.x) {
     s_v[i] = v[i];
     s_l[i] = l[i];
@@ -490,7 +492,7 @@ __device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
   __syncthreads();
   if (s_bad || tot != m) {
     if (tid == 0) flag(a.st, ERR_CORRUPT);
-    return;
+    return false;
   }
   // run index of every position: mark run starts, then a running maximum
   uint32_t* s_idx = s_start;  // starts are no longer needed once marked below
@@ -524,7 +526,6 @@ __device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
   uint32_t excl = __shfl_up_sync(~0u, incl, 1);
   if ((tid & 31) == 0) excl = 0;
   uint32_t cur = max(carry, excl);
-  uint16_t* out = a.codes + (uint64_t)b * kSlots;
   uint32_t vals[8];
 #pragma unroll
   for (int i = 0; i < 16; i++) {
@@ -537,6 +538,15 @@ __device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
   uint4* o4 = reinterpret_cast<uint4*>(out + p0);
   o4[0] = make_uint4(vals[0], vals[1], vals[2], vals[3]);
   o4[1] = make_uint4(vals[4], vals[5], vals[6], vals[7]);
+  return true;
+}
+
+// Run block b expanded in place in the code stream (global), with its own scratch.
+__device__ void rle_expand_body(const DecodeArgs& a, uint32_t b) {
+  __shared__ __align__(16) uint16_t s_v[kSlots];
+  __shared__ __align__(16) uint16_t s_l[kSlots];
+  __shared__ __align__(16) uint32_t s_start[kSlots + 1];
+  rle_expand_into(a, b, a.codes + (uint64_t)b * kSlots, s_v, s_l, s_start);
 }
 
 // One CTA per listed run block (the list the set-up wrote; it holds exactly the
@@ -559,8 +569,8 @@ __device__ __forceinline__ float scale(int32_t k, float ebx2) { return __fmul_rn
 // codes: the block's 4096 code slots (global memory, or a shared-memory copy)
 template <int ND>
 __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, const uint16_t* codes) {
+  // (the caller has checked the field's status, the same way in every thread)
   const int tid = threadIdx.x;
-  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
   uint32_t org[3], w[3];
   block_box(a.g, b, org, w);
   const uint32_t m = w[0] * w[1] * w[2];
@@ -868,19 +878,34 @@ __global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_batch_kernel(
   stream_decode_body(a, b0, b1);
 }
 
-__global__ __launch_bounds__(kRleThreads) void rle_expand_batch_kernel(const DecodeArgs* __restrict__ tasks,
-                                                                       const uint32_t* __restrict__ tile0, int nfields) {
-  const int f = field_of(tile0, nfields, blockIdx.x);
-  rle_expand_body(tasks[f], blockIdx.x - tile0[f]);
-}
-
+// Reconstruction of a batch, one CTA per codec block of every field.  A run block's
+// runs are expanded here, into shared memory, instead of by a separate launch: the
+// expansion's scratch then serves as the reconstruction's (s_q overlays the run
+// values and lengths, read no more once the codes are out).
 __global__ __launch_bounds__(kRecThreads) void reconstruct_batch_kernel(const DecodeArgs* __restrict__ tasks,
                                                                         const uint32_t* __restrict__ tile0, int nfields) {
-  __shared__ __align__(16) int32_t s_q[kSlots];
+  static_assert(kRecThreads == kRleThreads, "run expansion assumes its CTA size");
+  __shared__ __align__(16) uint32_t s_scr[kSlots + (kSlots + 1) + 3];  // run values and lengths, then starts
+  __shared__ __align__(16) uint16_t s_codes[kSlots];
+  __shared__ int s_go;
+  int32_t* s_q = reinterpret_cast<int32_t*>(s_scr);
   const int f = field_of(tile0, nfields, blockIdx.x);
   const DecodeArgs& a = tasks[f];
   const uint32_t b = blockIdx.x - tile0[f];
+  if (a.dead) return;
+  // the status is read once, by thread 0 (run expansions in other CTAs may flag
+  // corruption meanwhile), so every thread takes the same path
+  if (threadIdx.x == 0) s_go = !(a.st->status & ERR_CORRUPT);
+  __syncthreads();
+  if (!s_go) return;
+  const int codec = a.ar[a.off_codec + b];
   const uint16_t* codes = a.codes + (uint64_t)b * kSlots;
+  if (codec == CODEC_RLE || codec == CODEC_RLE_HUFF) {
+    uint16_t* sv = reinterpret_cast<uint16_t*>(s_scr);
+    if (!rle_expand_into(a, b, s_codes, sv, sv + kSlots, s_scr + kSlots)) return;
+    __syncthreads();
+    codes = s_codes;
+  }
   if (a.g.ndim == 1) reconstruct_body<1>(a, b, s_q, codes);
   else if (a.g.ndim == 2) reconstruct_body<2>(a, b, s_q, codes);
   else reconstruct_body<3>(a, b, s_q, codes);
@@ -903,10 +928,7 @@ cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
   stream_decode_batch_kernel<<<L.nchunks, 32 * kStreamWarps, lut_bytes, s>>>(L.tasks, L.chunk0, L.nfields);
   trace_end(K_STREAM_DECODE, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  trace_begin(K_RLE_EXPAND, s);
-  rle_expand_batch_kernel<<<L.ntiles, kRleThreads, 0, s>>>(L.tasks, L.tile0, L.nfields);
-  trace_end(K_RLE_EXPAND, s);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // (run blocks are expanded inside the reconstruction)
   trace_begin(K_RECONSTRUCT, s);
   reconstruct_batch_kernel<<<L.ntiles, kRecThreads, 0, s>>>(L.tasks, L.tile0, L.nfields);
   trace_end(K_RECONSTRUCT, s);
