@@ -73,3 +73,35 @@ def test_no_gpu_calls_fail_cleanly(L):
     nb = C.c_size_t()
     st = L.csz_compress(None, 1, d, 1, 1e-3, None, None, 0, None, 0, C.byref(nb), None)
     assert st == 1  # null pointers are rejected before any CUDA call
+
+
+def test_async_and_selftest_argument_checks_need_no_device(L, orc):
+    """The asynchronous decompression parses its host header copy before any launch:
+    missing pointers are CSZ_E_ARG, a copy that does not parse (or disagrees with the
+    byte count) is CSZ_E_CORRUPT, all without touching a device.  The wait self-test
+    rejects bad arguments the same way."""
+    import numpy as np
+    x = np.cumsum(np.random.default_rng(5).standard_normal(5000)).astype(np.float32)
+    st, ar = orc.compress(x, orc.EB_REL, 1e-3)
+    assert st == 0
+    hdr = (C.c_uint8 * 128).from_buffer_copy(bytes(ar[:128]))
+    fake = C.c_void_p(0x1000)  # never dereferenced: every case below fails on the host
+    status = C.c_void_p(0x2000)
+    # missing pointers
+    assert L.csz_decompress_async(None, ar.size, hdr, fake, 5000, fake, 1 << 20, status, None) == 1
+    assert L.csz_decompress_async(fake, ar.size, None, fake, 5000, fake, 1 << 20, status, None) == 1
+    assert L.csz_decompress_async(fake, ar.size, hdr, fake, 5000, fake, 1 << 20, None, None) == 1
+    # a header copy that does not parse, or does not fit the byte count
+    bad = bytearray(ar[:128])
+    bad[0] ^= 0xFF
+    badh = (C.c_uint8 * 128).from_buffer_copy(bytes(bad))
+    assert L.csz_decompress_async(fake, ar.size, badh, fake, 5000, fake, 1 << 20, status, None) == 4
+    assert L.csz_decompress_async(fake, ar.size - 1, hdr, fake, 5000, fake, 1 << 20, status, None) == 4
+    # output or workspace too small
+    assert L.csz_decompress_async(fake, ar.size, hdr, fake, 4999, fake, 1 << 20, status, None) == 5
+    assert L.csz_decompress_async(fake, ar.size, hdr, fake, 5000, fake, 16, status, None) == 5
+    # the self-test's argument checks
+    assert L.csz_wait_selftest(2, 100, fake, 512, None) == 1
+    assert L.csz_wait_selftest(0, 0, fake, 512, None) == 1
+    assert L.csz_wait_selftest(0, 100, fake, 64, None) == 1
+    assert L.csz_wait_selftest(0, 100, None, 512, None) == 1
