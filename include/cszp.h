@@ -42,7 +42,7 @@ typedef enum {
   CSZ_E_TIMEOUT = 7    /* a bounded device-side wait expired */
 } csz_status;
 
-/* Error-bound mode (Sec. VI-A): absolute, or relative to the field's value range
+/* Error-bound mode (Sec. II-B table captions, Sec. V-C): absolute, or relative to the field's value range
    (eb_abs = eb * (max - min), computed in double). */
 typedef enum { CSZ_EB_ABS = 0, CSZ_EB_REL = 1 } csz_eb_mode;
 
@@ -244,9 +244,11 @@ void csz_batch_destroy(csz_batch* batch);
  * compression pipeline with exhaustive sizing but writes no archive; for every codec
  * block b (block-major order, as in the archive) it writes
  *   d_feat[b][8]    features: zero-residual fraction, code entropy (bits), top-code
- *                   probability, |delta|<=1 fraction, runs per element, outlier
- *                   fraction, mean |delta|/r, fraction of codes differing from the
- *                   code 8 positions on (each a ratio of integers, one FP32 division)
+ *                   probability, log2(1 + max |delta|) over in-range codes, runs per
+ *                   element, outlier fraction, mean |delta|/r (outliers count 0), and
+ *                   the RLE roughness of Sec. III-B (binary-variance madogram pooled
+ *                   over the distances 1, 26, ..., 176); each a ratio of integers
+ *                   formed with one FP32 division
  *   d_target[b][3]  log2 of each codec's bits per element, in 1/65536 steps
  *   d_sizes[b][3]   each codec's exact payload bytes (0xffffffff: not applicable)
  *   d_valid[b]      1 where the learned selector decides the block

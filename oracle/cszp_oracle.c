@@ -137,7 +137,7 @@ int orc_geometry(int ndim, const uint64_t* dims, uint64_t* nblk, uint64_t* nelem
 /* error bound and prequantization                                                  */
 /* ------------------------------------------------------------------------------- */
 
-/* value range for the relative error bound (Sec. VI-A: eb relative to value range) */
+/* value range for the relative error bound (bounds relative to the value range: Sec. II-B table captions, Sec. V-C) */
 int orc_value_range(const float* x, uint64_t n, float* vmin, float* vmax) {
   float lo = INFINITY, hi = -INFINITY;
   for (uint64_t i = 0; i < n; i++) {
@@ -810,17 +810,31 @@ int orc_heuristic_pick(const uint32_t* h, int nsym, uint32_t m) {
 }
 
 /*
- * Selector features of one block (dense codes c[0..m), radius r):
- *  0 fraction of zero deltas (q == r)      4 runs per element
- *  1 entropy H of the block's codes (bits) 5 outlier fraction (q == 0)
- *  2 top-symbol probability p1             6 mean |delta| / r over in-range codes
- *  3 fraction with |delta| <= 1            7 binary variance at distance 8
- *    (in-range codes)                        (madogram, Sec. III-B2)
- * Each is a ratio of integers formed with one IEEE division in FP32.
+ * Selector features of one block (dense codes c[0..m), radius r).  q == 0 marks an
+ * outlier; every other code carries delta = q - r.  Each feature is a ratio of two
+ * integers, both exact in FP32, formed with one IEEE division:
+ *  0 zero-residual fraction        #(q == r) / m
+ *  1 code entropy H (bits)         (m log2 m - sum_s h_s log2 h_s) / m, Q16 logarithms
+ *  2 top-code probability p1       max_s h_s / m, outliers' code 0 included
+ *  3 log2(1 + max |delta|)         over in-range codes (0 if there are none), the Q16
+ *                                  logarithm divided by 65536
+ *  4 runs per element              #runs / m
+ *  5 outlier fraction              #(q == 0) / m
+ *  6 mean |delta| / r              sum of |q - r| over in-range codes / (m r): the
+ *                                  denominator counts all m codes, so an outlier adds 0
+ *                                  (its delta lives in a record, not in the code)
+ *  7 RLE roughness                 the madogram with binary variance (Sec. III-B,
+ *                                  "Modeling RLE Compressibility"): pairs (i, i + d)
+ *                                  whose codes differ, pooled over the distances
+ *                                  d = 1, 26, 51, ..., 176 (every 25th distance of the
+ *                                  paper's uniform d in [1, 200]), over the number of
+ *                                  such pairs inside the block (0 if none)
  */
+static const uint32_t MADO_D0 = 1, MADO_STEP = 25, MADO_N = 8;
+
 static void features_of(const uint16_t* c, uint64_t m, uint32_t radius, float* f) {
   uint32_t* h = (uint32_t*)calloc(NSYM_CODE, sizeof(uint32_t));
-  uint64_t zero = 0, near1 = 0, outl = 0, absd = 0, runs = 0, var8 = 0;
+  uint64_t zero = 0, outl = 0, absd = 0, maxd = 0, runs = 0, mism = 0, pairs = 0;
   for (uint64_t i = 0; i < m; i++) {
     h[c[i]]++;
     if (c[i] == 0) {
@@ -829,11 +843,17 @@ static void features_of(const uint16_t* c, uint64_t m, uint32_t radius, float* f
       int64_t d = (int64_t)c[i] - radius;
       if (d < 0) d = -d;
       if (d == 0) zero++;
-      if (d <= 1) near1++;
+      if ((uint64_t)d > maxd) maxd = (uint64_t)d;
       absd += (uint64_t)d;
     }
     if (i == 0 || c[i] != c[i - 1]) runs++;
-    if (i + 8 < m && c[i] != c[i + 8]) var8++;
+  }
+  for (uint32_t k = 0; k < MADO_N; k++) {
+    const uint64_t d = MADO_D0 + MADO_STEP * k;
+    for (uint64_t i = 0; i + d < m; i++) {
+      pairs++;
+      if (c[i] != c[i + d]) mism++;
+    }
   }
   int64_t Lm = orc_log2_q16(m), S = 0;
   uint32_t f1 = 0;
@@ -847,11 +867,11 @@ static void features_of(const uint16_t* c, uint64_t m, uint32_t radius, float* f
   f[0] = (float)zero / fm;
   f[1] = (float)NH / (float)(m * 65536);
   f[2] = (float)f1 / fm;
-  f[3] = (float)near1 / fm;
+  f[3] = (float)orc_log2_q16(1 + maxd) / 65536.0f;
   f[4] = (float)runs / fm;
   f[5] = (float)outl / fm;
   f[6] = (float)absd / (float)(m * radius);
-  f[7] = (float)var8 / fm;
+  f[7] = pairs ? (float)mism / (float)pairs : 0.0f;
   free(h);
 }
 

@@ -32,7 +32,7 @@ enum {
   ORC_E_CAPACITY = 5
 };
 
-/* error-bound modes: absolute, or relative to the value range (Sec. VI-A) */
+/* error-bound modes: absolute, or relative to the value range (Sec. II-B table captions, Sec. V-C) */
 enum { ORC_EB_ABS = 0, ORC_EB_REL = 1 };
 
 /* selection modes: three forced codecs and three adaptive pickers */

@@ -45,6 +45,9 @@ static_assert(kMlpParams == 1443, "MLP parameter count");
 // the runner-up within this many log2 units (about 2%) of the best prediction sends
 // the block to exact sizes
 constexpr float kMlpMargin = 0.028569152f;
+// RLE roughness feature (Sec. III-B madogram with binary variance): code changes at
+// the distances kMadoD0 + kMadoStep * k, k < kMadoN (every 25th distance of 1..200)
+constexpr uint32_t kMadoD0 = 1, kMadoStep = 25, kMadoN = 8;
 enum : int { SEL_HUFF = 0, SEL_RLE = 1, SEL_RLE_HUFF = 2, SEL_HEURISTIC = 3, SEL_EXHAUSTIVE = 4, SEL_LEARNED = 5 };
 
 // device status bits, folded into a csz_status by the host

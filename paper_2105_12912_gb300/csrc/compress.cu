@@ -704,40 +704,54 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
     for (uint32_t i = tid; i < nr; i += kEncThreads) atomicAdd(&s_hist[s_rv[i]], (uint32_t)s_rl[i]);
     __syncthreads();
     // block statistics in one pass and one reduction: entropy sum, |delta| sum, top
-    // count, and (selector) code changes at distance 8
+    // count and largest in-range |delta|, and (selector) the madogram's code changes
+    // at the distances 1, 26, ..., 176
     uint64_t S_ = 0, absd = 0;
-    uint32_t f1 = 0, var8 = 0;
+    uint32_t f1 = 0, maxd = 0, mism = 0;
     for (int c = tid; c < kNsymCode; c += kEncThreads) {
       const uint32_t h = s_hist[c];
       if (h) {
         S_ += (uint64_t)h * log2_q16_small(h);
         f1 = max(f1, h);
-        if (c != 0) absd += (uint64_t)h * (uint64_t)abs((int)c - (int)r);
+        if (c != 0) {
+          const uint32_t d = (uint32_t)abs((int)c - (int)r);
+          absd += (uint64_t)h * d;
+          maxd = max(maxd, d);
+        }
       }
     }
-    const bool want_var8 = !(sel == SEL_HEURISTIC && !analyze);
-    if (want_var8)
-      for (uint32_t j = tid; j + 8 < m; j += kEncThreads) var8 += s_c[j] != s_c[j + 8];
+    const bool want_mado = !(sel == SEL_HEURISTIC && !analyze);
+    if (want_mado) {
+#pragma unroll 1
+      for (uint32_t k = 0; k < kMadoN; k++) {
+        const uint32_t d = kMadoD0 + kMadoStep * k;
+        for (uint32_t j = tid; j + d < m; j += kEncThreads) mism += s_c[j] != s_c[j + d];
+      }
+    }
     S_ = warp_sum(S_);
     absd = warp_sum(absd);
-    var8 = warp_sum(var8);
+    mism = warp_sum(mism);
 #pragma unroll
-    for (int o = 16; o; o >>= 1) f1 = max(f1, __shfl_xor_sync(~0u, f1, o));
+    for (int o = 16; o; o >>= 1) {
+      f1 = max(f1, __shfl_xor_sync(~0u, f1, o));
+      maxd = max(maxd, __shfl_xor_sync(~0u, maxd, o));
+    }
     if ((tid & 31) == 0) {
       s_scan64[4 * wid + 0] = S_;
       s_scan64[4 * wid + 1] = absd;
-      s_scan64[4 * wid + 2] = f1;
-      s_scan64[4 * wid + 3] = var8;
+      s_scan64[4 * wid + 2] = ((uint64_t)f1 << 32) | maxd;
+      s_scan64[4 * wid + 3] = mism;
     }
     __syncthreads();
     if (tid == 0) {
       S_ = absd = 0;
-      f1 = var8 = 0;
+      f1 = maxd = mism = 0;
       for (int v = 0; v < kEncThreads / 32; v++) {
         S_ += s_scan64[4 * v + 0];
         absd += s_scan64[4 * v + 1];
-        f1 = max(f1, (uint32_t)s_scan64[4 * v + 2]);
-        var8 += (uint32_t)s_scan64[4 * v + 3];
+        f1 = max(f1, (uint32_t)(s_scan64[4 * v + 2] >> 32));
+        maxd = max(maxd, (uint32_t)s_scan64[4 * v + 2]);
+        mism += (uint32_t)s_scan64[4 * v + 3];
       }
     }
     const int64_t Lm = log2_q16_small(m);
@@ -758,17 +772,20 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
       if (tid == 0) {
         const uint32_t zero = s_hist[r];
         const uint32_t outl = s_hist[0];
-        const uint32_t near1 =
-            s_hist[r] + (r + 1 < 2 * r ? s_hist[r + 1] : 0u) + (r - 1 > 0 ? s_hist[r - 1] : 0u);
+        uint32_t pairs = 0;
+        for (uint32_t k = 0; k < kMadoN; k++) {
+          const uint32_t d = kMadoD0 + kMadoStep * k;
+          pairs += m > d ? m - d : 0u;
+        }
         const float fm = (float)m;
         s_feat[0] = (float)zero / fm;
         s_feat[1] = (float)NH / (float)((uint64_t)m * 65536ull);
         s_feat[2] = (float)f1 / fm;
-        s_feat[3] = (float)near1 / fm;
+        s_feat[3] = (float)log2_q16_small(1u + maxd) / 65536.0f;
         s_feat[4] = (float)nr / fm;
         s_feat[5] = (float)outl / fm;
         s_feat[6] = (float)absd / (float)((uint64_t)m * r);
-        s_feat[7] = (float)var8 / fm;
+        s_feat[7] = pairs ? (float)mism / (float)pairs : 0.0f;
       }
       __syncthreads();
       if (analyze) {

@@ -569,12 +569,15 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
     const ConstructArgs& A = T->a;
     const uint32_t b = t - base(f);
     if (T->use_tma) {
-      // every thread observes the completion itself (acquire of the TMA writes)
-      if (!mbar_wait(&S.bar[cur], phase[cur], spin_limit)) {
+      // every thread observes the completion itself (acquire of the TMA writes); the
+      // phase advances only when the wait succeeded, so that after a timeout the drain
+      // below still waits on the phase of the copy that did not complete
+      if (mbar_wait(&S.bar[cur], phase[cur], spin_limit)) {
+        phase[cur] ^= 1u;
+      } else {
         atomicOr(&A.st->status, ERR_TIMEOUT);
         s_fail = 1;
       }
-      phase[cur] ^= 1u;
     } else {
       load_tile_threads(A, b, S.in[cur]);
     }
@@ -590,7 +593,8 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
   if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   if (s_fail) {
     // a fetch did not complete in time: wait once more (bounded) for both buffers'
-    // copies so no transfer outlives the CTA, then leave
+    // copies so no transfer outlives the CTA, then leave (phase[cur] still names the
+    // phase of the copy that timed out; phase[cur ^ 1] that of the one issued after it)
     if (tid == 0) {
       mbar_wait(&S.bar[cur], phase[cur], spin_limit);
       if (s_f[cur ^ 1] >= 0 && task(s_f[cur ^ 1])->use_tma)

@@ -5,14 +5,17 @@
 #include <mutex>
 
 #include "cszp.h"
+#include "host.h"
 #include "kernels.h"
 
 namespace {
 
-// Scratch for any archive of at most kStaticMaxBlocks codec blocks (the workspace of
-// a 64-block shape is about 1.16 MiB).  Every GPU that loads the library holds this
-// array until the process exits.
+// Scratch for any archive of at most kStaticMaxBlocks codec blocks: the workspace of
+// a 64-block shape is about 1.16 MiB, and the last 256 bytes hold the call's status
+// word.  Every GPU that loads the library holds this array until the process exits.
 constexpr size_t kStaticScratchBytes = 1280 * 1024;
+constexpr size_t kStatusBytes = 256;
+constexpr size_t kStaticWorkspaceBytes = kStaticScratchBytes - kStatusBytes;
 constexpr uint64_t kStaticMaxBlocks = 64;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -23,13 +26,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-uint64_t blocks_of(int ndim, const uint64_t* d) {
-  auto cdiv = [](uint64_t a, uint64_t b) { return (a + b - 1) / b; };
-  if (ndim == 1) return cdiv(d[0], 4096);
-  if (ndim == 2) return cdiv(d[0], 64) * cdiv(d[1], 64);
-  return cdiv(d[0], 16) * cdiv(d[1], 16) * cdiv(d[2], 16);
-}
-
 }  // namespace
 
 extern "C" csz_status csz_decompress_static(const uint8_t* d_archive, size_t bytes, float* d_out,
@@ -38,7 +34,7 @@ extern "C" csz_status csz_decompress_static(const uint8_t* d_archive, size_t byt
   if (bytes < 128) return CSZ_E_CORRUPT;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CSZ_E_CUDA;
-  void* scratch = nullptr;
+  unsigned char* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
@@ -46,9 +42,10 @@ extern "C" csz_status csz_decompress_static(const uint8_t* d_archive, size_t byt
       if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) return CSZ_E_CUDA;
       g_scratch_addr[dev] = p;
     }
-    scratch = g_scratch_addr[dev];
+    scratch = static_cast<unsigned char*>(g_scratch_addr[dev]);
   }
-  // the size limit needs the shape, which is in the header
+  // the size limit needs the shape, which is in the header; the same host copy then
+  // drives the decompression (which checks it against the archive on the device)
   uint8_t h[128];
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemcpyAsync(h, d_archive, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
@@ -57,10 +54,17 @@ extern "C" csz_status csz_decompress_static(const uint8_t* d_archive, size_t byt
   uint64_t dims[3] = {0, 0, 0};
   csz_status r = csz_archive_info(h, sizeof(h), &ndim, dims, nullptr, nullptr);
   if (r != CSZ_OK) return r;
-  // (the decompression part of the workspace of a 64-block shape is about 1.16 MiB;
-  // csz_decompress checks the scratch size against it as well)
-  if (blocks_of(ndim, dims) > kStaticMaxBlocks) return CSZ_E_CAPACITY;
-  // csz_decompress clears the device status word at the start of every call; the
-  // rest of the scratch is fully rewritten before it is read
-  return csz_decompress(d_archive, bytes, d_out, out_cap_elems, scratch, kStaticScratchBytes, stream);
+  cszp::Geom g;
+  if (!cszp::make_geom(ndim, dims, g)) return CSZ_E_CORRUPT;
+  if (g.nblk > kStaticMaxBlocks) return CSZ_E_CAPACITY;
+  // the decompression clears the device status at the start of every call; the rest
+  // of the scratch is fully rewritten before it is read
+  uint32_t* d_status = reinterpret_cast<uint32_t*>(scratch + kStaticWorkspaceBytes);
+  r = csz_decompress_async(d_archive, bytes, h, d_out, out_cap_elems, scratch, kStaticWorkspaceBytes, d_status,
+                           stream);
+  if (r != CSZ_OK) return r;
+  uint32_t hs = 0;
+  if (cudaMemcpyAsync(&hs, d_status, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  return static_cast<csz_status>(hs);
 }

@@ -394,7 +394,7 @@ def test_features_special_cases(orc):
     st, ebd, ebf, x2, xr = orc.eb_params(orc.EB_ABS, 0.5)
     c = orc.construct(x, ebf, x2, xr)
     f = orc.block_features(c["codes"], (4096,))
-    assert np.allclose(f[0], [1, 0, 1, 1, 1 / 4096, 0, 0, 0])
+    assert np.allclose(f[0], [1, 0, 1, 0, 1 / 4096, 0, 0, 0])
     rng = np.random.default_rng(2)
     x = rng.integers(-300, 300, 4096).astype(np.float32)
     c = orc.construct(x, ebf, x2, xr)
@@ -405,6 +405,73 @@ def test_features_special_cases(orc):
     hst = np.bincount(codes, minlength=1024)
     p = hst[hst > 0] / 4096
     assert abs(f[1] - (-(p * np.log2(p)).sum())) < 1e-3
+
+
+MADO_DISTANCES = [1, 26, 51, 76, 101, 126, 151, 176]  # every 25th distance of 1..200 (Sec. III-B)
+
+
+def _hand_block(r=512):
+    """A 4096-code block built by hand: a run of 1000 zero residuals, a run of 100
+    outliers (code 0), then a period-8 pattern of residuals -3..4, with |delta| = 300
+    at position 2000 and the largest in-range |delta| = r - 1 at position 3000."""
+    c = [r] * 1000 + [0] * 100 + [r + (i % 8) - 3 for i in range(1100, 4096)]
+    c[2000] = r + 300
+    c[3000] = r - (r - 1)
+    return c
+
+
+def test_features_hand_computed_block(orc):
+    """All 8 selector features on a block with outliers, runs, known |delta| values and
+    a period-8 pattern, against counts written out here from the definitions
+    (Sec. III-B: p1, entropy, runs, and the binary-variance madogram)."""
+    r, m = 512, 4096
+    c = _hand_block(r)
+    f = orc.block_features(np.array(c, np.uint16), (m,), r)[0]
+    # zero residuals: the first run, plus the pattern's delta = 0 positions (i % 8 == 3);
+    # 2000 and 3000 are both 0 mod 8, so neither removes one
+    zero = 1000 + sum(1 for i in range(1100, 4096) if i % 8 == 3)
+    outl = 100
+    deltas = [abs(v - r) for v in c if v != 0]
+    absd = sum(deltas)
+    assert max(deltas) == r - 1 and len(deltas) == m - outl
+    runs = 1 + sum(1 for i in range(1, m) if c[i] != c[i - 1])
+    counts = {}
+    for v in c:
+        counts[v] = counts.get(v, 0) + 1
+    mism = sum(1 for d in MADO_DISTANCES for i in range(m - d) if c[i] != c[i + d])
+    pairs = sum(m - d for d in MADO_DISTANCES)
+    assert f[0] == np.float32(zero) / np.float32(m)
+    assert f[2] == np.float32(max(counts.values())) / np.float32(m)
+    assert max(counts, key=counts.get) == r  # the zero residual is the top code
+    assert f[3] == np.float32(9.0)           # log2(1 + 511), exact in Q16
+    assert f[4] == np.float32(runs) / np.float32(m)
+    assert f[5] == np.float32(outl) / np.float32(m)
+    assert f[6] == np.float32(absd) / np.float32(m * r)  # outliers count 0, denominator m r
+    assert f[7] == np.float32(mism) / np.float32(pairs)
+    p = np.array(list(counts.values()), np.float64) / m
+    assert abs(f[1] - float(-(p * np.log2(p)).sum())) < 1e-3
+
+
+def test_features_closed_forms(orc):
+    """Closed forms: a pure period-8 block changes code at every sampled distance but
+    176 (a multiple of 8); a block that is one code repeated never changes; a block
+    shorter than a distance has no pairs at that distance; log2(1 + max|delta|) is 0
+    for all-zero residuals and log2(5) for max |delta| = 4."""
+    r, m = 512, 4096
+    c = np.array([r + (i % 8) - 3 for i in range(m)], np.uint16)
+    f = orc.block_features(c, (m,), r)[0]
+    want = sum(m - d for d in MADO_DISTANCES if d % 8) / sum(m - d for d in MADO_DISTANCES)
+    assert f[7] == np.float32(sum(m - d for d in MADO_DISTANCES if d % 8)) / np.float32(
+        sum(m - d for d in MADO_DISTANCES))
+    assert abs(f[7] - want) < 1e-7
+    assert abs(f[3] - math.log2(5)) < 2 ** -15
+    assert f[4] == 1.0  # every element starts a run
+    assert f[0] == np.float32(m // 8) / np.float32(m)
+    # a 40-element 1-D field: one partial block; only d = 1 and d = 26 have pairs
+    c = np.array([r + (i % 2) for i in range(40)], np.uint16)
+    f = orc.block_features(c, (40,), r)[0]
+    assert f[7] == np.float32((40 - 1) + (40 - 26) * 0) / np.float32((40 - 1) + (40 - 26))
+    assert f[3] == np.float32(1.0)  # log2(1 + 1)
 
 
 # ---------------------------------------------------------------------------------

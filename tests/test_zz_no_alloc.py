@@ -55,16 +55,26 @@ def test_static_matches_workspace_decompress(api, shape):
         assert _static(lib, oar, onb, oout) == 0
 
 
-def test_static_rejects_more_than_64_blocks(api):
+@pytest.mark.parametrize("over,at", [
+    ((64 * 4096 + 1,), (64 * 4096,)),            # 1-D: 65 blocks / 64 blocks
+    ((512, 576), (512, 512)),                    # 2-D: 8 x 9 = 72 blocks / 8 x 8 = 64
+    ((64, 64, 65), (64, 64, 64)),                # 3-D: 4 x 4 x 5 = 80 blocks / 4^3 = 64
+    ((16, 16, 1040), (16, 16, 1024)),            # 3-D: 1 x 1 x 65 / 1 x 1 x 64
+])
+def test_static_block_limit(api, over, at):
+    """One block over the 64-block limit is refused with CSZ_E_CAPACITY before any
+    device work; exactly 64 blocks decompress, bit-identical to csz_decompress."""
     from paper_2105_12912_gb300 import _lib
     lib = _lib.lib()
-    x = torch.linspace(0, 1, 64 * 4096 + 1, device="cuda")
+    n = int(np.prod(over))
+    x = torch.linspace(0, 1, n, device="cuda").reshape(over)
     ar, nb, _ = api.compress(x, 1e-3)
     out = torch.empty_like(x)
     assert _static(lib, ar, nb, out) == 5  # CSZ_E_CAPACITY
-    y = torch.linspace(0, 1, 64 * 4096, device="cuda")
+    n = int(np.prod(at))
+    y = torch.linspace(0, 1, n, device="cuda").reshape(at)
     ar, nb, _ = api.compress(y, 1e-3)
-    out = torch.empty_like(y)
+    out = torch.full_like(y, float("nan"))
     assert _static(lib, ar, nb, out) == 0
     ref, _ = api.decompress(ar, nb)
-    assert torch.equal(out, ref)
+    assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
