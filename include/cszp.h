@@ -64,8 +64,18 @@ typedef struct {
   uint32_t radius;               /* quantization radius r (Alg. 1), 1..512; 0 = 512 */
   uint32_t select;               /* csz_select; default EXHAUSTIVE */
   const float* selector_weights; /* device pointer, CSZ_MLP_PARAMS floats; LEARNED only */
-  uint32_t reserved[4];          /* must be zero */
+  uint32_t flags;                /* CSZ_FLAG_* bits; 0 = chunked Lorenzo */
+  uint32_t reserved[3];          /* must be zero */
 } csz_options;
+
+/* Global (unchunked) Lorenzo prediction: one chunk spans the whole field, so the
+   predictor reads zero only outside the field, not at every chunk face (the paper's
+   partial-sum reconstruction, Sec. IV-B, holds for the whole field).  Smaller
+   archives on smooth fields; compression and decompression take more passes.
+   Single-field FP32 calls only (csz_compress / csz_compress_with_header with this
+   flag; decompression follows the archive's header flag): CSZ_E_ARG for double
+   fields and batches. */
+#define CSZ_FLAG_GLOBAL_LORENZO 1u
 
 #define CSZ_MLP_PARAMS 1443 /* W1[32][8] b1[32] W2[32][32] b2[32] W3[3][32] b3[3] */
 
@@ -133,6 +143,31 @@ csz_status csz_decompress(const uint8_t* d_archive, size_t bytes, float* d_out,
 csz_status csz_decompress_async(const uint8_t* d_archive, size_t bytes, const uint8_t* h_header,
                                 float* d_out, uint64_t out_cap_elems, void* d_workspace,
                                 size_t workspace_bytes, uint32_t* d_status, void* stream);
+
+/*
+ * Double-precision fields (SZ's double datasets; the paper's kernels take FP32).  The
+ * same method with prequantization in double: the quantization step is
+ * step = fl64(2 eb_d (1 - 2^-24)), k = nearest integer to x / step (checked exactly
+ * against the bound, moving to the neighbour if the product rounded across a half
+ * point), and the reconstruction x' = fl64(k * step).  Guarantee: |x - x'| <= eb_d on
+ * every element, with no verbatim patches (the shrink covers the rounding of
+ * k * step).  |x / step| must stay below 2^27 (CSZ_E_RANGE otherwise).  The archive is
+ * the FP32 layout with header flag 4; csz_decompress refuses it (CSZ_E_ARG) and
+ * csz_decompress_f64 refuses an FP32 archive.  Arguments, workspace (the same size),
+ * ownership and errors as for csz_compress / csz_decompress; the batch calls take FP32
+ * fields only.
+ */
+csz_status csz_compress_f64(const double* d_field, int ndim, const uint64_t* dims, int eb_mode,
+                            double eb, const csz_options* opt, void* d_workspace,
+                            size_t workspace_bytes, uint8_t* d_archive, size_t archive_cap,
+                            size_t* h_archive_bytes, void* stream);
+csz_status csz_decompress_f64(const uint8_t* d_archive, size_t bytes, double* d_out,
+                              uint64_t out_cap_elems, void* d_workspace, size_t workspace_bytes,
+                              void* stream);
+
+/* Bytes per element of the field an archive holds (4: FP32, 8: double), from its
+   header in host memory; 0 if the header is not valid. */
+int csz_archive_elem_bytes(const uint8_t* h_archive, size_t bytes);
 
 /*
  * Decompression that allocates nothing and takes no workspace.  Some callers cannot
@@ -246,9 +281,9 @@ void csz_batch_destroy(csz_batch* batch);
  *   d_feat[b][8]    features: zero-residual fraction, code entropy (bits), top-code
  *                   probability, log2(1 + max |delta|) over in-range codes, runs per
  *                   element, outlier fraction, mean |delta|/r (outliers count 0), and
- *                   the RLE roughness of Sec. III-B (binary-variance madogram pooled
- *                   over the distances 1, 26, ..., 176); each a ratio of integers
- *                   formed with one FP32 division
+ *                   the RLE roughness of Sec. III-B (binary-variance madogram on the
+ *                   pairs (i, i + 1 + 25 (i mod 8))); each a ratio of integers formed
+ *                   with one FP32 division
  *   d_target[b][3]  log2 of each codec's bits per element, in 1/65536 steps
  *   d_sizes[b][3]   each codec's exact payload bytes (0xffffffff: not applicable)
  *   d_valid[b]      1 where the learned selector decides the block

@@ -82,6 +82,14 @@ static int make_geom(int ndim, const uint64_t* dims, geom_t* g) {
   return ORC_OK;
 }
 
+/* Global (unchunked) Lorenzo prediction (the extension the paper's partial-sum proof
+   allows, Sec. IV-B "Partial-Sum Lorenzo Reconstruction": the proof holds for a
+   whole field): one chunk spans the field, so prediction reads zero only outside the
+   field.  Codec blocks are unchanged. */
+static void make_global(geom_t* g) {
+  for (int d = 0; d < 3; d++) g->chk[d] = g->n[d];
+}
+
 /* origin and in-field extents of codec block b (blocks in row-major order) */
 static void block_box(const geom_t* g, uint64_t b, uint64_t org[3], uint64_t w[3]) {
   uint64_t bi[3];
@@ -227,6 +235,88 @@ int orc_prequant(float x, float eb_f, float ebx2_f, float ebx2_r, int32_t* k, in
 }
 
 /* ------------------------------------------------------------------------------- */
+/* double-precision input (SZ's double-precision datasets, Sec. II-B and V-A; the    */
+/* paper's kernels take FP32).  Everything after prequantization is the FP32 path.  */
+/* ------------------------------------------------------------------------------- */
+
+int orc_value_range_f64(const double* x, uint64_t n, double* vmin, double* vmax) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (uint64_t i = 0; i < n; i++) {
+    if (!isfinite(x[i])) return ORC_E_NONFINITE;
+    if (x[i] < lo) lo = x[i];
+    if (x[i] > hi) hi = x[i];
+  }
+  *vmin = lo;
+  *vmax = hi;
+  return ORC_OK;
+}
+
+/*
+ * Bound and quantization step in double precision (a reading: the paper defines
+ * prequantization only as d° = round(d / 2eb)).  ABS: eb_d = eb; REL: eb_d =
+ * eb * (max - min).  The step is 2 eb_d shrunk by one part in 2^24,
+ * step = fl64(2 eb_d * (1 - 2^-24)), and rstep = fl64(1 / step).  With |k| < 2^27 the
+ * rounding of fl64(k * step) moves the reconstruction by at most 2^-53 * 2^28 eb_d
+ * = 2^-25 eb_d, less than the 2^-24 eb_d the shrink leaves, so the nearest integer
+ * always meets |x - fl64(k * step)| <= eb_d and no value needs a verbatim patch.
+ */
+int orc_eb_params_f64(int eb_mode, double eb, double vmin, double vmax, double* eb_d, double* step,
+                      double* rstep) {
+  if (!(eb > 0.0) || !isfinite(eb)) return ORC_E_ARG;
+  double d;
+  if (eb_mode == ORC_EB_ABS) {
+    d = eb;
+  } else if (eb_mode == ORC_EB_REL) {
+    d = eb * (vmax - vmin);
+  } else {
+    return ORC_E_ARG;
+  }
+  if (!(d > 0.0) || !isfinite(d)) return ORC_E_ARG;
+  double st = (2.0 * d) * (1.0 - 0x1p-24);
+  double r = 1.0 / st;
+  if (!(st > 0.0) || !isfinite(st) || !(r > 0.0) || !isfinite(r)) return ORC_E_ARG;
+  *eb_d = d;
+  *step = st;
+  *rstep = r;
+  return ORC_OK;
+}
+
+/* |x - y| > eb decided exactly for doubles: Knuth's TwoSum gives x - y = s + e
+   exactly with s = fl64(x - y); |s| < eb or |s| > eb decides by monotonicity of
+   rounding, |s| == eb by the sign of e. */
+static int exceeds_f64(double x, double y, double eb) {
+  double s = x - y;
+  if (fabs(s) < eb) return 0;
+  if (fabs(s) > eb) return 1;
+  double bv = s - x;
+  double e = (x - (s - bv)) + (-y - bv);
+  return s > 0.0 ? e > 0.0 : e < 0.0;
+}
+
+/* Prequantization of one double (Sec. IV-A1 read for FP64): k0 = nearest integer
+   (ties to even) to fl64(x * rstep); if fl64(k0 * step) misses x by more than eb_d,
+   the neighbour on x's side (k0 is within one of the exact nearest integer, which
+   always meets the bound).  |fl64(x * rstep)| must stay below 2^27 (Lorenzo sums in
+   int32: 3-D residuals reach 8 |k|); otherwise ORC_E_RANGE. */
+int orc_prequant_f64(double x, double eb_d, double step, double rstep, int32_t* k) {
+  if (!isfinite(x)) return ORC_E_NONFINITE;
+  double v = x * rstep;
+  if (!(fabs(v) < 134217728.0)) return ORC_E_RANGE;
+  int32_t k0 = (int32_t)rint(v);
+  double x0 = (double)k0 * step;
+  if (!exceeds_f64(x, x0, eb_d)) {
+    *k = k0;
+    return ORC_OK;
+  }
+  int32_t k1 = k0 + (x > x0 ? 1 : -1);
+  if (!exceeds_f64(x, (double)k1 * step, eb_d)) {
+    *k = k1;
+    return ORC_OK;
+  }
+  return ORC_E_RANGE; /* unreachable by the step's margin */
+}
+
+/* ------------------------------------------------------------------------------- */
 /* Lorenzo prediction (Sec. IV-B2 equations), chunk-local: a neighbour outside the  */
 /* element's chunk reads as zero ("we initially predict from zeros")                */
 /* ------------------------------------------------------------------------------- */
@@ -270,34 +360,16 @@ static int cmp_u64(const void* a, const void* b) {
  * radius; otherwise q = 0 and delta itself is the outlier (the cuSZ+ change).
  * Codes go to the block-major code stream; records are sorted by key.
  */
-int orc_construct(const float* x, int ndim, const uint64_t* dims, float eb_f, float ebx2_f,
-                  float ebx2_r, uint32_t radius, uint16_t* codes, uint32_t* rec_key,
-                  uint32_t* rec_val, uint64_t rec_cap, uint64_t* n_rec, uint32_t* hist) {
-  geom_t g;
-  int st = make_geom(ndim, dims, &g);
-  if (st) return st;
-  if (radius < 1 || radius > 512) return ORC_E_ARG;
+/* Residuals, codes and records from the prequantized integers K[nelem] (raster
+   order); P[e] marks a verbatim patch of the value patch_vals[e] (FP32 only; P may
+   be NULL). */
+static int construct_k(const int32_t* K, const uint8_t* P, const float* patch_vals, const geom_t* gp,
+                       uint32_t radius, uint16_t* codes, uint32_t* rec_key, uint32_t* rec_val,
+                       uint64_t rec_cap, uint64_t* n_rec, uint32_t* hist) {
+  const geom_t g = *gp;
   uint64_t n = g.nelem;
-  int32_t* K = (int32_t*)malloc(n * sizeof(int32_t));
-  uint8_t* P = (uint8_t*)malloc(n);
   uint64_t* recs = (uint64_t*)malloc((2 * n + 1) * sizeof(uint64_t));
-  if (!K || !P || !recs) {
-    free(K);
-    free(P);
-    free(recs);
-    return ORC_E_CAPACITY;
-  }
-  for (uint64_t e = 0; e < n; e++) {
-    int patch = 0;
-    st = orc_prequant(x[e], eb_f, ebx2_f, ebx2_r, &K[e], &patch);
-    if (st) {
-      free(K);
-      free(P);
-      free(recs);
-      return st;
-    }
-    P[e] = (uint8_t)patch;
-  }
+  if (!recs) return ORC_E_CAPACITY;
   memset(codes, 0, g.nblk * SLOTS * sizeof(uint16_t));
   memset(hist, 0, NSYM_CODE * sizeof(uint32_t));
   uint64_t nr = 0;
@@ -318,17 +390,15 @@ int orc_construct(const float* x, int ndim, const uint64_t* dims, float eb_f, fl
         }
         codes[slot] = q;
         hist[q]++;
-        if (P[e]) {
+        if (P && P[e]) {
           uint32_t bits;
-          memcpy(&bits, &x[e], 4);
+          memcpy(&bits, &patch_vals[e], 4);
           recs[nr++] = ((slot * 2 + 1) << 32) | bits;
         }
       }
   qsort(recs, nr, sizeof(uint64_t), cmp_u64);
   *n_rec = nr;
   if (nr > rec_cap) {
-    free(K);
-    free(P);
     free(recs);
     return ORC_E_CAPACITY;
   }
@@ -336,10 +406,52 @@ int orc_construct(const float* x, int ndim, const uint64_t* dims, float eb_f, fl
     rec_key[i] = (uint32_t)(recs[i] >> 32);
     rec_val[i] = (uint32_t)(recs[i] & 0xffffffffu);
   }
-  free(K);
-  free(P);
   free(recs);
   return ORC_OK;
+}
+
+int orc_construct(const float* x, int ndim, const uint64_t* dims, float eb_f, float ebx2_f,
+                  float ebx2_r, uint32_t radius, uint16_t* codes, uint32_t* rec_key,
+                  uint32_t* rec_val, uint64_t rec_cap, uint64_t* n_rec, uint32_t* hist) {
+  geom_t g;
+  int st = make_geom(ndim, dims, &g);
+  if (st) return st;
+  if (radius < 1 || radius > 512) return ORC_E_ARG;
+  uint64_t n = g.nelem;
+  int32_t* K = (int32_t*)malloc(n * sizeof(int32_t));
+  uint8_t* P = (uint8_t*)malloc(n);
+  if (!K || !P) {
+    free(K);
+    free(P);
+    return ORC_E_CAPACITY;
+  }
+  for (uint64_t e = 0; e < n && !st; e++) {
+    int patch = 0;
+    st = orc_prequant(x[e], eb_f, ebx2_f, ebx2_r, &K[e], &patch);
+    P[e] = (uint8_t)patch;
+  }
+  if (!st)
+    st = construct_k(K, P, x, &g, radius, codes, rec_key, rec_val, rec_cap, n_rec, hist);
+  free(K);
+  free(P);
+  return st;
+}
+
+/* Lorenzo construction of a double-precision field (prequantization above, then the
+   FP32 path's residuals; no patches). */
+int orc_construct_f64(const double* x, int ndim, const uint64_t* dims, double eb_d, double step,
+                      double rstep, uint32_t radius, uint16_t* codes, uint32_t* rec_key,
+                      uint32_t* rec_val, uint64_t rec_cap, uint64_t* n_rec, uint32_t* hist) {
+  geom_t g;
+  int st = make_geom(ndim, dims, &g);
+  if (st) return st;
+  if (radius < 1 || radius > 512) return ORC_E_ARG;
+  int32_t* K = (int32_t*)malloc(g.nelem * sizeof(int32_t));
+  if (!K) return ORC_E_CAPACITY;
+  for (uint64_t e = 0; e < g.nelem && !st; e++) st = orc_prequant_f64(x[e], eb_d, step, rstep, &K[e]);
+  if (!st) st = construct_k(K, NULL, NULL, &g, radius, codes, rec_key, rec_val, rec_cap, n_rec, hist);
+  free(K);
+  return st;
 }
 
 /* ------------------------------------------------------------------------------- */
@@ -824,11 +936,13 @@ int orc_heuristic_pick(const uint32_t* h, int nsym, uint32_t m) {
  *                                  denominator counts all m codes, so an outlier adds 0
  *                                  (its delta lives in a record, not in the code)
  *  7 RLE roughness                 the madogram with binary variance (Sec. III-B,
- *                                  "Modeling RLE Compressibility"): pairs (i, i + d)
- *                                  whose codes differ, pooled over the distances
- *                                  d = 1, 26, 51, ..., 176 (every 25th distance of the
- *                                  paper's uniform d in [1, 200]), over the number of
- *                                  such pairs inside the block (0 if none)
+ *                                  "Modeling RLE Compressibility") on a systematic
+ *                                  sample of pairs: position i is paired with
+ *                                  i + d(i), d(i) = 1 + 25 (i mod 8), so the distances
+ *                                  1, 26, ..., 176 (every 25th of the paper's uniform
+ *                                  d in [1, 200]) each take every 8th position; the
+ *                                  feature is the fraction of the pairs inside the
+ *                                  block whose codes differ (0 if there are none)
  */
 static const uint32_t MADO_D0 = 1, MADO_STEP = 25, MADO_N = 8;
 
@@ -848,9 +962,9 @@ static void features_of(const uint16_t* c, uint64_t m, uint32_t radius, float* f
     }
     if (i == 0 || c[i] != c[i - 1]) runs++;
   }
-  for (uint32_t k = 0; k < MADO_N; k++) {
-    const uint64_t d = MADO_D0 + MADO_STEP * k;
-    for (uint64_t i = 0; i + d < m; i++) {
+  for (uint64_t i = 0; i < m; i++) {
+    const uint64_t d = MADO_D0 + MADO_STEP * (i % MADO_N);
+    if (i + d < m) {
       pairs++;
       if (c[i] != c[i + d]) mism++;
     }
@@ -1109,24 +1223,38 @@ int orc_selector_targets(const uint64_t* sizes, int ndim, const uint64_t* dims, 
   return ORC_OK;
 }
 
-int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, double eb,
-                 uint32_t radius, int select, const float* mlp_w, uint8_t* out, size_t cap,
-                 size_t* out_bytes) {
+/* Compression of an FP32 field (x32) or, with the archive flag ORC_FLAG_F64, of a
+   double-precision one (x64). */
+static int compress_impl(const float* x32, const double* x64, int ndim, const uint64_t* dims, int eb_mode,
+                         double eb, uint32_t radius, int select, const float* mlp_w, int global, uint8_t* out,
+                         size_t cap, size_t* out_bytes) {
   geom_t g;
   int st = make_geom(ndim, dims, &g);
   if (st) return st;
+  if (global) make_global(&g);
   if (radius < 1 || radius > 512) return ORC_E_ARG;
   if (select < ORC_SEL_HUFF || select > ORC_SEL_LEARNED) return ORC_E_ARG;
   if (select == ORC_SEL_LEARNED && !mlp_w) return ORC_E_ARG;
   if (!(eb > 0.0) || !isfinite(eb) || (eb_mode != ORC_EB_ABS && eb_mode != ORC_EB_REL)) return ORC_E_ARG;
   /* a non-finite value is reported before any range error, in either mode */
-  float vmin = 0.0f, vmax = 0.0f;
-  st = orc_value_range(x, g.nelem, &vmin, &vmax);
-  if (st) return st;
-  double eb_d;
-  float eb_f, ebx2_f, ebx2_r;
-  st = orc_eb_params(eb_mode, eb, vmin, vmax, &eb_d, &eb_f, &ebx2_f, &ebx2_r);
-  if (st) return st;
+  double eb_d, step = 0.0, rstep = 0.0;
+  float eb_f = 0.0f, ebx2_f = 0.0f, ebx2_r = 0.0f;
+  if (x64) {
+    double vmin = 0.0, vmax = 0.0;
+    st = orc_value_range_f64(x64, g.nelem, &vmin, &vmax);
+    if (st) return st;
+    st = orc_eb_params_f64(eb_mode, eb, vmin, vmax, &eb_d, &step, &rstep);
+    if (st) return st;
+    /* informational FP32 copy of the bound: the largest float not above eb_d */
+    eb_f = (float)eb_d;
+    if ((double)eb_f > eb_d) eb_f = nextafterf(eb_f, 0.0f);
+  } else {
+    float vmin = 0.0f, vmax = 0.0f;
+    st = orc_value_range(x32, g.nelem, &vmin, &vmax);
+    if (st) return st;
+    st = orc_eb_params(eb_mode, eb, vmin, vmax, &eb_d, &eb_f, &ebx2_f, &ebx2_r);
+    if (st) return st;
+  }
 
   uint64_t slots = g.nblk * SLOTS;
   uint16_t* codes = (uint16_t*)malloc(slots * sizeof(uint16_t));
@@ -1138,8 +1266,29 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
   uint8_t* codec = (uint8_t*)malloc(g.nblk);
   run_t* runs = (run_t*)malloc(SLOTS * sizeof(run_t));
   uint64_t nrec = 0;
-  st = orc_construct(x, ndim, dims, eb_f, ebx2_f, ebx2_r, radius, codes, rk, rv, 2 * g.nelem + 1,
-                     &nrec, hist);
+  {
+    /* prequantization, then the residuals under the chunking of g */
+    int32_t* K = (int32_t*)malloc(g.nelem * sizeof(int32_t));
+    uint8_t* P = x64 ? NULL : (uint8_t*)malloc(g.nelem);
+    if (!K || (!x64 && !P)) {
+      free(K);
+      free(P);
+      st = ORC_E_CAPACITY;
+      goto done;
+    }
+    for (uint64_t e = 0; e < g.nelem && !st; e++) {
+      if (x64) {
+        st = orc_prequant_f64(x64[e], eb_d, step, rstep, &K[e]);
+      } else {
+        int patch = 0;
+        st = orc_prequant(x32[e], eb_f, ebx2_f, ebx2_r, &K[e], &patch);
+        P[e] = (uint8_t)patch;
+      }
+    }
+    if (!st) st = construct_k(K, P, x32, &g, radius, codes, rk, rv, 2 * g.nelem + 1, &nrec, hist);
+    free(K);
+    free(P);
+  }
   if (st) goto done;
   const int all_blocks = select == ORC_SEL_RLE_HUFF || select == ORC_SEL_RLE;
   orc_run_stats(codes, ndim, dims, all_blocks, vh, lh, nruns);
@@ -1181,7 +1330,8 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
     ncodec[c]++;
     payload += s[c];
   }
-  uint32_t flags = (ncodec[ORC_CODEC_HUFF] ? 1u : 0u) | (ncodec[ORC_CODEC_RLE_HUFF] ? 2u : 0u);
+  uint32_t flags = (ncodec[ORC_CODEC_HUFF] ? 1u : 0u) | (ncodec[ORC_CODEC_RLE_HUFF] ? 2u : 0u) |
+                   (x64 ? ORC_FLAG_F64 : 0u) | (global ? ORC_FLAG_GLOBAL : 0u);
   uint64_t off_bb = HDR + align8(g.nblk);
   uint64_t off_rec = off_bb + align8(4 * g.nblk);
   uint64_t off_pay = off_rec + 8 * nrec;
@@ -1261,6 +1411,25 @@ done:
   return st;
 }
 
+int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, double eb,
+                 uint32_t radius, int select, const float* mlp_w, uint8_t* out, size_t cap,
+                 size_t* out_bytes) {
+  return compress_impl(x, NULL, ndim, dims, eb_mode, eb, radius, select, mlp_w, 0, out, cap, out_bytes);
+}
+
+int orc_compress_f64(const double* x, int ndim, const uint64_t* dims, int eb_mode, double eb,
+                     uint32_t radius, int select, const float* mlp_w, uint8_t* out, size_t cap,
+                     size_t* out_bytes) {
+  return compress_impl(NULL, x, ndim, dims, eb_mode, eb, radius, select, mlp_w, 0, out, cap, out_bytes);
+}
+
+int orc_compress_ex(const float* x32, const double* x64, int ndim, const uint64_t* dims, int eb_mode,
+                    double eb, uint32_t radius, int select, const float* mlp_w, int global, uint8_t* out,
+                    size_t cap, size_t* out_bytes) {
+  if ((x32 == NULL) == (x64 == NULL)) return ORC_E_ARG;
+  return compress_impl(x32, x64, ndim, dims, eb_mode, eb, radius, select, mlp_w, global, out, cap, out_bytes);
+}
+
 /* parse and validate an archive: header, sections, books, per-block decode into codes */
 typedef struct {
   hdr_t h;
@@ -1278,9 +1447,16 @@ static int parse(const uint8_t* ar, size_t bytes, parsed_t* P) {
   if (make_geom(h->ndim, h->dims, &P->g)) return ORC_E_CORRUPT;
   for (int i = h->ndim; i < 3; i++)
     if (h->dims[i]) return ORC_E_CORRUPT;
-  if (h->radius < 1 || h->radius > 512 || h->lanes != LANES || h->flags > 3) return ORC_E_CORRUPT;
+  if (h->radius < 1 || h->radius > 512 || h->lanes != LANES || h->flags > 15) return ORC_E_CORRUPT;
+  if (h->flags & ORC_FLAG_GLOBAL) make_global(&P->g);
   if (h->nblk != P->g.nblk || h->n_rec != h->n_out + h->n_patch) return ORC_E_CORRUPT;
-  if (!(h->eb_f > 0.0f) || !isfinite(2.0f * h->eb_f)) return ORC_E_CORRUPT;
+  if (h->flags & ORC_FLAG_F64) {
+    /* double fields: the step follows from eb_d; there are no verbatim patches */
+    double d = h->eb_d, stp = (2.0 * d) * (1.0 - 0x1p-24);
+    if (!(d > 0.0) || !isfinite(d) || !(stp > 0.0) || !isfinite(stp) || h->n_patch) return ORC_E_CORRUPT;
+  } else if (!(h->eb_f > 0.0f) || !isfinite(2.0f * h->eb_f)) {
+    return ORC_E_CORRUPT;
+  }
   if (h->n_rec > 2 * P->g.nelem || h->payload > bytes || (h->payload & 3)) return ORC_E_CORRUPT;
   P->off_bb = HDR + align8(h->nblk);
   P->off_rec = P->off_bb + align8(4 * h->nblk);
@@ -1427,26 +1603,15 @@ int orc_decode_codes(const uint8_t* ar, size_t bytes, uint16_t* codes, uint64_t 
  * Decompression (Alg. 1 decompression part, read through the recurrence it replaces):
  * fuse q' = q - r, or delta at an outlier slot (Sec. IV-B1), then rebuild each
  * prequantized integer sequentially, k = p(k) + q', in raster order (every
- * predictor neighbour precedes its element), scale by 2eb, and put back the
- * verbatim patches.
+ * predictor neighbour precedes its element).  K receives the integers; the callers
+ * scale them by the quantization step and put back the verbatim patches.
  */
-int orc_decompress(const uint8_t* ar, size_t bytes, float* out, uint64_t cap_elems) {
-  parsed_t* P = (parsed_t*)malloc(sizeof(parsed_t));
-  int st = parse(ar, bytes, P);
-  if (st) {
-    free(P);
-    return st;
-  }
+static int rebuild_k(const uint8_t* ar, size_t bytes, parsed_t* P, int32_t* K) {
   const geom_t* g = &P->g;
-  if (cap_elems < g->nelem) {
-    free(P);
-    return ORC_E_CAPACITY;
-  }
   uint64_t slots = g->nblk * SLOTS;
   uint16_t* codes = (uint16_t*)malloc(slots * sizeof(uint16_t));
   int32_t* qp = (int32_t*)malloc(slots * sizeof(int32_t));
-  int32_t* K = (int32_t*)malloc(g->nelem * sizeof(int32_t));
-  st = decode_all(ar, bytes, P, codes);
+  int st = decode_all(ar, bytes, P, codes);
   if (st) goto fail;
   const int32_t r = (int32_t)P->h.radius;
   for (uint64_t s = 0; s < slots; s++) qp[s] = (int32_t)codes[s] - r;
@@ -1469,19 +1634,50 @@ int orc_decompress(const uint8_t* ar, size_t bytes, float* out, uint64_t cap_ele
         int64_t k = lorenzo_predict(K, g, z, y, x) + qp[slot_of(g, z, y, x)];
         K[e] = (int32_t)(uint32_t)k; /* modular int32: the exact k of a valid archive */
       }
-  const float ebx2 = 2.0f * P->h.eb_f;
-  for (uint64_t e = 0; e < g->nelem; e++) out[e] = (float)K[e] * ebx2;
-  for (uint64_t i = 0; i < P->h.n_rec; i++) {
-    uint32_t key = get32(ar + P->off_rec + 8 * i);
-    if (key & 1) {
-      uint32_t val = get32(ar + P->off_rec + 8 * i + 4);
-      memcpy(&out[elem_of_slot(g, key >> 1)], &val, 4);
-    }
-  }
   st = ORC_OK;
 fail:
   free(codes);
   free(qp);
+  return st;
+}
+
+/* FP32 archive: x' = fl32(k * 2 eb_f), then the verbatim patches */
+int orc_decompress(const uint8_t* ar, size_t bytes, float* out, uint64_t cap_elems) {
+  parsed_t* P = (parsed_t*)malloc(sizeof(parsed_t));
+  int st = parse(ar, bytes, P);
+  if (st == ORC_OK && (P->h.flags & ORC_FLAG_F64)) st = ORC_E_ARG; /* a double field */
+  if (st == ORC_OK && cap_elems < P->g.nelem) st = ORC_E_CAPACITY;
+  int32_t* K = st ? NULL : (int32_t*)malloc(P->g.nelem * sizeof(int32_t));
+  if (st == ORC_OK) st = rebuild_k(ar, bytes, P, K);
+  if (st == ORC_OK) {
+    const geom_t* g = &P->g;
+    const float ebx2 = 2.0f * P->h.eb_f;
+    for (uint64_t e = 0; e < g->nelem; e++) out[e] = (float)K[e] * ebx2;
+    for (uint64_t i = 0; i < P->h.n_rec; i++) {
+      uint32_t key = get32(ar + P->off_rec + 8 * i);
+      if (key & 1) {
+        uint32_t val = get32(ar + P->off_rec + 8 * i + 4);
+        memcpy(&out[elem_of_slot(g, key >> 1)], &val, 4);
+      }
+    }
+  }
+  free(K);
+  free(P);
+  return st;
+}
+
+/* double archive: x' = fl64(k * step), step = fl64(2 eb_d (1 - 2^-24)) */
+int orc_decompress_f64(const uint8_t* ar, size_t bytes, double* out, uint64_t cap_elems) {
+  parsed_t* P = (parsed_t*)malloc(sizeof(parsed_t));
+  int st = parse(ar, bytes, P);
+  if (st == ORC_OK && !(P->h.flags & ORC_FLAG_F64)) st = ORC_E_ARG; /* an FP32 field */
+  if (st == ORC_OK && cap_elems < P->g.nelem) st = ORC_E_CAPACITY;
+  int32_t* K = st ? NULL : (int32_t*)malloc(P->g.nelem * sizeof(int32_t));
+  if (st == ORC_OK) st = rebuild_k(ar, bytes, P, K);
+  if (st == ORC_OK) {
+    const double step = (2.0 * P->h.eb_d) * (1.0 - 0x1p-24);
+    for (uint64_t e = 0; e < P->g.nelem; e++) out[e] = (double)K[e] * step;
+  }
   free(K);
   free(P);
   return st;

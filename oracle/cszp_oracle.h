@@ -66,6 +66,31 @@ int orc_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode, do
 
 int orc_decompress(const uint8_t* ar, size_t bytes, float* out, uint64_t cap_elems);
 
+/* double-precision fields: the same archive with flag ORC_FLAG_F64; prequantization in
+   double with the step 2 eb (1 - 2^-24), reconstruction x' = fl64(k * step), and the
+   guarantee |x - x'| <= eb_d on every element.  orc_decompress refuses such an
+   archive (ORC_E_ARG), orc_decompress_f64 an FP32 one. */
+#define ORC_FLAG_F64 4u
+/* global (unchunked) Lorenzo: one chunk spans the whole field, so prediction reads
+   zero only outside it; the archive carries flag ORC_FLAG_GLOBAL and decompresses
+   through the same recurrence */
+#define ORC_FLAG_GLOBAL 8u
+/* general entry: exactly one of x32 / x64; global selects the unchunked predictor */
+int orc_compress_ex(const float* x32, const double* x64, int ndim, const uint64_t* dims, int eb_mode,
+                    double eb, uint32_t radius, int select, const float* mlp_w, int global, uint8_t* out,
+                    size_t cap, size_t* out_bytes);
+int orc_compress_f64(const double* x, int ndim, const uint64_t* dims, int eb_mode, double eb,
+                     uint32_t radius, int select, const float* mlp_w, uint8_t* out, size_t cap,
+                     size_t* out_bytes);
+int orc_decompress_f64(const uint8_t* ar, size_t bytes, double* out, uint64_t cap_elems);
+int orc_value_range_f64(const double* x, uint64_t n, double* vmin, double* vmax);
+int orc_eb_params_f64(int eb_mode, double eb, double vmin, double vmax, double* eb_d, double* step,
+                      double* rstep);
+int orc_prequant_f64(double x, double eb_d, double step, double rstep, int32_t* k);
+int orc_construct_f64(const double* x, int ndim, const uint64_t* dims, double eb_d, double step,
+                      double rstep, uint32_t radius, uint16_t* codes, uint32_t* rec_key,
+                      uint32_t* rec_val, uint64_t rec_cap, uint64_t* n_rec, uint32_t* hist);
+
 /* ---- stage-level entry points (parity and pin tests) ------------------------------ */
 int orc_value_range(const float* x, uint64_t n, float* vmin, float* vmax);
 

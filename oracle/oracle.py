@@ -66,6 +66,13 @@ def lib():
             "orc_decode_codes": (C.c_int, [_u8p, C.c_size_t, _u16p, C.c_uint64]),
             "orc_selector_targets": (C.c_int, [_u64p, C.c_int, _u64p, _f32p, _u8p]),
             "orc_learned_pick": (C.c_int, [_f32p, _u64p]),
+            "orc_compress_f64": (C.c_int, [_f64p, C.c_int, _u64p, C.c_int, C.c_double, C.c_uint32, C.c_int,
+                                           _f32p, _u8p, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "orc_decompress_f64": (C.c_int, [_u8p, C.c_size_t, _f64p, C.c_uint64]),
+            "orc_eb_params_f64": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, _f64p, _f64p, _f64p]),
+            "orc_prequant_f64": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, _i32p]),
+            "orc_compress_ex": (C.c_int, [_f32p, _f64p, C.c_int, _u64p, C.c_int, C.c_double, C.c_uint32, C.c_int,
+                                          _f32p, C.c_int, _u8p, C.c_size_t, C.POINTER(C.c_size_t)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -300,3 +307,72 @@ def sections(ar):
     rec = ar[off_rec:off_pay].view(np.uint32).reshape(-1, 2) if h["n_rec"] else np.zeros((0, 2), np.uint32)
     return dict(header=h, codec=ar[128:128 + nblk], blk_bytes=ar[off_bb:off_bb + 4 * nblk].view(np.uint32),
                 records=rec, payload=ar[off_pay:off_pay + h["payload"]], books=ar[off_books:h["total"]])
+
+
+# ---- double-precision fields ----------------------------------------------------------
+FLAG_F64 = 4
+
+
+def compress_f64(x: np.ndarray, eb_mode=EB_REL, eb=1e-4, radius=512, select=SEL_EXHAUSTIVE, mlp_w=None,
+                 raise_on_error=True):
+    """Double-precision field -> (status, archive bytes as np.uint8 array)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    dims = x.shape
+    cap = max_archive_bytes(dims) if x.size else 1024
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    nbytes = C.c_size_t(0)
+    w = None if mlp_w is None else np.ascontiguousarray(mlp_w, dtype=np.float32)
+    st = lib().orc_compress_f64(_p(x, _f64p), x.ndim, _p(_dims(dims), _u64p), int(eb_mode), float(eb), int(radius),
+                                int(select), None if w is None else _p(w, _f32p), _p(out, _u8p), out.size,
+                                C.byref(nbytes))
+    if st and raise_on_error:
+        raise OracleError(st, "compress_f64")
+    return st, out[: nbytes.value].copy() if st == 0 else None
+
+
+def decompress_f64(ar: np.ndarray, n: int, raise_on_error=True):
+    ar = np.ascontiguousarray(ar, dtype=np.uint8)
+    out = np.zeros(max(n, 1), dtype=np.float64)
+    st = lib().orc_decompress_f64(_p(ar, _u8p), ar.size, _p(out, _f64p), n)
+    if st and raise_on_error:
+        raise OracleError(st, "decompress_f64")
+    return st, out[:n]
+
+
+def eb_params_f64(eb_mode, eb, vmin=0.0, vmax=0.0):
+    """(status, eb_d, step, rstep)"""
+    ebd, step, rstep = C.c_double(), C.c_double(), C.c_double()
+    st = lib().orc_eb_params_f64(int(eb_mode), float(eb), float(vmin), float(vmax), C.byref(ebd), C.byref(step),
+                                 C.byref(rstep))
+    return st, ebd.value, step.value, rstep.value
+
+
+def prequant_f64(x, eb_d, step, rstep):
+    """(status, k)"""
+    k = C.c_int32()
+    st = lib().orc_prequant_f64(float(x), float(eb_d), float(step), float(rstep), C.byref(k))
+    return st, k.value
+
+
+# ---- general entry (FP32 or double; chunked or global Lorenzo) ------------------------
+FLAG_GLOBAL = 8
+
+
+def compress_ex(x: np.ndarray, eb_mode=EB_REL, eb=1e-4, radius=512, select=SEL_EXHAUSTIVE, mlp_w=None,
+                global_lorenzo=False, raise_on_error=True):
+    """(status, archive) for an FP32 or float64 field; global_lorenzo selects the
+    unchunked predictor (archive flag FLAG_GLOBAL)."""
+    f64 = np.asarray(x).dtype == np.float64
+    x = np.ascontiguousarray(x, dtype=np.float64 if f64 else np.float32)
+    dims = x.shape
+    cap = max_archive_bytes(dims) if x.size else 1024
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    nbytes = C.c_size_t(0)
+    w = None if mlp_w is None else np.ascontiguousarray(mlp_w, dtype=np.float32)
+    st = lib().orc_compress_ex(None if f64 else _p(x, _f32p), _p(x, _f64p) if f64 else None, x.ndim,
+                               _p(_dims(dims), _u64p), int(eb_mode), float(eb), int(radius), int(select),
+                               None if w is None else _p(w, _f32p), 1 if global_lorenzo else 0, _p(out, _u8p),
+                               out.size, C.byref(nbytes))
+    if st and raise_on_error:
+        raise OracleError(st, "compress_ex")
+    return st, out[: nbytes.value].copy() if st == 0 else None

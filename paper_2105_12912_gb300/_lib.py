@@ -14,7 +14,7 @@ STATUS_NAMES = ["ok", "E_ARG", "E_NONFINITE", "E_RANGE", "E_CORRUPT", "E_CAPACIT
 
 class csz_options(C.Structure):
     _fields_ = [("radius", C.c_uint32), ("select", C.c_uint32), ("selector_weights", C.c_void_p),
-                ("reserved", C.c_uint32 * 4)]
+                ("flags", C.c_uint32), ("reserved", C.c_uint32 * 3)]
 
 
 class csz_field(C.Structure):
@@ -52,6 +52,12 @@ SIGNATURES = {
                                            C.POINTER(C.c_size_t), C.c_void_p, C.c_void_p]),
     "csz_decompress_async": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p,
                                        C.c_size_t, C.c_void_p, C.c_void_p]),
+    "csz_compress_f64": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint64), C.c_int, C.c_double,
+                                   C.POINTER(csz_options), C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t,
+                                   C.POINTER(C.c_size_t), C.c_void_p]),
+    "csz_decompress_f64": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t,
+                                     C.c_void_p]),
+    "csz_archive_elem_bytes": (C.c_int, [C.c_void_p, C.c_size_t]),
     "csz_wait_selftest": (C.c_int, [C.c_int, C.c_uint32, C.c_void_p, C.c_size_t, C.c_void_p]),
     "csz_decompress_static": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint64, C.c_void_p]),
     "csz_selector_rows": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint64), C.c_int, C.c_double, C.c_uint32,

@@ -56,16 +56,19 @@ def workspace_bytes(dims) -> int:
 _opt_cache = {}
 
 
-def _options(radius, select, weights):
+FLAG_GLOBAL_LORENZO = 1
+
+
+def _options(radius, select, weights, flags=0):
     if weights is not None:
         if not (weights.is_cuda and weights.dtype == torch.float32 and weights.numel() == MLP_PARAMS):
             raise ValueError("weights must be a float32 CUDA tensor of 1443 parameters")
     key = (int(radius), SELECT[select] if isinstance(select, str) else int(select),
-           weights.data_ptr() if weights is not None else 0)
+           weights.data_ptr() if weights is not None else 0, int(flags))
     opt = _opt_cache.get(key)
     if opt is None:
         opt = L.csz_options()
-        opt.radius, opt.select = key[0], key[1]
+        opt.radius, opt.select, opt.flags = key[0], key[1], key[3]
         if weights is not None:
             opt.selector_weights = C.c_void_p(key[2])
         _opt_cache[key] = opt
@@ -99,18 +102,21 @@ def _ws(device, ws):
 
 def compress(field: torch.Tensor, eb: float, eb_mode: str = "rel", radius: int = 512,
              select: str = "exhaustive", weights: torch.Tensor | None = None, out: torch.Tensor | None = None,
-             workspace: Workspace | None = None, stream=None, raise_on_error: bool = True):
-    """Compress a contiguous FP32 CUDA tensor (1-3 dims).  Returns (archive, nbytes, status):
-    archive is a uint8 CUDA tensor whose first nbytes bytes hold the archive."""
-    if not (field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()):
-        raise ValueError("field must be a contiguous float32 CUDA tensor")
+             workspace: Workspace | None = None, stream=None, raise_on_error: bool = True,
+             global_lorenzo: bool = False):
+    """Compress a contiguous FP32 or float64 CUDA tensor (1-3 dims; float64 goes to
+    csz_compress_f64).  Returns (archive, nbytes, status): archive is a uint8 CUDA
+    tensor whose first nbytes bytes hold the archive."""
+    if not (field.is_cuda and field.dtype in (torch.float32, torch.float64) and field.is_contiguous()):
+        raise ValueError("field must be a contiguous float32 or float64 CUDA tensor")
     dims = tuple(field.shape)
     if out is None:
         out = torch.empty(max_archive_bytes(dims) or 1, dtype=torch.uint8, device=field.device)
     ws = _ws(field.device, workspace).get(workspace_bytes(dims) or 256)
-    opt = _options(radius, select, weights)
+    opt = _options(radius, select, weights, FLAG_GLOBAL_LORENZO if global_lorenzo else 0)
     nbytes = C.c_size_t(0)
-    st = L.lib().csz_compress(C.c_void_p(field.data_ptr()), len(dims), _dims_c(dims),
+    fn = L.lib().csz_compress_f64 if field.dtype == torch.float64 else L.lib().csz_compress
+    st = fn(C.c_void_p(field.data_ptr()), len(dims), _dims_c(dims),
                               EB_MODES[eb_mode] if isinstance(eb_mode, str) else int(eb_mode), float(eb),
                               C.byref(opt), C.c_void_p(ws.data_ptr()), ws.numel(), C.c_void_p(out.data_ptr()),
                               out.numel(), C.byref(nbytes), _stream_ptr(stream))
@@ -139,25 +145,34 @@ def decompress(archive: torch.Tensor, nbytes: int | None = None, out: torch.Tens
         raise ValueError("archive must be a uint8 CUDA tensor")
     if nbytes is None:
         nbytes = archive.numel()
-    if dims is None:
+    if dims is None or out is None:
         head = bytes(archive[:128].cpu().numpy().tobytes())
-        dims, _, _ = archive_info(head)
-    n = 1
-    for d in dims:
-        n *= int(d)
-    if out is None:
-        out = torch.empty(tuple(dims), dtype=torch.float32, device=archive.device)
+        if dims is None:
+            dims, _, _ = archive_info(head)
+        if out is None:
+            esz = elem_bytes(head)
+            out = torch.empty(tuple(dims), dtype=torch.float64 if esz == 8 else torch.float32,
+                              device=archive.device)
     ws = _ws(archive.device, workspace).get(workspace_bytes(dims) or 256)
-    st = L.lib().csz_decompress(C.c_void_p(archive.data_ptr()), int(nbytes), C.c_void_p(out.data_ptr()),
-                                out.numel(), C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream))
+    f64 = out.dtype == torch.float64
+    fn = L.lib().csz_decompress_f64 if f64 else L.lib().csz_decompress
+    st = fn(C.c_void_p(archive.data_ptr()), int(nbytes), C.c_void_p(out.data_ptr()), out.numel(),
+            C.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream))
     if raise_on_error:
-        _check(st, "csz_decompress")
+        _check(st, "csz_decompress_f64" if f64 else "csz_decompress")
     return out, st
+
+
+def elem_bytes(archive_host_head: bytes) -> int:
+    """4 (FP32) or 8 (double) for the field an archive holds; 0 if the header is invalid."""
+    buf = (C.c_uint8 * len(archive_host_head)).from_buffer_copy(archive_host_head)
+    return int(L.lib().csz_archive_elem_bytes(C.cast(buf, C.c_void_p), len(archive_host_head)))
 
 
 def compress_with_header(field: torch.Tensor, eb: float, eb_mode: str = "rel", radius: int = 512,
                          select: str = "exhaustive", weights: torch.Tensor | None = None,
-                         out: torch.Tensor | None = None, workspace: Workspace | None = None, stream=None):
+                         out: torch.Tensor | None = None, workspace: Workspace | None = None, stream=None,
+                         global_lorenzo: bool = False):
     """compress() that also returns the archive's 128-byte header as bytes (copied in
     the same synchronisation), for decompress_async.  Returns (archive, nbytes, header)."""
     if not (field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()):
@@ -166,7 +181,7 @@ def compress_with_header(field: torch.Tensor, eb: float, eb_mode: str = "rel", r
     if out is None:
         out = torch.empty(max_archive_bytes(dims) or 1, dtype=torch.uint8, device=field.device)
     ws = _ws(field.device, workspace).get(workspace_bytes(dims) or 256)
-    opt = _options(radius, select, weights)
+    opt = _options(radius, select, weights, FLAG_GLOBAL_LORENZO if global_lorenzo else 0)
     nbytes = C.c_size_t(0)
     hdr = (C.c_uint8 * 128)()
     st = L.lib().csz_compress_with_header(

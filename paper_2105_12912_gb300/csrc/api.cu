@@ -73,9 +73,16 @@ csz_status parse_header(const uint8_t* h, size_t bytes, Header& H, Geom& g, bool
   if (!make_geom(H.ndim, H.dims, g)) return CSZ_E_CORRUPT;
   for (int i = H.ndim; i < 3; i++)
     if (H.dims[i]) return CSZ_E_CORRUPT;
-  if (H.radius < 1 || H.radius > 512 || H.lanes != (uint32_t)kLanes || H.flags > 3) return CSZ_E_CORRUPT;
+  if (H.radius < 1 || H.radius > 512 || H.lanes != (uint32_t)kLanes || H.flags > 15) return CSZ_E_CORRUPT;
   if (H.nblk != g.nblk || H.n_rec != H.n_out + H.n_patch) return CSZ_E_CORRUPT;
-  if (!(H.eb_f > 0.0f) || !std::isfinite(2.0f * H.eb_f)) return CSZ_E_CORRUPT;
+  if (H.flags & kFlagF64) {
+    // double fields: the step follows from eb_d; they have no verbatim patches
+    const double stp = (2.0 * H.eb_d) * kStepShrink;
+    if (!(H.eb_d > 0.0) || !std::isfinite(H.eb_d) || !(stp > 0.0) || !std::isfinite(stp) || H.n_patch)
+      return CSZ_E_CORRUPT;
+  } else if (!(H.eb_f > 0.0f) || !std::isfinite(2.0f * H.eb_f)) {
+    return CSZ_E_CORRUPT;
+  }
   if (H.n_rec > 2 * g.nelem || (whole && H.payload > bytes) || (H.payload & 3)) return CSZ_E_CORRUPT;
   const uint64_t off_bb = kHdr + a8(H.nblk);
   const uint64_t off_rec = off_bb + a8(4 * H.nblk);
@@ -136,6 +143,14 @@ csz_status csz_trace_enable(int on) {
 }
 
 csz_status csz_trace_read(double* ms, uint64_t* launches, int reset) {
+  // launches whose events are complete but not yet folded (an asynchronous
+  // decompression has no synchronisation of its own to fold them at)
+  for (int k = 0; k < K_COUNT; k++)
+    if (g_trace.armed[k] && cudaEventQuery(g_trace.ev[k][1]) == cudaSuccess) {
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, g_trace.ev[k][0], g_trace.ev[k][1]) == cudaSuccess) g_trace.ms[k] += t;
+      g_trace.armed[k] = false;
+    }
   for (int k = 0; k < K_COUNT; k++) {
     if (ms) ms[k] = g_trace.ms[k];
     if (launches) launches[k] = g_trace.launches[k];
@@ -205,9 +220,10 @@ struct Analysis {
 // The compression pipeline on the caller's stream: value range or bound, Lorenzo
 // construction, books, per-block selection and encoding (or, with `an`, the analysis
 // of every block), then one synchronisation to read the device status and size.
-csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
+csz_status run_pipeline(const void* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
                         const csz_options* opt, void* d_ws, size_t ws_bytes, uint8_t* d_ar, size_t cap,
-                        size_t* h_bytes, const Analysis* an, void* stream, uint8_t* h_header = nullptr) {
+                        size_t* h_bytes, const Analysis* an, void* stream, uint8_t* h_header = nullptr,
+                        bool f64 = false) {
   Geom g;
   if (!d_field || !d_ws) return CSZ_E_ARG;
   if (!an && (!d_ar || !h_bytes)) return CSZ_E_ARG;
@@ -217,8 +233,12 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
   if (radius > 512 || select < 0 || select > SEL_LEARNED) return CSZ_E_ARG;
   if (select == SEL_LEARNED && !(opt && opt->selector_weights)) return CSZ_E_ARG;
   if (opt)
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < 3; i++)
       if (opt->reserved[i]) return CSZ_E_ARG;
+  const uint32_t oflags = opt ? opt->flags : 0u;
+  if (oflags & ~CSZ_FLAG_GLOBAL_LORENZO) return CSZ_E_ARG;
+  const bool global = (oflags & CSZ_FLAG_GLOBAL_LORENZO) != 0;
+  if (global && f64) return CSZ_E_ARG;  // the global reconstruction is FP32 only
   if (!(eb > 0.0) || !std::isfinite(eb) || (eb_mode != CSZ_EB_ABS && eb_mode != CSZ_EB_REL)) return CSZ_E_ARG;
   const Layout L = layout(g);
   if (ws_bytes < L.total) return CSZ_E_CAPACITY;
@@ -229,14 +249,18 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
   DevState* st = at<DevState>(d_ws, L.st);
 
   if (cudaMemsetAsync(d_ws, 0, L.zero_end, s) != cudaSuccess) return CSZ_E_CUDA;
-  cudaError_t e = eb_mode == CSZ_EB_REL ? launch_range(d_field, g.nelem, st, 1, eb, s)
-                                        : launch_abs_params(st, eb, s);
+  const float* x32 = f64 ? nullptr : static_cast<const float*>(d_field);
+  const double* x64 = f64 ? static_cast<const double*>(d_field) : nullptr;
+  cudaError_t e = f64 ? launch_range_d(x64, g.nelem, st, eb_mode == CSZ_EB_REL ? 1 : 0, eb, s)
+                      : (eb_mode == CSZ_EB_REL ? launch_range(x32, g.nelem, st, 1, eb, s)
+                                               : launch_abs_params(st, eb, s));
   if (e != cudaSuccess) return CSZ_E_CUDA;
 
   ConstructTask task;
   memset(&task, 0, sizeof(task));
   ConstructArgs& ca = task.a;
-  ca.x = d_field;
+  ca.x = x32;
+  ca.x64 = x64;
   ca.g = g;
   ca.st = st;
   ca.radius = radius;
@@ -250,6 +274,7 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
   ca.block_runs = at<uint16_t>(d_ws, L.runs);
   ca.spin_limit = g_spin_limit;
   ca.all_runs = (select == SEL_RLE || select == SEL_RLE_HUFF) ? 1 : 0;
+  ca.global = global ? 1 : 0;
   prepare_construct_task(task);
   if (launch_construct(task, &st->ticket_construct, s) != cudaSuccess) return CSZ_E_CUDA;
 
@@ -266,7 +291,7 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
   if (!an) {
     // a fourth CTA beside the book builders scans the record counts; the encode
     // CTAs then write each block's records
-    ra.x = d_field;
+    ra.x = x32;  // patch values (FP32 fields only: double fields have no patches)
     ra.counts = ca.counts;
     ra.masks = ca.masks;
     ra.deltas = ca.deltas;
@@ -309,6 +334,8 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
   ea.rec = ra;
   FinalizeArgs& fa = ea.fin;
   fa.st = st;
+  fa.f64 = f64 ? 1 : 0;
+  fa.global = global ? 1 : 0;
   fa.ar = d_ar;
   fa.cap = cap;
   fa.ndim = ndim;
@@ -338,17 +365,22 @@ csz_status run_pipeline(const float* d_field, int ndim, const uint64_t* dims, in
 // Decode set-up from a parsed header h (read back from the device, or a host copy
 // the caller kept: then check_hdr makes the device compare it with the archive) and
 // the decode launches.  *st_out: the decompression's device state.
-csz_status enqueue_decode(const uint8_t* d_ar, size_t bytes, const uint8_t* h, bool check_hdr, float* d_out,
-                          uint64_t out_cap, void* d_ws, size_t ws_bytes, cudaStream_t s, DevState** st_out) {
+csz_status enqueue_decode(const uint8_t* d_ar, size_t bytes, const uint8_t* h, bool check_hdr, void* d_out,
+                          uint64_t out_cap, void* d_ws, size_t ws_bytes, cudaStream_t s, DevState** st_out,
+                          bool f64 = false) {
   Header H;
   Geom g;
   csz_status r = parse_header(h, bytes, H, g);
   if (r != CSZ_OK) return r;
+  if (((H.flags & kFlagF64) != 0) != f64) return CSZ_E_ARG;  // the output's type is not the field's
+  const bool global = (H.flags & kFlagGlobal) != 0;
+  if (global && f64) return CSZ_E_CORRUPT;  // no such archive is written
   if (out_cap < g.nelem) return CSZ_E_CAPACITY;
   const Layout L = layout(g);
   if (ws_bytes < L.dec_total) return CSZ_E_CAPACITY;
   DevState* st = at<DevState>(d_ws, L.st);
-  if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return CSZ_E_CUDA;
+  // the device state and the set-up's look-back states (adjacent)
+  if (cudaMemsetAsync(st, 0, L.hist_code - L.st, s) != cudaSuccess) return CSZ_E_CUDA;
   DecodeArgs da;
   memset(&da, 0, sizeof(da));
   da.g = g;
@@ -373,7 +405,22 @@ csz_status enqueue_decode(const uint8_t* d_ar, size_t bytes, const uint8_t* h, b
   da.runv = da.codes;  // run values of an RLE+Huffman block wait in its own code slots
   da.runl = at<uint16_t>(d_ws, L.runl);
   da.runblk = at<uint32_t>(d_ws, L.runblk);
-  da.out = d_out;
+  da.slowblk = at<uint32_t>(d_ws, L.slowblk);
+  da.prep_lb = at<uint64_t>(d_ws, L.prep_lb);
+  da.fuse = global ? 0 : 1;
+  da.f64 = f64 ? 1 : 0;
+  if (global) {
+    // the x pass's look-back states, one per 4096 elements (at most one per codec block)
+    da.global = 1;
+    da.scan_state = at<uint64_t>(d_ws, L.lb_e);
+    if (cudaMemsetAsync(da.scan_state, 0, 8ull * ((g.nelem + 4095) / 4096), s) != cudaSuccess) return CSZ_E_CUDA;
+  }
+  if (f64) {
+    da.out64 = static_cast<double*>(d_out);
+    da.step_d = (2.0 * H.eb_d) * kStepShrink;
+  } else {
+    da.out = static_cast<float*>(d_out);
+  }
   da.check_hdr = check_hdr ? 1 : 0;
   memcpy(da.hdr, h, kHdr);
   if (launch_decode(da, s) != cudaSuccess) return CSZ_E_CUDA;
@@ -434,6 +481,39 @@ csz_status csz_decompress(const uint8_t* d_ar, size_t bytes, float* d_out, uint6
   if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
   trace_collect();
   return fold(hs.status);
+}
+
+csz_status csz_compress_f64(const double* d_field, int ndim, const uint64_t* dims, int eb_mode, double eb,
+                            const csz_options* opt, void* d_ws, size_t ws_bytes, uint8_t* d_ar, size_t cap,
+                            size_t* h_bytes, void* stream) {
+  return run_pipeline(d_field, ndim, dims, eb_mode, eb, opt, d_ws, ws_bytes, d_ar, cap, h_bytes, nullptr, stream,
+                      nullptr, true);
+}
+
+csz_status csz_decompress_f64(const uint8_t* d_ar, size_t bytes, double* d_out, uint64_t out_cap, void* d_ws,
+                              size_t ws_bytes, void* stream) {
+  if (!d_ar || !d_out || !d_ws) return CSZ_E_ARG;
+  if (bytes < (size_t)kHdr) return CSZ_E_CORRUPT;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t h[kHdr];
+  if (cudaMemcpyAsync(h, d_ar, kHdr, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  DevState* st = nullptr;
+  const csz_status r = enqueue_decode(d_ar, bytes, h, false, d_out, out_cap, d_ws, ws_bytes, s, &st, true);
+  if (r != CSZ_OK) return r;
+  DevState hs;
+  if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CSZ_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
+  trace_collect();
+  return fold(hs.status);
+}
+
+int csz_archive_elem_bytes(const uint8_t* h, size_t bytes) {
+  if (!h) return 0;
+  Header H;
+  Geom g;
+  if (parse_header(h, bytes, H, g, false) != CSZ_OK) return 0;
+  return (H.flags & kFlagF64) ? 8 : 4;
 }
 
 csz_status csz_decompress_async(const uint8_t* d_ar, size_t bytes, const uint8_t* h_header, float* d_out,

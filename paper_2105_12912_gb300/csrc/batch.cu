@@ -184,9 +184,11 @@ csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_opti
   const int select = opt ? (int)opt->select : SEL_EXHAUSTIVE;
   if (radius > 512 || select < 0 || select > SEL_LEARNED) return CSZ_E_ARG;
   if (select == SEL_LEARNED && !(opt && opt->selector_weights)) return CSZ_E_ARG;
-  if (opt)
-    for (int i = 0; i < 4; i++)
+  if (opt) {
+    for (int i = 0; i < 3; i++)
       if (opt->reserved[i]) return CSZ_E_ARG;
+    if (opt->flags) return CSZ_E_ARG;  // batches compress with chunked Lorenzo only
+  }
   const BatchLayout B = batch_layout(gs);
   if (ws_bytes < B.total) return CSZ_E_CAPACITY;
   for (int f = 0; f < nfields; f++) {

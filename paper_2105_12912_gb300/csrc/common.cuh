@@ -34,6 +34,8 @@ constexpr int kLutBits = 12;
 constexpr uint32_t kSpinLimit = 1u << 20;
 
 enum : int { CODEC_HUFF = 0, CODEC_RLE = 1, CODEC_RLE_HUFF = 2 };
+constexpr uint32_t kFlagF64 = 4u;     // header flag: the field is double precision
+constexpr uint32_t kFlagGlobal = 8u;  // header flag: global (unchunked) Lorenzo prediction
 
 // learned selector: MLP 8 -> 32 -> 32 -> 3 with ReLU, parameters packed as
 // W1[32][8] b1[32] W2[32][32] b2[32] W3[3][32] b3[3]
@@ -45,8 +47,9 @@ static_assert(kMlpParams == 1443, "MLP parameter count");
 // the runner-up within this many log2 units (about 2%) of the best prediction sends
 // the block to exact sizes
 constexpr float kMlpMargin = 0.028569152f;
-// RLE roughness feature (Sec. III-B madogram with binary variance): code changes at
-// the distances kMadoD0 + kMadoStep * k, k < kMadoN (every 25th distance of 1..200)
+// RLE roughness feature (Sec. III-B madogram with binary variance): position j is
+// paired with j + kMadoD0 + kMadoStep * (j mod kMadoN), i.e. the distances 1, 26,
+// ..., 176 (every 25th of 1..200), each on every 8th position
 constexpr uint32_t kMadoD0 = 1, kMadoStep = 25, kMadoN = 8;
 enum : int { SEL_HUFF = 0, SEL_RLE = 1, SEL_RLE_HUFF = 2, SEL_HEURISTIC = 3, SEL_EXHAUSTIVE = 4, SEL_LEARNED = 5 };
 
@@ -84,6 +87,13 @@ __host__ __device__ inline void block_box(const Geom& g, uint32_t b, uint32_t or
   }
 }
 
+// codec block b has the full block extent on every axis (not cut by the field's edge)
+__host__ __device__ inline bool block_is_full(const Geom& g, uint32_t b) {
+  uint32_t org[3], w[3];
+  block_box(g, b, org, w);
+  return w[0] == g.blk[0] && w[1] == g.blk[1] && w[2] == g.blk[2];
+}
+
 // Values the device derives once per compression (error bound, range, counters).
 struct DevState {
   double eb_d;
@@ -102,6 +112,10 @@ struct DevState {
   unsigned long long payload;
   unsigned long long total;
   float vmin, vmax;
+  uint32_t n_slow;        // decompression: blocks the reconstruction kernel takes (listed)
+  // double-precision fields: value range as order keys, quantization step and inverse
+  unsigned long long range64_lo_inv, range64_hi;
+  double step_d, rstep_d;
 };
 
 // ---------------------------------------------------------------------------------
@@ -284,6 +298,51 @@ __device__ __forceinline__ bool prequant_fast(float x, float eb_f, float ebx2_f,
   k = __float2int_rn(v);
   const float s = __fsub_rn(x, __fmul_rn(__int2float_rn(k), ebx2_f));
   return (fabsf(v) < 8388608.0f) & (fabsf(s) < eb_f);
+}
+
+// ---------------------------------------------------------------------------------
+// double-precision fields: the same prequantization with the step
+// step = fl64(2 eb (1 - 2^-24)); |k| < 2^27 keeps the rounding of fl64(k * step)
+// (at most 2^-25 eb) inside the margin the shrink leaves, so the nearest integer, or
+// its neighbour when the product x * (1 / step) rounds across a half point, always
+// meets the bound and no value needs a verbatim patch
+// ---------------------------------------------------------------------------------
+constexpr double kStepShrink = 1.0 - 0x1p-24;
+constexpr double kMaxK64 = 134217728.0;  // 2^27
+
+__device__ __forceinline__ bool exceeds_exact_d(double x, double y, double eb) {
+  const double s = __dsub_rn(x, y);
+  if (fabs(s) < eb) return false;
+  if (fabs(s) > eb) return true;
+  const double bb = __dsub_rn(s, x);
+  const double e = __dadd_rn(__dsub_rn(x, __dsub_rn(s, bb)), __dsub_rn(-y, bb));
+  return s > 0.0 ? e > 0.0 : e < 0.0;
+}
+
+// Returns ERR_* bits (0 on success); no patches for doubles.
+__device__ __forceinline__ uint32_t prequant_d(double x, double eb_d, double step, double rstep, int32_t& k) {
+  k = 0;
+  const double v = __dmul_rn(x, rstep);
+  if (!(fabs(v) < kMaxK64)) return isfinite(x) ? ERR_RANGE : ERR_NONFINITE;
+  const int32_t k0 = __double2int_rn(v);
+  const double x0 = __dmul_rn((double)k0, step);
+  if (!exceeds_exact_d(x, x0, eb_d)) {
+    k = k0;
+    return 0;
+  }
+  const int32_t k1 = k0 + (x > x0 ? 1 : -1);
+  if (!exceeds_exact_d(x, __dmul_rn((double)k1, step), eb_d)) {
+    k = k1;
+    return 0;
+  }
+  return ERR_RANGE;  // unreachable by the step's margin
+}
+
+__device__ __forceinline__ bool prequant_fast_d(double x, double eb_d, double step, double rstep, int32_t& k) {
+  const double v = __dmul_rn(x, rstep);
+  k = __double2int_rn(v);
+  const double s = __dsub_rn(x, __dmul_rn((double)k, step));
+  return (fabs(v) < kMaxK64) & (fabs(s) < eb_d);
 }
 
 // Binary logarithm in Q16 by bit-by-bit squaring of the mantissa (integer only).

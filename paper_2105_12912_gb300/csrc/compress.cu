@@ -48,6 +48,98 @@ __global__ void abs_params_kernel(DevState* st, double eb) {
   if (threadIdx.x == 0 && blockIdx.x == 0) derive_eb(st, 0, eb, 0.0f, 0.0f);
 }
 
+// Double-precision fields: eb_d as above (from the double range), the quantization
+// step fl64(2 eb_d (1 - 2^-24)) and its inverse; eb_f is the largest float <= eb_d
+// (informational, in the header).  Degenerate bounds -> ERR_ARG.
+__device__ void derive_eb_d(DevState* st, int mode, double eb, double vmin, double vmax) {
+  const double d = mode == 0 ? eb : __dmul_rn(eb, __dsub_rn(vmax, vmin));
+  const double stp = __dmul_rn(__dmul_rn(2.0, d), kStepShrink);
+  const double r = __ddiv_rn(1.0, stp);
+  st->eb_d = d;
+  st->eb_f = __double2float_rd(d);
+  st->step_d = stp;
+  st->rstep_d = r;
+  if (!(d > 0.0) || !isfinite(d) || !(stp > 0.0) || !isfinite(stp) || !(r > 0.0) || !isfinite(r))
+    atomicOr(&st->status, ERR_ARG);
+}
+
+__global__ void abs_params_d_kernel(DevState* st, double eb) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) derive_eb_d(st, 0, eb, 0.0, 0.0);
+}
+
+__device__ __forceinline__ unsigned long long order_key_d(double f) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(f);
+  return (b >> 63) ? ~b : (b | (1ull << 63));
+}
+__device__ __forceinline__ double key_to_double(unsigned long long k) {
+  return __longlong_as_double((long long)((k >> 63) ? (k & ~(1ull << 63)) : ~k));
+}
+
+// Min / max of a double field (grid-stride, 16-byte loads); the last CTA derives the
+// bound and the step.
+__global__ __launch_bounds__(256) void range_d_kernel(const double* __restrict__ x, uint64_t n, DevState* st,
+                                                      int mode, double eb) {
+  __shared__ unsigned long long s_red[2][33];
+  __shared__ bool s_last;
+  unsigned long long lo_inv = 0, hi = 0;
+  uint32_t bad = 0;
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  const bool vec = (((uintptr_t)x) & 15) == 0;
+  const uint64_t nvec = vec ? n / 2 : 0;
+  const double2* x2 = reinterpret_cast<const double2*>(x);
+  auto take = [&](double a) {
+    if (!isfinite(a)) {
+      bad = 1;
+    } else {
+      const unsigned long long key = order_key_d(a);
+      lo_inv = max(lo_inv, ~key);
+      hi = max(hi, key);
+    }
+  };
+  for (uint64_t i = tid; i < nvec; i += nth) {
+    const double2 v = __ldcs(&x2[i]);
+    take(v.x);
+    take(v.y);
+  }
+  for (uint64_t i = nvec * 2 + tid; i < n; i += nth) take(x[i]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    lo_inv = max(lo_inv, __shfl_xor_sync(~0u, lo_inv, o));
+    hi = max(hi, __shfl_xor_sync(~0u, hi, o));
+  }
+  bad = __any_sync(~0u, bad);
+  if (lane == 0) {
+    s_red[0][wid] = lo_inv;
+    s_red[1][wid] = hi;
+  }
+  if (bad && lane == 0) atomicOr(&st->status, ERR_NONFINITE);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      a = max(a, s_red[0][w]);
+      b = max(b, s_red[1][w]);
+    }
+    atomicMax(&st->range64_lo_inv, a);
+    atomicMax(&st->range64_hi, b);
+    __threadfence();
+    s_last = atomicAdd(&st->range_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long a = atomicAdd(&st->range64_lo_inv, 0ull);
+    const unsigned long long b = atomicAdd(&st->range64_hi, 0ull);
+    if (b == 0) {  // nothing finite was seen
+      atomicOr(&st->status, ERR_NONFINITE);
+      return;
+    }
+    derive_eb_d(st, mode, eb, key_to_double(~a), key_to_double(b));
+  }
+}
+
 // Grid-stride min/max with float4 loads; non-finite values are flagged.  The last CTA
 // to finish derives the error bound.
 __device__ __forceinline__ void range_body(const float* __restrict__ x, uint64_t n, DevState* st, int mode, double eb,
@@ -449,7 +541,8 @@ __device__ void finalize_body(const FinalizeArgs& a) {
   const int tid = threadIdx.x;
   if (tid == 0) {
     const uint64_t n_rec = st->n_rec, payload = st->payload;
-    const uint32_t flags = (st->ncodec[CODEC_HUFF] ? 1u : 0u) | (st->ncodec[CODEC_RLE_HUFF] ? 2u : 0u);
+    const uint32_t flags = (st->ncodec[CODEC_HUFF] ? 1u : 0u) | (st->ncodec[CODEC_RLE_HUFF] ? 2u : 0u) |
+                           (a.f64 ? kFlagF64 : 0u) | (a.global ? kFlagGlobal : 0u);
     const uint64_t off_pay = a.off_rec + 8 * n_rec;
     const uint64_t off_books = off_pay + ((payload + 7) & ~7ull);
     const uint64_t total = off_books + ((flags & 1) ? kNsymCode : 0) + ((flags & 2) ? kNsymCode + kNsymLen : 0);
@@ -544,6 +637,8 @@ __device__ __forceinline__ uint32_t units_from_partials(const uint32_t* part) {
   for (int wv = 0; wv < kEncThreads / 32; wv++) bits += part[32 * wv + lane];
   return warp_sum(ihs_lane_units(bits));
 }
+
+static_assert(kEncThreads % kMadoN == 0, "madogram distances by thread");
 
 // Selection and encoding of codec block b of one field (all threads of the CTA).
 __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
@@ -705,7 +800,7 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
     __syncthreads();
     // block statistics in one pass and one reduction: entropy sum, |delta| sum, top
     // count and largest in-range |delta|, and (selector) the madogram's code changes
-    // at the distances 1, 26, ..., 176
+    // on the pairs (j, j + 1 + 25 (j mod 8))
     uint64_t S_ = 0, absd = 0;
     uint32_t f1 = 0, maxd = 0, mism = 0;
     for (int c = tid; c < kNsymCode; c += kEncThreads) {
@@ -722,11 +817,9 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
     }
     const bool want_mado = !(sel == SEL_HEURISTIC && !analyze);
     if (want_mado) {
-#pragma unroll 1
-      for (uint32_t k = 0; k < kMadoN; k++) {
-        const uint32_t d = kMadoD0 + kMadoStep * k;
-        for (uint32_t j = tid; j + d < m; j += kEncThreads) mism += s_c[j] != s_c[j + d];
-      }
+      // kEncThreads is a multiple of kMadoN, so a thread's distance is fixed
+      const uint32_t d = kMadoD0 + kMadoStep * (tid % kMadoN);
+      for (uint32_t j = tid; j + d < m; j += kEncThreads) mism += s_c[j] != s_c[j + d];
     }
     S_ = warp_sum(S_);
     absd = warp_sum(absd);
@@ -772,10 +865,11 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
       if (tid == 0) {
         const uint32_t zero = s_hist[r];
         const uint32_t outl = s_hist[0];
+        // pairs inside the block: positions j < m - d for each residue class j mod 8
         uint32_t pairs = 0;
         for (uint32_t k = 0; k < kMadoN; k++) {
           const uint32_t d = kMadoD0 + kMadoStep * k;
-          pairs += m > d ? m - d : 0u;
+          if (m > d + k) pairs += (m - d - k + kMadoN - 1) / kMadoN;
         }
         const float fm = (float)m;
         s_feat[0] = (float)zero / fm;
@@ -955,6 +1049,14 @@ cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, dou
   const uint32_t grid = range_ctas(n);
   trace_begin(K_RANGE, s);
   range_kernel<<<grid, 256, 0, s>>>(x, n, st, mode, eb);
+  trace_end(K_RANGE, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range_d(const double* x, uint64_t n, DevState* st, int mode, double eb, cudaStream_t s) {
+  trace_begin(K_RANGE, s);
+  if (mode == 0) abs_params_d_kernel<<<1, 32, 0, s>>>(st, eb);
+  else range_d_kernel<<<range_ctas(2 * n), 256, 0, s>>>(x, n, st, mode, eb);
   trace_end(K_RANGE, s);
   return cudaGetLastError();
 }

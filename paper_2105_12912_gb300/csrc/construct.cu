@@ -27,7 +27,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPer = kSlots / kThreads;  // 16 elements per thread
-constexpr uint32_t kTileBytes = kSlots * 4;
 constexpr int kHlShared = 256;  // run lengths counted in shared memory; longer runs go to the field's
                                 // histogram directly (they are rare: one per long constant stretch)
 
@@ -46,9 +45,53 @@ struct Chunk<3> {
   static constexpr uint32_t z = 8, y = 8, x = 8;
 };
 
+// ---- prequantization by element type (Sec. IV-A1; doubles: step 2eb (1 - 2^-24)) ---
+template <typename T>
+struct Pq;
+template <>
+struct Pq<float> {
+  float eb_f, ebx2_f, ebx2_r;
+  __device__ explicit Pq(const DevState* st) : eb_f(st->eb_f), ebx2_f(st->ebx2_f), ebx2_r(st->ebx2_r) {}
+  __device__ __forceinline__ bool fast(float x, int32_t& k) const { return prequant_fast(x, eb_f, ebx2_f, ebx2_r, k); }
+  __device__ __forceinline__ uint32_t full(float x, int32_t& k, bool& patch) const {
+    return prequant(x, eb_f, ebx2_f, ebx2_r, k, patch);
+  }
+};
+template <>
+struct Pq<double> {
+  double eb_d, step, rstep;
+  __device__ explicit Pq(const DevState* st) : eb_d(st->eb_d), step(st->step_d), rstep(st->rstep_d) {}
+  __device__ __forceinline__ bool fast(double x, int32_t& k) const { return prequant_fast_d(x, eb_d, step, rstep, k); }
+  __device__ __forceinline__ uint32_t full(double x, int32_t& k, bool& patch) const {
+    patch = false;
+    return prequant_d(x, eb_d, step, rstep, k);
+  }
+};
+
+// 16 consecutive elements of a shared-memory tile (16-byte loads)
+__device__ __forceinline__ void load16(const float* p, float (&f)[16]) {
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const float4 v = reinterpret_cast<const float4*>(p)[i];
+    f[4 * i] = v.x;
+    f[4 * i + 1] = v.y;
+    f[4 * i + 2] = v.z;
+    f[4 * i + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load16(const double* p, double (&f)[16]) {
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const double2 v = reinterpret_cast<const double2*>(p)[i];
+    f[2 * i] = v.x;
+    f[2 * i + 1] = v.y;
+  }
+}
+
 // ---- shared memory -----------------------------------------------------------------
-struct Smem {
-  float in[2][kSlots];          // TMA destinations (box layout); in 3-D the current
+template <typename T, uint32_t NIN = kSlots>
+struct SmemT {
+  T in[2][NIN];                 // TMA destinations (box layout); in 3-D the current
                                 // one then carries k for the y difference
   uint16_t c[kSlots];           // codes of the current tile (dense order)
   uint32_t hc[kNsymCode];       // code histogram (per CTA, current field)
@@ -92,12 +135,13 @@ __device__ __forceinline__ void tma_load(int rank, void* dst, const CUtensorMap*
 
 // Start fetching tile b of task T into buffer `buf` (thread 0 only).  The buffer was
 // last touched by ordinary loads and stores, hence the proxy fence.
-__device__ void issue_tile(const ConstructTask* T, const uint32_t* org, float* buf, unsigned long long* bar) {
+template <typename E>
+__device__ void issue_tile(const ConstructTask* T, const uint32_t* org, E* buf, unsigned long long* bar) {
   const Geom& g = T->a.g;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(bar, kTileBytes);
+  mbar_expect_tx(bar, (uint32_t)(kSlots * sizeof(E)));
   if (g.ndim == 1) {
-    // a 1-D box holds at most 256 elements: 16 copies of 1 KB
+    // a 1-D box holds at most 256 elements: 16 copies
     for (int i = 0; i < kSlots / 256; i++)
       tma_load(1, buf + 256 * i, &T->tmap, (int32_t)(org[2] + 256 * i), 0, 0, bar);
   } else if (g.ndim == 2) {
@@ -107,8 +151,17 @@ __device__ void issue_tile(const ConstructTask* T, const uint32_t* org, float* b
   }
 }
 
+template <typename E>
+__device__ __forceinline__ const E* field_ptr(const ConstructArgs& A);
+template <>
+__device__ __forceinline__ const float* field_ptr<float>(const ConstructArgs& A) { return A.x; }
+template <>
+__device__ __forceinline__ const double* field_ptr<double>(const ConstructArgs& A) { return A.x64; }
+
 // Thread-loaded tile (fields TMA cannot describe): box layout, zeros outside.
-__device__ void load_tile_threads(const ConstructArgs& A, uint32_t b, float* buf) {
+template <typename E>
+__device__ void load_tile_threads(const ConstructArgs& A, uint32_t b, E* buf) {
+  const E* xs = field_ptr<E>(A);
   const Geom& g = A.g;
   uint32_t org[3], w[3];
   block_box(g, b, org, w);
@@ -128,9 +181,8 @@ __device__ void load_tile_threads(const ConstructArgs& A, uint32_t b, float* buf
       yy = (p >> 4) & 15;
       xx = p & 15;
     }
-    float v = 0.0f;
-    if (zz < w[0] && yy < w[1] && xx < w[2])
-      v = A.x[((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx];
+    E v = E(0);
+    if (zz < w[0] && yy < w[1] && xx < w[2]) v = xs[((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx];
     buf[p] = v;
   }
 }
@@ -145,11 +197,11 @@ __device__ __forceinline__ void flush_hist(const uint32_t* h, int n, uint32_t* g
 // ---- edge blocks (not inlined: keeps the full-block paths compact in the
 // instruction cache): prequantize into registers in dense order, stage k, residuals
 // from the staged neighbours.  Returns error bits.
-template <int ND>
-__device__ __noinline__ uint32_t edge_codes(const ConstructArgs& A, uint32_t b, Smem& S, float* in,
+template <int ND, typename E>
+__device__ __noinline__ uint32_t edge_codes(const ConstructArgs& A, uint32_t b, SmemT<E>& S, E* in,
                                             const uint32_t* w, uint32_t m, int32_t* dglob) {
   const int tid = threadIdx.x, lane = tid & 31;
-  const float eb_f = A.st->eb_f, ebx2_f = A.st->ebx2_f, ebx2_r = A.st->ebx2_r;
+  const Pq<E> pq(A.st);
   const int32_t r = (int32_t)A.radius;
   int32_t* s_k = reinterpret_cast<int32_t*>(in);
   uint32_t err = 0;
@@ -178,7 +230,7 @@ __device__ __noinline__ uint32_t edge_codes(const ConstructArgs& A, uint32_t b, 
       }
       const uint32_t box = ND == 1 ? xx : (ND == 2 ? yy * 64 + xx : (zz * 16 + yy) * 16 + xx);
       bool p;
-      err |= prequant(in[box], eb_f, ebx2_f, ebx2_r, kv[i], p);
+      err |= pq.full(in[box], kv[i], p);
       pm |= (uint32_t)p << i;
     }
   }
@@ -236,180 +288,12 @@ __device__ __noinline__ uint32_t edge_codes(const ConstructArgs& A, uint32_t b, 
     return err;
 }
 
-// ---- one tile ------------------------------------------------------------------------
-// Codes, records and histogram updates of codec block b (origin box[0..2], extent
-// box[3..5]) from the box in `in` (which this call overwrites with k and outlier
-// deltas).  Thread 0 adds the tile's record and patch counts to n_rec_acc /
-// n_patch_acc.
-template <int ND>
-__device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t* box, Smem& S, float* in,
-                             uint32_t& n_rec_acc, uint32_t& n_patch_acc) {
+// ---- the tile's tail: run heads at word boundaries (full tiles), counts from the
+// bit words, bulk copies of codes and masks, run histograms of run-eligible blocks
+template <typename E, uint32_t NIN>
+__device__ void tile_tail(const ConstructArgs& A, uint32_t b, SmemT<E, NIN>& S, uint32_t m, bool full, uint32_t err,
+                          uint32_t& n_rec_acc, uint32_t& n_patch_acc) {
   const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t w[3] = {box[3], box[4], box[5]};
-  const uint32_t m = w[0] * w[1] * w[2];
-  const float eb_f = A.st->eb_f, ebx2_f = A.st->ebx2_f, ebx2_r = A.st->ebx2_r;
-  const int32_t r = (int32_t)A.radius;
-  const Geom& g = A.g;
-  const bool full = w[0] == g.blk[0] && w[1] == g.blk[1] && w[2] == g.blk[2];
-  int32_t* s_k = reinterpret_cast<int32_t*>(in);
-  int32_t* dglob = A.deltas + (uint64_t)b * kSlots;  // outlier residuals of this block, by slot
-  uint32_t err = 0;
-
-  // Postquantization of one warp step over the 32 consecutive slots of word j >> 5:
-  // code, outlier delta, the word's outlier / patch / run-head bits, and the code
-  // histogram (one add for the whole step when its 32 codes agree, as in zero
-  // regions).  Head bit 0 compares with the previous word, written by another warp:
-  // it is left clear here and set after the tile.
-  auto post = [&](int32_t delta, uint32_t j, bool patch_step, bool patch_bit) {
-    const uint32_t u = (uint32_t)(delta + r);
-    const uint32_t q = u - 1u < (uint32_t)(2 * r - 1) ? u : 0u;  // |delta| < r
-    S.c[j] = (uint16_t)q;
-    if (q == 0) dglob[j] = delta;
-    const uint32_t left = __shfl_up_sync(~0u, q, 1);
-    const uint32_t hd = __ballot_sync(~0u, lane != 0 && q != left);
-    const uint32_t ob = __ballot_sync(~0u, q == 0);
-    const uint32_t pb = patch_step ? __ballot_sync(~0u, patch_bit) : 0u;
-    if (hd == 0) {
-      if (lane == 0) atomicAdd(&S.hc[q], 32u);
-    } else {
-      atomicAdd(&S.hc[q], 1u);
-    }
-    if (lane == 0) {
-      S.head[j >> 5] = hd;
-      S.outl[j >> 5] = ob;
-      S.patch[j >> 5] = pb;
-    }
-  };
-
-  // ---- prequantization, Lorenzo residual (Sec. IV-B2), postquantization ----------
-  // The residual is the mixed difference (1 - S_x)(1 - S_y)(1 - S_z) k, each shift
-  // reading zero outside the chunk; that expansion is the paper's 1/2/3-D predictor.
-  if (full) {
-    if (ND == 1) {
-      // thread t: 16 consecutive elements (a warp covers two whole 256-chunks)
-      int32_t k[16];
-      uint32_t pm = 0, slow = 0;
-      const float4* in4 = reinterpret_cast<const float4*>(in) + 4 * tid;
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const float4 v = in4[i];
-        const float f[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int c = 0; c < 4; c++)
-          slow |= (uint32_t)!prequant_fast(f[c], eb_f, ebx2_f, ebx2_r, k[4 * i + c]) << (4 * i + c);
-      }
-      if (__any_sync(~0u, slow != 0)) {
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-          if ((slow >> i) & 1u) {
-            bool p;
-            err |= prequant(in[16 * tid + i], eb_f, ebx2_f, ebx2_r, k[i], p);
-            pm |= (uint32_t)p << i;
-          }
-        }
-      }
-      const int32_t prev = __shfl_up_sync(~0u, k[15], 1);
-      uint32_t om = 0, hm = 0, qprev = 0, qfirst = 0;
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const uint32_t j = 16 * tid + i;
-        const int32_t left = i ? k[i - 1] : prev;
-        const int32_t delta = (j & 255) ? k[i] - left : k[i];
-        const uint32_t u = (uint32_t)(delta + r);
-        const uint32_t q = u - 1u < (uint32_t)(2 * r - 1) ? u : 0u;  // |delta| < r
-        S.c[j] = (uint16_t)q;
-        if (q == 0) dglob[j] = delta;
-        atomicAdd(&S.hc[q], 1u);
-        om |= (uint32_t)(q == 0) << i;
-        if (i == 0) qfirst = q;
-        else hm |= (uint32_t)(q != qprev) << i;
-        qprev = q;
-      }
-      // the first slot's left neighbour is the last slot of the lane below (lane 0:
-      // another warp's, set after the tile)
-      const uint32_t qbelow = __shfl_up_sync(~0u, qprev, 1);
-      if (lane != 0 && qfirst != qbelow) hm |= 1u;
-      const uint32_t om2 = __shfl_down_sync(~0u, om, 1), pm2 = __shfl_down_sync(~0u, pm, 1),
-                     hm2 = __shfl_down_sync(~0u, hm, 1);
-      if ((lane & 1) == 0) {
-        S.outl[tid >> 1] = om | (om2 << 16);
-        S.patch[tid >> 1] = pm | (pm2 << 16);
-        S.head[tid >> 1] = hm | (hm2 << 16);
-      }
-    } else if (ND == 2) {
-      // thread t: column xx = t & 63 of the 16-row chunk band t >> 6
-      const uint32_t xx = tid & 63, ry = tid >> 6;
-      int32_t k[16];
-      uint32_t pm = 0, slow = 0;
-#pragma unroll
-      for (int i = 0; i < 16; i++)
-        slow |= (uint32_t)!prequant_fast(in[(16 * ry + i) * 64 + xx], eb_f, ebx2_f, ebx2_r, k[i]) << i;
-      if (__any_sync(~0u, slow != 0)) {
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-          if ((slow >> i) & 1u) {
-            bool p;
-            err |= prequant(in[(16 * ry + i) * 64 + xx], eb_f, ebx2_f, ebx2_r, k[i], p);
-            pm |= (uint32_t)p << i;
-          }
-        }
-      }
-      const bool anyp = __any_sync(~0u, pm != 0);
-#pragma unroll
-      for (int i = 15; i > 0; i--) k[i] -= k[i - 1];  // y difference within the chunk band
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const int32_t left = __shfl_up_sync(~0u, k[i], 1);
-        const int32_t delta = (xx & 15) ? k[i] - left : k[i];  // x difference
-        const uint32_t j = (16 * ry + i) * 64 + xx;
-        post(delta, j, anyp, (pm >> i) & 1u);
-      }
-    } else {
-      // thread t: z column of (xx, yy) = (t & 15, t >> 4); z and x differences in
-      // registers and shuffles, the y difference through shared memory
-      const uint32_t xx = tid & 15, yy = tid >> 4;
-      int32_t k[16];
-      uint32_t pm = 0, slow = 0;
-#pragma unroll
-      for (int i = 0; i < 16; i++)
-        slow |= (uint32_t)!prequant_fast(in[(i * 16 + yy) * 16 + xx], eb_f, ebx2_f, ebx2_r, k[i]) << i;
-      if (__any_sync(~0u, slow != 0)) {
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-          if ((slow >> i) & 1u) {
-            bool p;
-            err |= prequant(in[(i * 16 + yy) * 16 + xx], eb_f, ebx2_f, ebx2_r, k[i], p);
-            pm |= (uint32_t)p << i;
-          }
-        }
-      }
-#pragma unroll
-      for (int i = 15; i > 0; i--)
-        if (i & 7) k[i] -= k[i - 1];  // z difference within 8-chunks
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const int32_t left = __shfl_up_sync(~0u, k[i], 1);
-        if (xx & 7) k[i] -= left;  // x difference
-      }
-      const bool anyp = __any_sync(~0u, pm != 0);
-      __syncthreads();  // every thread has read the box: it carries k from here
-#pragma unroll
-      for (int i = 0; i < 16; i++) s_k[(i * 16 + yy) * 16 + xx] = k[i];
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const uint32_t j = (i * 16 + yy) * 16 + xx;
-        const int32_t below = (yy & 7) ? s_k[(i * 16 + yy - 1) * 16 + xx] : 0;
-        post(k[i] - below, j, anyp, (pm >> i) & 1u);
-      }
-    }
-    __syncthreads();
-  } else {
-    err |= edge_codes<ND>(A, b, S, in, w, m, dglob);
-    run_head_words(S.c, m, S.head);
-    __syncthreads();
-  }
-
   // ---- head bit 0 of every word, then the tile's counts from the bit words -------
   // (outliers << 42 | patches << 21 | runs; each count is at most 4096)
   if (tid < kSlots / 32) {
@@ -476,6 +360,327 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t*
   if (err) atomicOr(&A.st->status, err);
 }
 
+// ---- one tile ------------------------------------------------------------------------
+// Codes, records and histogram updates of codec block b (origin box[0..2], extent
+// box[3..5]) from the box in `in` (which this call overwrites with k and outlier
+// deltas).  Thread 0 adds the tile's record and patch counts to n_rec_acc /
+// n_patch_acc.
+template <int ND, typename E>
+__device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t* box, SmemT<E>& S, E* in,
+                             uint32_t& n_rec_acc, uint32_t& n_patch_acc) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t w[3] = {box[3], box[4], box[5]};
+  const uint32_t m = w[0] * w[1] * w[2];
+  const Pq<E> pq(A.st);
+  const int32_t r = (int32_t)A.radius;
+  const Geom& g = A.g;
+  const bool full = w[0] == g.blk[0] && w[1] == g.blk[1] && w[2] == g.blk[2];
+  int32_t* s_k = reinterpret_cast<int32_t*>(in);
+  int32_t* dglob = A.deltas + (uint64_t)b * kSlots;  // outlier residuals of this block, by slot
+  uint32_t err = 0;
+
+  // Postquantization of one warp step over the 32 consecutive slots of word j >> 5:
+  // code, outlier delta, the word's outlier / patch / run-head bits, and the code
+  // histogram (one add for the whole step when its 32 codes agree, as in zero
+  // regions).  Head bit 0 compares with the previous word, written by another warp:
+  // it is left clear here and set after the tile.
+  auto post = [&](int32_t delta, uint32_t j, bool patch_step, bool patch_bit) {
+    const uint32_t u = (uint32_t)(delta + r);
+    const uint32_t q = u - 1u < (uint32_t)(2 * r - 1) ? u : 0u;  // |delta| < r
+    S.c[j] = (uint16_t)q;
+    if (q == 0) dglob[j] = delta;
+    const uint32_t left = __shfl_up_sync(~0u, q, 1);
+    const uint32_t hd = __ballot_sync(~0u, lane != 0 && q != left);
+    const uint32_t ob = __ballot_sync(~0u, q == 0);
+    const uint32_t pb = patch_step ? __ballot_sync(~0u, patch_bit) : 0u;
+    if (hd == 0) {
+      if (lane == 0) atomicAdd(&S.hc[q], 32u);
+    } else {
+      atomicAdd(&S.hc[q], 1u);
+    }
+    if (lane == 0) {
+      S.head[j >> 5] = hd;
+      S.outl[j >> 5] = ob;
+      S.patch[j >> 5] = pb;
+    }
+  };
+
+  // ---- prequantization, Lorenzo residual (Sec. IV-B2), postquantization ----------
+  // The residual is the mixed difference (1 - S_x)(1 - S_y)(1 - S_z) k, each shift
+  // reading zero outside the chunk; that expansion is the paper's 1/2/3-D predictor.
+  if (full) {
+    if (ND == 1) {
+      // thread t: 16 consecutive elements (a warp covers two whole 256-chunks)
+      int32_t k[16];
+      uint32_t pm = 0, slow = 0;
+      E f[16];
+      load16(in + 16 * tid, f);
+#pragma unroll
+      for (int i = 0; i < 16; i++) slow |= (uint32_t)!pq.fast(f[i], k[i]) << i;
+      if (__any_sync(~0u, slow != 0)) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          if ((slow >> i) & 1u) {
+            bool p;
+            err |= pq.full(in[16 * tid + i], k[i], p);
+            pm |= (uint32_t)p << i;
+          }
+        }
+      }
+      const int32_t prev = __shfl_up_sync(~0u, k[15], 1);
+      uint32_t om = 0, hm = 0, qprev = 0, qfirst = 0;
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const uint32_t j = 16 * tid + i;
+        const int32_t left = i ? k[i - 1] : prev;
+        const int32_t delta = (j & 255) ? k[i] - left : k[i];
+        const uint32_t u = (uint32_t)(delta + r);
+        const uint32_t q = u - 1u < (uint32_t)(2 * r - 1) ? u : 0u;  // |delta| < r
+        S.c[j] = (uint16_t)q;
+        if (q == 0) dglob[j] = delta;
+        atomicAdd(&S.hc[q], 1u);
+        om |= (uint32_t)(q == 0) << i;
+        if (i == 0) qfirst = q;
+        else hm |= (uint32_t)(q != qprev) << i;
+        qprev = q;
+      }
+      // the first slot's left neighbour is the last slot of the lane below (lane 0:
+      // another warp's, set after the tile)
+      const uint32_t qbelow = __shfl_up_sync(~0u, qprev, 1);
+      if (lane != 0 && qfirst != qbelow) hm |= 1u;
+      const uint32_t om2 = __shfl_down_sync(~0u, om, 1), pm2 = __shfl_down_sync(~0u, pm, 1),
+                     hm2 = __shfl_down_sync(~0u, hm, 1);
+      if ((lane & 1) == 0) {
+        S.outl[tid >> 1] = om | (om2 << 16);
+        S.patch[tid >> 1] = pm | (pm2 << 16);
+        S.head[tid >> 1] = hm | (hm2 << 16);
+      }
+    } else if (ND == 2) {
+      // thread t: column xx = t & 63 of the 16-row chunk band t >> 6
+      const uint32_t xx = tid & 63, ry = tid >> 6;
+      int32_t k[16];
+      uint32_t pm = 0, slow = 0;
+#pragma unroll
+      for (int i = 0; i < 16; i++)
+        slow |= (uint32_t)!pq.fast(in[(16 * ry + i) * 64 + xx], k[i]) << i;
+      if (__any_sync(~0u, slow != 0)) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          if ((slow >> i) & 1u) {
+            bool p;
+            err |= pq.full(in[(16 * ry + i) * 64 + xx], k[i], p);
+            pm |= (uint32_t)p << i;
+          }
+        }
+      }
+      const bool anyp = __any_sync(~0u, pm != 0);
+#pragma unroll
+      for (int i = 15; i > 0; i--) k[i] -= k[i - 1];  // y difference within the chunk band
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const int32_t left = __shfl_up_sync(~0u, k[i], 1);
+        const int32_t delta = (xx & 15) ? k[i] - left : k[i];  // x difference
+        const uint32_t j = (16 * ry + i) * 64 + xx;
+        post(delta, j, anyp, (pm >> i) & 1u);
+      }
+    } else {
+      // thread t: z column of (xx, yy) = (t & 15, t >> 4); z and x differences in
+      // registers and shuffles, the y difference through shared memory
+      const uint32_t xx = tid & 15, yy = tid >> 4;
+      int32_t k[16];
+      uint32_t pm = 0, slow = 0;
+#pragma unroll
+      for (int i = 0; i < 16; i++)
+        slow |= (uint32_t)!pq.fast(in[(i * 16 + yy) * 16 + xx], k[i]) << i;
+      if (__any_sync(~0u, slow != 0)) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          if ((slow >> i) & 1u) {
+            bool p;
+            err |= pq.full(in[(i * 16 + yy) * 16 + xx], k[i], p);
+            pm |= (uint32_t)p << i;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 15; i > 0; i--)
+        if (i & 7) k[i] -= k[i - 1];  // z difference within 8-chunks
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const int32_t left = __shfl_up_sync(~0u, k[i], 1);
+        if (xx & 7) k[i] -= left;  // x difference
+      }
+      const bool anyp = __any_sync(~0u, pm != 0);
+      __syncthreads();  // every thread has read the box: it carries k from here
+#pragma unroll
+      for (int i = 0; i < 16; i++) s_k[(i * 16 + yy) * 16 + xx] = k[i];
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const uint32_t j = (i * 16 + yy) * 16 + xx;
+        const int32_t below = (yy & 7) ? s_k[(i * 16 + yy - 1) * 16 + xx] : 0;
+        post(k[i] - below, j, anyp, (pm >> i) & 1u);
+      }
+    }
+    __syncthreads();
+  } else {
+    err |= edge_codes<ND, E>(A, b, S, in, w, m, dglob);
+    run_head_words(S.c, m, S.head);
+    __syncthreads();
+  }
+
+  tile_tail(A, b, S, m, full, err, n_rec_acc, n_patch_acc);
+}
+
+// ---- global (unchunked) Lorenzo: tiles with a halo -----------------------------------
+// The box holds the tile and the elements one step before it on every axis, so the
+// predictor of the tile's first row, column and plane reads its real neighbours
+// instead of zeros; x is padded to four elements before the tile so that the box
+// starts on a 16-byte boundary (the TMA's rule).  Outside the field the box reads
+// zero: the predictor's boundary at the field's faces.
+template <int ND>
+struct Halo;
+template <>
+struct Halo<1> {
+  static constexpr uint32_t X = 17 * 256, Y = 1, Z = 1;  // 17 copies of 256 from x0 - 4
+};
+template <>
+struct Halo<2> {
+  static constexpr uint32_t X = 68, Y = 65, Z = 1;
+};
+template <>
+struct Halo<3> {
+  static constexpr uint32_t X = 20, Y = 17, Z = 17;
+};
+constexpr uint32_t kHaloPadX = 4;
+// the largest box (3-D, 5780 elements) rounded up to 32 elements, so each buffer
+// starts 128-byte aligned like the chunked tiles
+constexpr uint32_t kHaloMax = (20 * 17 * 17 + 31) / 32 * 32;
+static_assert(Halo<1>::X <= kHaloMax && Halo<2>::X * Halo<2>::Y <= kHaloMax, "halo boxes fit the buffer");
+
+template <typename E>
+__device__ void issue_tile_global(const ConstructTask* T, const uint32_t* org, E* buf, unsigned long long* bar) {
+  const Geom& g = T->a.g;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const int32_t x0 = (int32_t)org[2] - (int32_t)kHaloPadX;
+  if (g.ndim == 1) {
+    mbar_expect_tx(bar, (uint32_t)(Halo<1>::X * sizeof(E)));
+    for (int i = 0; i < 17; i++) tma_load(1, buf + 256 * i, &T->tmap, x0 + 256 * i, 0, 0, bar);
+  } else if (g.ndim == 2) {
+    mbar_expect_tx(bar, (uint32_t)(Halo<2>::X * Halo<2>::Y * sizeof(E)));
+    tma_load(2, buf, &T->tmap, x0, (int32_t)org[1] - 1, 0, bar);
+  } else {
+    mbar_expect_tx(bar, (uint32_t)(Halo<3>::X * Halo<3>::Y * Halo<3>::Z * sizeof(E)));
+    tma_load(3, buf, &T->tmap, x0, (int32_t)org[1] - 1, (int32_t)org[0] - 1, bar);
+  }
+}
+
+// Thread-loaded halo box (fields TMA cannot describe), zeros outside the field.
+template <int ND, typename E>
+__device__ void load_halo_threads(const ConstructArgs& A, const uint32_t* org, E* buf) {
+  using H = Halo<ND>;
+  constexpr uint32_t NB = H::X * H::Y * H::Z;
+  constexpr int hz = ND == 3 ? 1 : 0, hy = ND >= 2 ? 1 : 0;
+  const E* xs = field_ptr<E>(A);
+  const Geom& g = A.g;
+  for (uint32_t p = threadIdx.x; p < NB; p += kThreads) {
+    const int64_t x = (int64_t)org[2] + (int64_t)(p % H::X) - (int64_t)kHaloPadX;
+    const int64_t y = (int64_t)org[1] + (int64_t)((p / H::X) % H::Y) - hy;
+    const int64_t z = (int64_t)org[0] + (int64_t)(p / (H::X * H::Y)) - hz;
+    E v = E(0);
+    if (x >= 0 && y >= 0 && z >= 0 && x < (int64_t)g.n[2] && y < (int64_t)g.n[1] && z < (int64_t)g.n[0])
+      v = xs[((uint64_t)z * g.n[1] + (uint64_t)y) * g.n[2] + (uint64_t)x];
+    buf[p] = v;
+  }
+}
+
+// Codes, records and histograms of codec block b under the global predictor: the
+// halo'd box is prequantized in place (each element's k as int32), then every slot's
+// residual is the mixed difference (1 - S_x)(1 - S_y)(1 - S_z) k over the box (the
+// paper's 1/2/3-D predictor, Sec. IV-B2, with no chunk restarts), then the tail.
+template <int ND, typename E>
+__device__ void process_tile_global(const ConstructArgs& A, uint32_t b, const uint32_t* box,
+                                    SmemT<E, kHaloMax>& S, E* in, uint32_t& n_rec_acc, uint32_t& n_patch_acc) {
+  using H = Halo<ND>;
+  constexpr uint32_t NB = H::X * H::Y * H::Z;
+  constexpr uint32_t PER = (NB + kThreads - 1) / kThreads;
+  constexpr int hz = ND == 3 ? 1 : 0, hy = ND >= 2 ? 1 : 0;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t w[3] = {box[3], box[4], box[5]};
+  const uint32_t m = w[0] * w[1] * w[2];
+  const Pq<E> pq(A.st);
+  const int32_t r = (int32_t)A.radius;
+  int32_t* dglob = A.deltas + (uint64_t)b * kSlots;
+  uint32_t err = 0;
+  if (tid < kSlots / 32) S.patch[tid] = 0;
+  __syncthreads();
+  // prequantize every box element the predictor reads (x >= -1) into registers
+  int32_t kv[PER];
+#pragma unroll
+  for (uint32_t i = 0; i < PER; i++) {
+    const uint32_t p = tid + kThreads * i;
+    kv[i] = 0;
+    if (p < NB) {
+      const int x = (int)(p % H::X) - (int)kHaloPadX;
+      const int y = (int)((p / H::X) % H::Y) - hy, z = (int)(p / (H::X * H::Y)) - hz;
+      if (x >= -1) {
+        bool patch = false;
+        if (!pq.fast(in[p], kv[i])) err |= pq.full(in[p], kv[i], patch);
+        if (patch && x >= 0 && y >= 0 && z >= 0 && (uint32_t)x < w[2] && (uint32_t)y < w[1] && (uint32_t)z < w[0]) {
+          const uint32_t j = ((uint32_t)z * w[1] + (uint32_t)y) * w[2] + (uint32_t)x;
+          atomicOr(&S.patch[j >> 5], 1u << (j & 31));
+        }
+      }
+    }
+  }
+  __syncthreads();  // every element read: the box now carries k (int32, from its start)
+  int32_t* K = reinterpret_cast<int32_t*>(in);
+#pragma unroll
+  for (uint32_t i = 0; i < PER; i++) {
+    const uint32_t p = tid + kThreads * i;
+    if (p < NB) K[p] = kv[i];
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int i = 0; i < kPer; i++) {
+    const uint32_t j = tid + kThreads * i;
+    const bool inb = j < m;
+    uint32_t q = 0;
+    if (inb) {
+      uint32_t x = j, y = 0, z = 0;
+      if (ND == 2) {
+        y = j / w[2];
+        x = j - y * w[2];
+      } else if (ND == 3) {
+        const uint32_t pl = w[1] * w[2];
+        z = j / pl;
+        const uint32_t rr = j - z * pl;
+        y = rr / w[2];
+        x = rr - y * w[2];
+      }
+      const uint32_t p = ((z + hz) * H::Y + (y + hy)) * H::X + (x + kHaloPadX);
+      int32_t d = K[p] - K[p - 1];
+      if (ND >= 2) d -= K[p - H::X] - K[p - H::X - 1];
+      if (ND == 3) {
+        constexpr uint32_t PL = H::X * H::Y;
+        d -= K[p - PL] - K[p - PL - 1];
+        d += K[p - PL - H::X] - K[p - PL - H::X - 1];
+      }
+      const uint32_t u = (uint32_t)(d + r);
+      q = u - 1u < (uint32_t)(2 * r - 1) ? u : 0u;  // |delta| < r
+      atomicAdd(&S.hc[q], 1u);
+      if (q == 0) dglob[j] = d;
+    }
+    S.c[j] = (uint16_t)q;  // zero beyond m
+    const uint32_t ob = __ballot_sync(~0u, inb && q == 0);
+    if (lane == 0) S.outl[j >> 5] = ob;
+  }
+  __syncthreads();
+  run_head_words(S.c, m, S.head);
+  __syncthreads();
+  tile_tail(A, b, S, m, false, err, n_rec_acc, n_patch_acc);
+}
+
 __device__ __forceinline__ int find_field(const uint32_t* tile0, int nfields, uint32_t t, int hint) {
   if (t < tile0[hint + 1]) return hint;
   int lo = hint + 1, hi = nfields - 1;  // tile0[lo] <= t
@@ -493,14 +698,17 @@ __device__ __forceinline__ int find_field(const uint32_t* tile0, int nfields, ui
 // entry passes the task by value (`one`, tasks == nullptr, ntiles = its block
 // count); batches pass a device table and tile0[f], the first global tile of field
 // f (tile0[nfields] = ntiles).
-template <int ND>  // 1, 2, 3; 0 = any (batches of mixed dimensionality)
+// ND 1, 2, 3; 0 = any (batches of mixed dimensionality); E the element type; G the
+// global (unchunked) predictor with halo'd tiles
+template <int ND, typename E, bool G = false>
 __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_constant__ ConstructTask one,
                                                              const ConstructTask* __restrict__ tasks,
                                                              const uint32_t* __restrict__ tile0, int nfields,
                                                              uint32_t ntiles, uint32_t* ticket,
                                                              uint32_t spin_limit) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  using SM = SmemT<E, G ? kHaloMax : kSlots>;
+  SM& S = *reinterpret_cast<SM*>(smem_raw);
   __shared__ uint32_t s_t[2];
   __shared__ int s_f[2];
   __shared__ uint32_t s_fail;
@@ -517,7 +725,10 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
     if (f >= 0) {
       uint32_t* bx = S.box[slot];
       block_box(task(f)->a.g, t - base(f), bx, bx + 3);
-      if (task(f)->use_tma) issue_tile(task(f), bx, S.in[slot], &S.bar[slot]);
+      if (task(f)->use_tma) {
+        if (G) issue_tile_global(task(f), bx, S.in[slot], &S.bar[slot]);
+        else issue_tile(task(f), bx, S.in[slot], &S.bar[slot]);
+      }
     }
   };
   uint32_t pending = 0;
@@ -579,14 +790,21 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
         s_fail = 1;
       }
     } else {
-      load_tile_threads(A, b, S.in[cur]);
+      if (G) load_halo_threads<ND == 0 ? 3 : ND, E>(A, S.box[cur], S.in[cur]);
+      else load_tile_threads(A, b, S.in[cur]);
     }
     __syncthreads();
     if (s_fail) break;
     const uint32_t* bx = S.box[cur];
-    if (ND == 1 || (ND == 0 && A.g.ndim == 1)) process_tile<1>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
-    else if (ND == 2 || (ND == 0 && A.g.ndim == 2)) process_tile<2>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
-    else process_tile<3>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
+    if constexpr (G) {
+      static_assert(ND != 0, "global tiles: one dimensionality per launch");
+      process_tile_global<ND == 0 ? 3 : ND, E>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
+    } else {
+      if (ND == 1 || (ND == 0 && A.g.ndim == 1)) process_tile<1, E>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
+      else if (ND == 2 || (ND == 0 && A.g.ndim == 2))
+        process_tile<2, E>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
+      else process_tile<3, E>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
+    }
     __syncthreads();
     cur ^= 1;
   }
@@ -606,7 +824,7 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
   if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-size_t construct_smem_bytes() { return sizeof(Smem); }
+size_t construct_smem_bytes() { return sizeof(SmemT<float>); }
 
 // ---- host side ------------------------------------------------------------------------
 namespace {
@@ -630,7 +848,7 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-int g_sms = 0, g_occ = 0;
+int g_sms = 0;
 
 }  // namespace
 
@@ -639,9 +857,12 @@ int g_sms = 0, g_occ = 0;
 void prepare_construct_task(ConstructTask& T) {
   T.use_tma = 0;
   const Geom& g = T.a.g;
-  const uintptr_t base = reinterpret_cast<uintptr_t>(T.a.x);
+  const bool f64 = T.a.x64 != nullptr;
+  const uint32_t esz = f64 ? 8u : 4u;
+  void* xp = f64 ? const_cast<double*>(T.a.x64) : static_cast<void*>(const_cast<float*>(T.a.x));
+  const uintptr_t base = reinterpret_cast<uintptr_t>(xp);
   if (base & 15) return;
-  if (g.ndim >= 2 && (g.n[2] % 4) != 0) return;
+  if (g.ndim >= 2 && ((uint64_t)g.n[2] * esz) % 16 != 0) return;
   EncodeTiledFn fn = encode_fn();
   if (!fn) return;
   cuuint64_t dim[3], stride[2];
@@ -653,48 +874,76 @@ void prepare_construct_task(ConstructTask& T) {
   } else if (rank == 2) {
     dim[0] = g.n[2];
     dim[1] = g.n[1];
-    stride[0] = (cuuint64_t)g.n[2] * 4;
-    box[0] = 64;
-    box[1] = 64;
+    stride[0] = (cuuint64_t)g.n[2] * esz;
+    box[0] = T.a.global ? Halo<2>::X : 64;
+    box[1] = T.a.global ? Halo<2>::Y : 64;
   } else {
     dim[0] = g.n[2];
     dim[1] = g.n[1];
     dim[2] = g.n[0];
-    stride[0] = (cuuint64_t)g.n[2] * 4;
-    stride[1] = (cuuint64_t)g.n[2] * g.n[1] * 4;
-    box[0] = box[1] = box[2] = 16;
+    stride[0] = (cuuint64_t)g.n[2] * esz;
+    stride[1] = (cuuint64_t)g.n[2] * g.n[1] * esz;
+    box[0] = T.a.global ? Halo<3>::X : 16;
+    box[1] = T.a.global ? Halo<3>::Y : 16;
+    box[2] = T.a.global ? Halo<3>::Z : 16;
   }
   if (rank == 1 && g.nelem >= (1ull << 32)) return;
-  const CUresult r = fn(&T.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<float*>(T.a.x), dim,
-                        stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  const CUresult r = fn(&T.tmap, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        (cuuint32_t)rank, xp, dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   T.use_tma = r == CUDA_SUCCESS ? 1 : 0;
 }
 
-// Persistent grid size: resident CTAs per SM times SMs, capped by the tile count.
-int construct_grid(uint32_t ntiles) {
+// Persistent grid size: resident CTAs per SM (of the kernel that runs, with its
+// shared memory) times SMs, capped by the tile count.
+template <int ND, typename E, bool G>
+int grid_of(uint32_t ntiles) {
+  using SM = SmemT<E, G ? kHaloMax : kSlots>;
+  static int occ = 0;
   if (g_sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(construct_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaFuncSetAttribute(construct_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaFuncSetAttribute(construct_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaFuncSetAttribute(construct_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ, construct_kernel<0>, kThreads, sizeof(Smem));
     if (g_sms <= 0) g_sms = 1;
-    if (g_occ <= 0) g_occ = 1;
   }
-  const uint64_t cap = (uint64_t)g_sms * g_occ;
+  if (occ == 0) {
+    cudaFuncSetAttribute(construct_kernel<ND, E, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, construct_kernel<ND, E, G>, kThreads, sizeof(SM));
+    if (occ <= 0) occ = 1;
+  }
+  const uint64_t cap = (uint64_t)g_sms * occ;
   return (int)(ntiles < cap ? (ntiles ? ntiles : 1) : cap);
 }
 
-cudaError_t launch_construct(const ConstructTask& one, uint32_t* ticket, cudaStream_t s) {
-  const int grid = construct_grid(one.a.g.nblk);
-  trace_begin(K_CONSTRUCT, s);
+int construct_grid(uint32_t ntiles) { return grid_of<0, float, false>(ntiles); }
+
+template <int ND, typename E, bool G>
+void launch_one(const ConstructTask& one, uint32_t* ticket, cudaStream_t s) {
+  using SM = SmemT<E, G ? kHaloMax : kSlots>;
+  const int grid = grid_of<ND, E, G>(one.a.g.nblk);
+  construct_kernel<ND, E, G><<<grid, kThreads, sizeof(SM), s>>>(one, nullptr, nullptr, 1, one.a.g.nblk, ticket,
+                                                                one.a.spin_limit);
+}
+
+template <typename E, bool G>
+void launch_nd(const ConstructTask& one, uint32_t* ticket, cudaStream_t s) {
   const int nd = one.a.g.ndim;
-  auto k = nd == 1 ? construct_kernel<1> : (nd == 2 ? construct_kernel<2> : construct_kernel<3>);
-  k<<<grid, kThreads, sizeof(Smem), s>>>(one, nullptr, nullptr, 1, one.a.g.nblk, ticket, one.a.spin_limit);
+  if (nd == 1) launch_one<1, E, G>(one, ticket, s);
+  else if (nd == 2) launch_one<2, E, G>(one, ticket, s);
+  else launch_one<3, E, G>(one, ticket, s);
+}
+
+cudaError_t launch_construct(const ConstructTask& one, uint32_t* ticket, cudaStream_t s) {
+  const bool f64 = one.a.x64 != nullptr, global = one.a.global != 0;
+  trace_begin(K_CONSTRUCT, s);
+  if (f64) {
+    if (global) launch_nd<double, true>(one, ticket, s);
+    else launch_nd<double, false>(one, ticket, s);
+  } else {
+    if (global) launch_nd<float, true>(one, ticket, s);
+    else launch_nd<float, false>(one, ticket, s);
+  }
   trace_end(K_CONSTRUCT, s);
   return cudaGetLastError();
 }
@@ -704,12 +953,16 @@ cudaError_t launch_construct_batch(const ConstructTask* d_tasks, const uint32_t*
                                    cudaStream_t s) {
   ConstructTask dummy;
   memset(&dummy, 0, sizeof(dummy));
-  if (grid <= 0) grid = construct_grid(ntiles);
-  // the specialised kernel when every field has the same dimensionality
-  auto k = nd == 1 ? construct_kernel<1>
-                   : (nd == 2 ? construct_kernel<2> : (nd == 3 ? construct_kernel<3> : construct_kernel<0>));
+  // the specialised kernel when every field has the same dimensionality (grid_of also
+  // sets the kernel's shared-memory limit); an explicit grid comes from the autotuner
+  const int full = nd == 1 ? grid_of<1, float, false>(ntiles)
+                           : (nd == 2 ? grid_of<2, float, false>(ntiles)
+                                      : (nd == 3 ? grid_of<3, float, false>(ntiles) : grid_of<0, float, false>(ntiles)));
+  if (grid <= 0) grid = full;
+  auto k = nd == 1 ? construct_kernel<1, float>
+                   : (nd == 2 ? construct_kernel<2, float> : (nd == 3 ? construct_kernel<3, float> : construct_kernel<0, float>));
   trace_begin(K_CONSTRUCT, s);
-  k<<<grid, kThreads, sizeof(Smem), s>>>(dummy, d_tasks, d_tile0, nfields, ntiles, ticket, spin_limit);
+  k<<<grid, kThreads, sizeof(SmemT<float>), s>>>(dummy, d_tasks, d_tile0, nfields, ntiles, ticket, spin_limit);
   trace_end(K_CONSTRUCT, s);
   return cudaGetLastError();
 }

@@ -36,29 +36,37 @@ __device__ void dec_prep_body(const DecodeArgs& a) {
   }
   if (tid < 3) s_nc[tid] = 0;
   __syncthreads();
-  // payload offsets and, packed above bit 48 of the same scan, the list of run blocks
-  constexpr uint64_t kLow = (1ull << 48) - 1;
-  uint64_t carry = 0, rcarry = 0;
+  // payload offsets and, packed above them in the same scan (bits 40-51 and 52-63; a
+  // scan step covers at most 1024 blocks), the lists of run blocks and of the blocks
+  // the reconstruction kernel takes (those not reconstructed by their decoder warps)
+  constexpr uint64_t kLow = (1ull << 40) - 1, kMid = (1ull << 12) - 1;
+  uint64_t carry = 0, rcarry = 0, scarry = 0;
   bool bad = false;
   for (uint32_t base = 0; base < a.g.nblk; base += blockDim.x) {
     const uint32_t b = base + tid;
     uint64_t bb = 0;
-    bool run = false;
+    bool run = false, slow = false;
     if (b < a.g.nblk) {
       const uint32_t c = a.ar[a.off_codec + b];
       bb = reinterpret_cast<const uint32_t*>(a.ar + a.off_bb)[b];
-      if (c > 2 || (bb & 3)) bad = true;
+      if (c > 2 || (bb & 3) || bb >= (1ull << 30)) bad = true;  // a valid block is below 2^17 bytes
       else atomicAdd(&s_nc[c], 1u);
       run = c == CODEC_RLE || c == CODEC_RLE_HUFF;
+      slow = !(a.fuse && c == CODEC_HUFF && block_is_full(a.g, b));
     }
+    if (bb >= (1ull << 30)) bb = 0;
     uint64_t tot;
-    const uint64_t ex = block_excl_scan<uint64_t>(bb | ((uint64_t)run << 48), s_scan, &tot);
+    const uint64_t ex =
+        block_excl_scan<uint64_t>(bb | ((uint64_t)slow << 40) | ((uint64_t)run << 52), s_scan, &tot);
     if (b < a.g.nblk) a.blk_off[b] = carry + (ex & kLow);
-    if (run && a.runblk) a.runblk[rcarry + (ex >> 48)] = b;
+    if (run && a.runblk) a.runblk[rcarry + (ex >> 52)] = b;
+    if (slow && a.slowblk) a.slowblk[scarry + ((ex >> 40) & kMid)] = b;
     carry += tot & kLow;
-    rcarry += tot >> 48;
+    rcarry += tot >> 52;
+    scarry += (tot >> 40) & kMid;
   }
   if (tid == 0) {
+    a.st->n_slow = (uint32_t)scarry;
     a.blk_off[a.g.nblk] = carry;
     if (carry != a.payload) bad = true;
     if ((s_nc[CODEC_HUFF] && !(a.flags & 1u)) || (s_nc[CODEC_RLE_HUFF] && !(a.flags & 2u))) bad = true;
@@ -66,6 +74,87 @@ __device__ void dec_prep_body(const DecodeArgs& a) {
       if (s_nc[c] != a.n_codec[c]) bad = true;  // the header's counts decide which kernels run
   }
   if (bad) flag(a.st, ERR_CORRUPT);
+}
+
+// Single-field set-up, one CTA per 1024 codec blocks (chunks taken by ticket and
+// chained by decoupled look-back, so no CTA scans the whole block list): codec and
+// block-size validation, payload offsets, the lists of run blocks and of the blocks
+// the reconstruction kernel takes, per-codec counts.  The chunk counted last checks
+// the totals against the header.
+__device__ void dec_prep_chunk_body(const DecodeArgs& a, uint32_t nchunks) {
+  __shared__ uint64_t s_scan[33];
+  __shared__ uint32_t s_scan32[33];
+  __shared__ uint32_t s_nc[3];
+  __shared__ uint32_t s_chunk;
+  __shared__ unsigned long long s_cp, s_cc;
+  __shared__ bool s_last;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_chunk = atomicAdd(&a.st->ticket_encode, 1u);
+  if (tid < 3) s_nc[tid] = 0;
+  __syncthreads();
+  const uint32_t chunk = s_chunk;
+  if (chunk == 0 && a.check_hdr && tid < 32) {
+    // the launch was set up from a host copy of the header: it must be this archive's
+    const uint8_t* h = a.ar + 4 * tid;
+    const uint32_t v = (uint32_t)h[0] | ((uint32_t)h[1] << 8) | ((uint32_t)h[2] << 16) | ((uint32_t)h[3] << 24);
+    if (__any_sync(~0u, v != a.hdr[tid]) && tid == 0) flag(a.st, ERR_CORRUPT);
+  }
+  const uint32_t b = chunk * 1024u + tid;
+  uint64_t bb = 0;
+  bool run = false, slow = false, bad = false;
+  if (b < a.g.nblk) {
+    const uint32_t c = a.ar[a.off_codec + b];
+    bb = reinterpret_cast<const uint32_t*>(a.ar + a.off_bb)[b];
+    if (c > 2 || (bb & 3)) bad = true;
+    else atomicAdd(&s_nc[c], 1u);
+    run = c == CODEC_RLE || c == CODEC_RLE_HUFF;
+    slow = !(a.fuse && c == CODEC_HUFF && block_is_full(a.g, b));
+  }
+  uint64_t tot_pay;
+  const uint64_t ex_pay = block_excl_scan<uint64_t>(bb, s_scan, &tot_pay);
+  uint32_t tot_cnt;  // (slow << 16) | run, at most 1024 each in a chunk
+  const uint32_t ex_cnt = block_excl_scan<uint32_t>(((uint32_t)slow << 16) | (uint32_t)run, s_scan32, &tot_cnt);
+  if (tid < 32) {
+    // chunk totals: payload bytes; (slow blocks << 32) | run blocks (each below 2^19)
+    const uint64_t cnt = ((uint64_t)(tot_cnt >> 16) << 32) | (tot_cnt & 0xffffu);
+    if (tid == 0) {
+      lookback_publish(a.prep_lb, chunk, tot_pay);
+      lookback_publish(a.prep_lb + nchunks, chunk, cnt);
+    }
+    const uint64_t cp = lookback_warp(a.prep_lb, chunk, tot_pay, &a.st->status, kSpinLimit);
+    const uint64_t cc = lookback_warp(a.prep_lb + nchunks, chunk, cnt, &a.st->status, kSpinLimit);
+    if (tid == 0) {
+      s_cp = cp;
+      s_cc = cc;
+    }
+  }
+  __syncthreads();
+  const uint64_t cp = s_cp, cc = s_cc;
+  if (b < a.g.nblk) a.blk_off[b] = cp + ex_pay;
+  if (run && a.runblk) a.runblk[(uint32_t)cc + (ex_cnt & 0xffffu)] = b;
+  if (slow && a.slowblk) a.slowblk[(uint32_t)(cc >> 32) + (ex_cnt >> 16)] = b;
+  if (tid == 0) {
+    if (chunk == nchunks - 1) {
+      a.blk_off[a.g.nblk] = cp + tot_pay;
+      a.st->n_slow = (uint32_t)(cc >> 32) + (tot_cnt >> 16);
+      if (cp + tot_pay != a.payload) bad = true;
+    }
+    for (int c = 0; c < 3; c++)
+      if (s_nc[c]) atomicAdd(&a.st->ncodec[c], s_nc[c]);
+    __threadfence();
+    s_last = atomicAdd(&a.st->encode_done, 1u) == nchunks - 1;
+  }
+  if (bad) flag(a.st, ERR_CORRUPT);
+  __syncthreads();
+  if (s_last && tid == 0) {
+    __threadfence();
+    uint32_t nc[3];
+    for (int c = 0; c < 3; c++) nc[c] = atomicAdd(&a.st->ncodec[c], 0u);
+    bool wrong = (nc[CODEC_HUFF] && !(a.flags & 1u)) || (nc[CODEC_RLE_HUFF] && !(a.flags & 2u));
+    for (int c = 0; c < 3; c++)
+      if (nc[c] != a.n_codec[c]) wrong = true;  // the header's counts decide which kernels run
+    if (wrong) flag(a.st, ERR_CORRUPT);
+  }
 }
 
 __device__ void dec_records_body(const DecodeArgs& a, uint32_t cta, uint32_t nctas) {
@@ -76,7 +165,7 @@ __device__ void dec_records_body(const DecodeArgs& a, uint32_t cta, uint32_t nct
   for (uint64_t i = cta * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)nctas * blockDim.x) {
     if (i < a.n_rec) {
       const uint32_t key = rec[2 * i];
-      bool bad = (i + 1 < a.n_rec) && key >= rec[2 * (i + 1)];
+      bool bad = ((i + 1 < a.n_rec) && key >= rec[2 * (i + 1)]) || (a.f64 && (key & 1u));
       const uint64_t slot = key >> 1;
       if (slot >= nslots) {
         bad = true;
@@ -194,16 +283,16 @@ __device__ void dec_tables_body(const DecodeArgs& a, int book) {
   }
 }
 
-// One launch for archive set-up: CTA 0 validates codecs and scans block sizes, CTAs
-// 1-3 build the decode tables of the three books, the rest validate records and find
-// each block's first record.
-__global__ __launch_bounds__(1024) void dec_setup_kernel(DecodeArgs a) {
-  if (blockIdx.x == 0) {
-    dec_prep_body(a);
-  } else if (blockIdx.x <= 3) {
-    dec_tables_body(a, (int)blockIdx.x - 1);
+// One launch for archive set-up: the first `nchunks` CTAs validate codecs and scan
+// block sizes (one chunk of 1024 blocks each), the next three build the decode tables
+// of the three books, the rest validate records and find each block's first record.
+__global__ __launch_bounds__(1024) void dec_setup_kernel(DecodeArgs a, uint32_t nchunks) {
+  if (blockIdx.x < nchunks) {
+    dec_prep_chunk_body(a, nchunks);
+  } else if (blockIdx.x < nchunks + 3) {
+    dec_tables_body(a, (int)(blockIdx.x - nchunks));
   } else {
-    dec_records_body(a, blockIdx.x - 4, gridDim.x - 4);
+    dec_records_body(a, blockIdx.x - nchunks - 3, gridDim.x - nchunks - 3);
   }
 }
 
@@ -251,25 +340,43 @@ __device__ __forceinline__ int ihs_match(uint64_t bb, int nb, const BookView& bk
   return lo;
 }
 
-// One warp decodes N symbols (+add) from in[0..avail) into out[].  Returns false
-// (warp-uniform) if the stream is damaged; *used gets the units read.
-// The warp reads the stream strictly in order, so the next 96 units are kept in three
-// 32-unit register windows (lane i holds unit base+i of each); a top-up takes its unit
-// from a window by shuffle and a window is reloaded (one 64-byte load) two windows
-// before it is needed, so no load sits on the decode's critical path.
-__device__ bool ihs_decode_warp(const uint16_t* __restrict__ in, uint32_t avail, uint32_t N,
-                                const BookView& bk, uint16_t* out, int add, uint32_t* used) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t T = (N + 31) / 32;
-  auto fetch = [&](uint32_t i) -> uint32_t { return i < avail ? (uint32_t)__ldg(&in[i]) : 0u; };
-  uint32_t w0 = fetch(lane), w1 = fetch(32 + lane), w2 = fetch(64 + lane);
-  uint32_t wbase = 0;  // stream index of w0's lane 0
-  uint64_t bb = 0;
-  int nb = 0;
-  uint32_t cur = 0;
-  bool bad = false;
-  for (uint32_t t = 0; t < T; t++) {
-    const bool active = 32 * t + lane < N && !bad;
+// A warp's reader of one interleaved stream in[0..avail).  The warp reads the stream
+// strictly in order, so the next 96 units are kept in three 32-unit register windows
+// (lane i holds unit base+i of each); a top-up takes its unit from a window by
+// shuffle and a window is reloaded (one 64-byte load) two windows before it is
+// needed, so no load sits on the decode's critical path.
+struct IhsReader {
+  const uint16_t* __restrict__ in;
+  uint32_t avail;
+  uint32_t w0, w1, w2;
+  uint32_t wbase;  // stream index of w0's lane 0
+  uint32_t cur;    // units taken so far by the warp
+  uint64_t bb;     // this lane's bits, left-aligned
+  int nb;
+  bool bad;        // this lane met a damaged stream
+
+  __device__ __forceinline__ uint32_t fetch(uint32_t i) const { return i < avail ? (uint32_t)__ldg(&in[i]) : 0u; }
+
+  __device__ __forceinline__ void init(const uint16_t* p, uint32_t n) {
+    const uint32_t lane = threadIdx.x & 31;
+    in = p;
+    avail = n;
+    w0 = fetch(lane);
+    w1 = fetch(32 + lane);
+    w2 = fetch(64 + lane);
+    wbase = 0;
+    cur = 0;
+    bb = 0;
+    nb = 0;
+    bad = false;
+  }
+
+  // One decoding step of the 32 lanes (every lane calls): each active lane tops up
+  // its bits in rounds until a codeword is complete, then consumes it.  Returns the
+  // symbol, meaningful where the lane was active and is not bad.
+  __device__ __forceinline__ int step(bool active, const BookView& bk) {
+    const uint32_t lane = threadIdx.x & 31;
+    active = active && !bad;
     int sym = 0, ml = active ? ihs_match(bb, nb, bk, sym) : 0;
     bool need = active && ml == 0;
     uint32_t ballot;
@@ -298,27 +405,284 @@ __device__ bool ihs_decode_warp(const uint16_t* __restrict__ in, uint32_t avail,
       }
     }
     if (active && !bad) {
-      out[32 * t + lane] = (uint16_t)(sym + add);
       bb = ml >= 64 ? 0ull : bb << ml;
       nb -= ml;
     }
+    return sym;
   }
-  *used = cur;
-  return !__any_sync(~0u, bad);
+};
+
+// One warp decodes N symbols (+add) from in[0..avail) into out[].  Returns false
+// (warp-uniform) if the stream is damaged; *used gets the units read.
+__device__ bool ihs_decode_warp(const uint16_t* __restrict__ in, uint32_t avail, uint32_t N,
+                                const BookView& bk, uint16_t* out, int add, uint32_t* used) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t T = (N + 31) / 32;
+  IhsReader rd;
+  rd.init(in, avail);
+  for (uint32_t t = 0; t < T; t++) {
+    const bool active = 32 * t + lane < N;
+    const int sym = rd.step(active, bk);
+    if (active && !rd.bad) out[32 * t + lane] = (uint16_t)(sym + add);
+  }
+  *used = rd.cur;
+  return !__any_sync(~0u, rd.bad);
+}
+
+__device__ __forceinline__ float scale(int32_t k, float ebx2) { return __fmul_rn(__int2float_rn(k), ebx2); }
+
+// The reconstruction's output by element type: x' = fl32(k * 2eb_f) for FP32 fields,
+// x' = fl64(k * step) for double fields (which have no verbatim patches).
+template <typename E>
+struct Out;
+template <>
+struct Out<float> {
+  float* __restrict__ p;
+  float ebx2;
+  __device__ explicit Out(const DecodeArgs& a) : p(a.out), ebx2(a.ebx2_f) {}
+  __device__ __forceinline__ float value(int32_t k) const { return scale(k, ebx2); }
+  __device__ __forceinline__ void put(uint64_t i, int32_t k) const { __stcs(&p[i], scale(k, ebx2)); }
+  __device__ __forceinline__ void put_patch(uint64_t i, int32_t k, bool patch, uint32_t bits) const {
+    __stcs(&p[i], patch ? __uint_as_float(bits) : scale(k, ebx2));
+  }
+  __device__ __forceinline__ void patch(uint64_t i, uint32_t bits) const { p[i] = __uint_as_float(bits); }
+};
+template <>
+struct Out<double> {
+  double* __restrict__ p;
+  double step;
+  __device__ explicit Out(const DecodeArgs& a) : p(a.out64), step(a.step_d) {}
+  __device__ __forceinline__ void put(uint64_t i, int32_t k) const { __stcs(&p[i], __dmul_rn((double)k, step)); }
+  __device__ __forceinline__ void put_patch(uint64_t i, int32_t k, bool, uint32_t) const { put(i, k); }
+  __device__ __forceinline__ void patch(uint64_t, uint32_t) const {}
+};
+
+// =================================================================================
+// fused decoding and reconstruction of full Huffman blocks (Alg. 1 decompression,
+// Sec. IV-B "Partial-Sum Lorenzo Reconstruction")
+//
+// A full block's stream A holds its first 2048 codes and stream B the rest, and
+// 2048 codes end on a Lorenzo-chunk boundary in every dimensionality: 8 chunks of
+// 256 (1-D), rows 0-31 / 32-63 (2-D, 16x16 chunks), z 0-7 / 8-15 (3-D, 8^3 chunks).
+// So the warp that decodes a stream owns whole chunks, and at step t lane l holds
+// code 32t + l, which is already where the partial sums want it:
+//   1-D  element 32t + l: the x sum is a warp scan plus a carry within each chunk
+//        of 8 steps;
+//   2-D  row t/2, column 32(t&1) + l: x sums over 16-lane groups by shuffles, y sums
+//        in a register per column half, restarting every 16 rows;
+//   3-D  plane t/8, row 2(t%8) + l/16, column l%16: x sums over 8-lane groups, y sums
+//        across the lane pair (l, l^16) by one shuffle and a running pair sum that
+//        restarts every 4 steps, z sums in a register per step of the plane.
+// Each step then scales the exact integers and stores them: the codes never leave
+// the registers.  Outliers (code 0) take their delta from the block's records, found
+// by binary search (records are sorted by slot); verbatim patches overwrite their
+// elements after the warp's own stores.
+// =================================================================================
+
+// The block's outlier records, merged into the decode order.  Records are sorted by
+// key (slot * 2 + kind), and step t of a stream covers 32 consecutive slots, so the
+// warp keeps the key of its next record in a register; only a step that reaches it
+// loads the step's records (at most 64: an outlier and a patch per slot) and hands
+// each outlier's delta to the lane of its slot through a 32-word per-warp table in
+// shared memory (the fused code q' of Alg. 1).  The step's outlier records must match
+// its code-0 slots one for one; anything else marks the stream corrupt.  Patches are
+// applied after the stream (they only overwrite output values).
+struct RecordCursor {
+  const uint2* __restrict__ rec;
+  uint32_t ptr, end;  // next record, end of the block's records
+  uint32_t next;      // key of rec[ptr] (0xffffffff when none is left)
+
+  // Positions the cursor at the first record with key >= key_lo among rec[rs..re).
+  __device__ __forceinline__ void init(const uint2* r, uint32_t rs, uint32_t re, uint32_t key_lo) {
+    rec = r;
+    end = re;
+    uint32_t lo = rs, hi = re;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (rec[mid].x < key_lo) lo = mid + 1;
+      else hi = mid;
+    }
+    ptr = lo;
+    next = ptr < end ? rec[ptr].x : 0xffffffffu;
+  }
+
+  // The step whose first slot has key key0 (the calling lane's slot has key key0 +
+  // 2 lane): where sym == 0, q becomes the outlier's delta.  All lanes call
+  // (warp-uniform control flow).  s_tab: this warp's 32 words of shared memory.
+  __device__ __forceinline__ void step(uint32_t key0, int sym, int32_t& q, bool& bad, uint32_t* s_tab) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (next >= key0 + 64u) {  // no record in this step (the common case)
+      bad |= sym == 0;
+      return;
+    }
+    uint32_t omask = 0;
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      const uint32_t i = ptr + lane;  // ptr has moved past the first half's records
+      const uint2 kv = i < end ? rec[i] : make_uint2(0xffffffffu, 0u);
+      const bool here = kv.x < key0 + 64u;
+      const uint32_t l = ((kv.x >> 1) - (key0 >> 1)) & 31u;  // the record's lane
+      const bool outlier = here && !(kv.x & 1u);
+      if (outlier) s_tab[l] = kv.y;
+      omask |= __reduce_or_sync(~0u, outlier ? 1u << l : 0u);
+      const uint32_t hb = __ballot_sync(~0u, here);
+      ptr += __popc(hb);
+      if (hb != ~0u) break;
+    }
+    __syncwarp();
+    if ((omask >> lane) & 1u) q = (int32_t)s_tab[lane];
+    bad |= __ballot_sync(~0u, sym == 0) != omask;
+    next = ptr < end ? rec[ptr].x : 0xffffffffu;
+    __syncwarp();  // the table is free again
+  }
+};
+
+// Decodes stream `which` (0: A, 1: B) of full Huffman block b from u[0..avail) and
+// writes its 2048 reconstructed elements.  The warp decodes 8 steps into a register
+// window, then runs their 8 prefix chains together (independent shuffles overlap)
+// and stores them.  Returns false (warp-uniform) if the stream is damaged or its records do not
+// match its outlier slots; *used gets the units read.  s_tab: this warp's 288 words
+// of shared memory (the record table, then the 3-D running sums).
+template <int ND, typename E>
+__device__ bool fused_decode_reconstruct(const DecodeArgs& a, uint32_t b, uint32_t which, const uint16_t* u,
+                                         uint32_t avail, const BookView& bk, uint32_t* used, uint32_t* s_tab) {
+  const uint32_t lane = threadIdx.x & 31;
+  const int32_t r = (int32_t)a.radius;
+  const Out<E> out(a);
+  const uint32_t key0 = (b * (uint32_t)kSlots + 2048u * which) * 2u;  // record key of the stream's first slot
+  uint32_t org[3], w[3];
+  block_box(a.g, b, org, w);
+  const uint64_t ny = a.g.n[1], nx = a.g.n[2];
+  const uint2* rec = reinterpret_cast<const uint2*>(a.ar + a.off_rec);
+  const uint32_t rs = a.rec_start[b], re = a.rec_start[b + 1];
+  IhsReader rd;
+  rd.init(u, avail);
+  RecordCursor rc;
+  rc.init(rec, rs, re, key0);
+  bool bad = false;
+  // 3-D: the running z sum of each of the lane's 8 rows of a plane, in this warp's
+  // shared-memory strip (row s of lane l at zs[32 s + l]: no bank conflicts)
+  int32_t* zs = reinterpret_cast<int32_t*>(s_tab) + 32;
+  int32_t carry = 0, ysum0 = 0, ysum1 = 0;
+  if (ND == 3) {
+#pragma unroll
+    for (int s = 0; s < 8; s++) zs[32 * s + lane] = 0;
+  }
+#pragma unroll 1
+  for (uint32_t t0 = 0; t0 < 64; t0 += 8) {
+    // the decoding step stays rolled (one copy of its code: unrolling it overflows the
+    // instruction cache); each step's q' shifts into an 8-register window
+    int32_t q[8];
+#pragma unroll 1
+    for (uint32_t s = 0; s < 8; s++) {
+      const int sym = rd.step(true, bk);
+      int32_t v = sym - r;
+      rc.step(key0 + 64u * (t0 + s), sym, v, bad, s_tab);
+#pragma unroll
+      for (int k = 0; k < 7; k++) q[k] = q[k + 1];
+      q[7] = v;
+    }
+    if (ND == 1) {
+      // 8 steps = one 256-element chunk: per-step warp scans, then the carries
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+          const int32_t up = __shfl_up_sync(~0u, q[s], o);
+          if (lane >= (uint32_t)o) q[s] += up;
+        }
+      }
+      carry = 0;
+      const uint64_t base = (uint64_t)org[2] + 2048u * which + 32u * t0 + lane;
+#pragma unroll
+      for (int s = 0; s < 8; s++) {
+        const int32_t v = q[s] + carry;
+        carry += __shfl_sync(~0u, q[s], 31);
+        out.put(base + 32u * s, v);
+      }
+    } else if (ND == 2) {
+      // rows t/2, columns 32 (t&1) + lane: x sums over 16-lane groups, y sums down
+      // each column half, restarting every 16 rows (32 steps)
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+          const int32_t up = __shfl_up_sync(~0u, q[s], o);
+          if ((lane & 15) >= (uint32_t)o) q[s] += up;
+        }
+      }
+      if ((t0 & 31) == 0) ysum0 = ysum1 = 0;
+      const uint64_t base = ((uint64_t)org[1] + 32u * which + (t0 >> 1)) * nx + org[2] + lane;
+#pragma unroll
+      for (int s = 0; s < 8; s++) {
+        int32_t& ys = (s & 1) ? ysum1 : ysum0;
+        ys += q[s];
+        out.put(base + (uint64_t)(s >> 1) * nx + 32u * (s & 1), ys);
+      }
+    } else {
+      // plane t/8 of the stream's z chunk, rows 2s + lane/16, column lane%16: x sums
+      // over 8-lane groups, y sums across the lane pair (l, l^16) within each 8-row
+      // chunk, z sums in registers
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+          const int32_t up = __shfl_up_sync(~0u, q[s], o);
+          if ((lane & 7) >= (uint32_t)o) q[s] += up;
+        }
+      }
+      const uint32_t p = lane >> 4;
+      const uint32_t zp = t0 >> 3;
+      const uint64_t base = ((uint64_t)(org[0] + 8u * which + zp) * ny + org[1] + p) * nx + org[2] + (lane & 15);
+      int32_t pair = 0;
+#pragma unroll
+      for (int s = 0; s < 8; s++) {
+        const int32_t other = __shfl_xor_sync(~0u, q[s], 16);
+        if (s == 4) pair = 0;  // rows 8-15: the second y chunk
+        const int32_t k = zs[32 * s + lane] + pair + q[s] + (p ? other : 0);
+        zs[32 * s + lane] = k;
+        pair += q[s] + other;
+        out.put(base + (uint64_t)(2 * s) * nx, k);
+      }
+    }
+  }
+  *used = rd.cur;
+  const bool ok = !__any_sync(~0u, rd.bad || bad);
+  // verbatim patches of this stream's slots overwrite their elements (after the
+  // warp's own stores: __syncwarp orders them)
+  __syncwarp();
+  for (uint32_t i = rs + lane; i < re; i += 32) {
+    const uint2 kv = rec[i];
+    const uint32_t j = (kv.x >> 1) % kSlots;
+    if ((kv.x & 1u) && (j >> 11) == which) {
+      uint64_t e;
+      if (ND == 1) e = (uint64_t)org[2] + j;
+      else if (ND == 2) e = (uint64_t)(org[1] + (j >> 6)) * nx + org[2] + (j & 63);
+      else e = ((uint64_t)(org[0] + (j >> 8)) * ny + org[1] + ((j >> 4) & 15)) * nx + org[2] + (j & 15);
+      out.patch(e, kv.y);
+    }
+  }
+  return ok;
 }
 
 constexpr int kStreamWarps = kStreamWarpsPerCta;
 
 // Entropy decoding, persistent: each CTA stages the lookup tables of the books the
-// archive uses in shared memory once, then its warps take codec blocks from a ticket;
-// a warp decodes a Huffman block's code stream, or an RLE+Huffman block's value
-// stream and then its length stream (runs go to the workspace run arrays).
+// archive uses in shared memory once, then its warps take (block, stream) slots from
+// a ticket; a warp decodes one stream of a Huffman block, or the value or the length
+// stream of an RLE+Huffman block (runs go to the workspace run arrays).  With fusion
+// (ND != 0 and a.fuse), a stream of a full Huffman block is reconstructed by the
+// warp as it is decoded (fused_decode_reconstruct); other Huffman streams leave
+// their codes in the workspace for the reconstruction kernel.
 // Blocks come from the field's ticket (b_end == 0) or, in batches, warp i of the
 // CTA takes block b_begin + i if below b_end.
+template <int ND, typename E>
 __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32_t b_end) {
   extern __shared__ __align__(16) uint32_t s_luts[];  // the present books' tables
   __shared__ unsigned long long s_first[kMaxLen + 1], s_limit[kMaxLen + 1];
   __shared__ uint32_t s_off[kMaxLen + 1], s_count[kMaxLen + 1];
+  // fused streams: per warp a record table (32 words) and the 3-D running sums (256)
+  __shared__ uint32_t s_rectab[ND != 0 ? kStreamWarps * 288 : 1];
   __shared__ int s_go;
   if (a.dead) return;
   // the status is read once, by thread 0, and acted on after the staging barrier, so
@@ -386,7 +750,16 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
       }
       const uint32_t h = huff_split(m);
       const BookView bk{lut_code, s_first, s_limit, s_count, s_off, t->sorted, (int)t->maxlen, t->fullmask};
-      if (which == 0) {
+      if (ND != 0 && a.fuse && m == (uint32_t)kSlots) {
+        if (which == 0) {
+          ok = fused_decode_reconstruct<ND, E>(a, b, 0, u + 1, na, bk, &used, s_rectab + 288 * (threadIdx.x >> 5));
+          ok = ok && used == na;
+        } else {
+          ok = fused_decode_reconstruct<ND, E>(a, b, 1, u + 1 + na, nu - 1 - na, bk, &used,
+                                            s_rectab + 288 * (threadIdx.x >> 5));
+          ok = ok && ((2ull * (1ull + na + used) + 3) & ~3ull) == bytes;
+        }
+      } else if (which == 0) {
         ok = ihs_decode_warp(u + 1, na, h, bk, a.codes + (uint64_t)b * kSlots, 0, &used);
         ok = ok && used == na;
       } else {
@@ -424,8 +797,9 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
   }
 }
 
-__global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_kernel(DecodeArgs a) {
-  stream_decode_body(a, 0, 0);
+template <int ND, typename E>
+__global__ __launch_bounds__(32 * kStreamWarps, 2) void stream_decode_kernel(DecodeArgs a) {
+  stream_decode_body<ND, E>(a, 0, 0);
 }
 
 constexpr int kRleThreads = 256;
@@ -564,10 +938,8 @@ __global__ __launch_bounds__(kRleThreads) void rle_expand_kernel(DecodeArgs a) {
 // =================================================================================
 constexpr int kRecThreads = 256;
 
-__device__ __forceinline__ float scale(int32_t k, float ebx2) { return __fmul_rn(__int2float_rn(k), ebx2); }
-
 // codes: the block's 4096 code slots (global memory, or a shared-memory copy)
-template <int ND>
+template <int ND, typename E>
 __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, const uint16_t* codes) {
   // (the caller has checked the field's status, the same way in every thread)
   const int tid = threadIdx.x;
@@ -575,7 +947,7 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, 
   block_box(a.g, b, org, w);
   const uint32_t m = w[0] * w[1] * w[2];
   const int32_t r = (int32_t)a.radius;
-  const float ebx2 = a.ebx2_f;
+  const Out<E> out(a);
   const uint32_t rs = a.rec_start[b], re = a.rec_start[b + 1];
   const uint2* rec = reinterpret_cast<const uint2*>(a.ar + a.off_rec);
   // a full 3-D block without records reads its codes directly; otherwise
@@ -600,7 +972,6 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, 
     __syncthreads();
   }
   const uint64_t ny = a.g.n[1], nx = a.g.n[2];
-  float* __restrict__ out = a.out;
   if (ND == 1) {
     // each warp scans whole 256-chunks, 32 elements per step
     const int lane = tid & 31, wid = tid >> 5;
@@ -612,7 +983,7 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, 
         const int32_t v = j < m ? s_q[j] : 0;
         const int32_t inc = warp_incl_scan(v) + carry;
         carry = __shfl_sync(~0u, inc, 31);
-        if (j < m) __stcs(&out[(uint64_t)org[2] + j], scale(inc, ebx2));
+        if (j < m) out.put((uint64_t)org[2] + j, inc);
       }
     }
   } else if (ND == 2) {
@@ -640,7 +1011,7 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, 
 #pragma unroll
       for (int i = 0; i < 16; i++) {
         const uint32_t y = ry * 16 + i;
-        if (y < w[1]) __stcs(&out[base + (uint64_t)y * nx], scale(v[i], ebx2));
+        if (y < w[1]) out.put(base + (uint64_t)y * nx, v[i]);
       }
     }
   } else if (m == (uint32_t)kSlots) {
@@ -676,7 +1047,7 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, 
       if (i & 7) v[i] += v[i - 1];
     const uint64_t base = ((uint64_t)(org[0] + z) * ny + org[1]) * nx + org[2] + x;
 #pragma unroll
-    for (int i = 0; i < 16; i++) __stcs(&out[base + (uint64_t)i * nx], scale(v[i], ebx2));
+    for (int i = 0; i < 16; i++) out.put(base + (uint64_t)i * nx, v[i]);
   } else {
     // edge block: z sums in registers, x sums by shuffles, y sums through shared
     // memory
@@ -716,7 +1087,7 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, 
     for (uint32_t j = tid; j < m; j += kRecThreads) {
       const uint32_t p = w[1] * w[2];
       const uint32_t zz = j / p, rem = j - zz * p, yy = rem / w[2], xx = rem - yy * w[2];
-      __stcs(&out[((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx], scale(s_q[j], ebx2));
+      out.put(((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx, s_q[j]);
     }
   }
   __syncthreads();
@@ -727,14 +1098,16 @@ __device__ void reconstruct_body(const DecodeArgs& a, uint32_t b, int32_t* s_q, 
       const uint32_t j = (kv.x >> 1) % kSlots;
       const uint32_t p = w[1] * w[2];
       const uint32_t zz = j / p, rem = j - zz * p, yy = rem / w[2], xx = rem - yy * w[2];
-      out[((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx] = __uint_as_float(kv.y);
+      out.patch(((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx, kv.y);
     }
   }
 }
 
-// Persistent: CTA c takes blocks c, c + grid, ...; while it reconstructs one, a bulk
-// copy is already bringing the next block's 8 KB of codes into shared memory.
-template <int ND>
+// Persistent: CTA c takes work items c, c + grid, ...; while it reconstructs one
+// block, a bulk copy is already bringing the next block's 8 KB of codes into shared
+// memory.  The work items are all blocks, or, when the entropy decoder reconstructs
+// full Huffman blocks itself (a.fuse), the listed other blocks.
+template <int ND, typename E>
 __global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) {
   __shared__ __align__(128) uint16_t s_codes[2][kSlots];
   __shared__ __align__(16) int32_t s_q[kSlots];
@@ -743,6 +1116,8 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) 
   if (a.dead || (a.st->status & ERR_CORRUPT)) return;
   const int tid = threadIdx.x;
   const uint32_t grid = gridDim.x;
+  const uint32_t nwork = a.fuse ? a.st->n_slow : a.g.nblk;
+  auto block_of = [&](uint32_t i) -> uint32_t { return a.fuse ? a.slowblk[i] : i; };
   auto issue = [&](uint32_t b, int buf) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&s_bar[buf], kSlots * 2);
@@ -753,22 +1128,23 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) 
     mbar_init(&s_bar[1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
-    if (blockIdx.x < a.g.nblk) issue(blockIdx.x, 0);
+    if (blockIdx.x < nwork) issue(block_of(blockIdx.x), 0);
   }
   __syncthreads();
-  uint32_t it = 0, b = blockIdx.x;
+  uint32_t it = 0, i = blockIdx.x;
   bool next_issued = false;
-  for (; b < a.g.nblk; b += grid, it++) {
+  for (; i < nwork; i += grid, it++) {
     const int cur = it & 1;
-    next_issued = b + grid < a.g.nblk;
-    if (tid == 0 && next_issued) issue(b + grid, cur ^ 1);
+    const uint32_t b = block_of(i);
+    next_issued = i + grid < nwork;
+    if (tid == 0 && next_issued) issue(block_of(i + grid), cur ^ 1);
     if (!mbar_wait(&s_bar[cur], (it >> 1) & 1u, kSpinLimit)) {
       atomicOr(&a.st->status, ERR_TIMEOUT);
       s_fail = 1;
     }
     __syncthreads();
     if (s_fail) break;
-    reconstruct_body<ND>(a, b, s_q, s_codes[cur]);
+    reconstruct_body<ND, E>(a, b, s_q, s_codes[cur]);
     __syncthreads();
   }
   if (s_fail && tid == 0) {
@@ -776,6 +1152,250 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_kernel(DecodeArgs a) 
     mbar_wait(&s_bar[it & 1], (it >> 1) & 1u, kSpinLimit);
     if (next_issued) mbar_wait(&s_bar[(it + 1) & 1], ((it + 1) >> 1) & 1u, kSpinLimit);
   }
+}
+
+// =================================================================================
+// global (unchunked) Lorenzo reconstruction: the N-D partial sum of q' over the whole
+// field (Sec. IV-B "Partial-Sum Lorenzo Reconstruction" holds without chunks), as
+// one pass per axis over an int32 copy of q' kept in the output buffer; the last pass
+// scales to FP32 in place, then the verbatim patches are written.
+// =================================================================================
+constexpr uint32_t kScanTile = 4096;  // elements per tile of the x pass (256 threads x 16)
+
+// q' of codec block b (q - r, or the outlier's delta) at its elements' field positions.
+__global__ __launch_bounds__(kRecThreads) void gfuse_kernel(DecodeArgs a) {
+  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
+  const uint32_t b = blockIdx.x;
+  uint32_t org[3], w[3];
+  block_box(a.g, b, org, w);
+  const uint32_t m = w[0] * w[1] * w[2];
+  const int32_t r = (int32_t)a.radius;
+  int32_t* q = reinterpret_cast<int32_t*>(a.out);
+  const uint16_t* codes = a.codes + (uint64_t)b * kSlots;
+  const uint64_t ny = a.g.n[1], nx = a.g.n[2];
+  auto elem = [&](uint32_t j) -> uint64_t {
+    const uint32_t pl = w[1] * w[2], zz = j / pl, rr = j - zz * pl, yy = rr / w[2], xx = rr - yy * w[2];
+    return ((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx;
+  };
+  for (uint32_t j = threadIdx.x; j < m; j += kRecThreads) q[elem(j)] = (int32_t)codes[j] - r;
+  __syncthreads();  // orders the outliers' writes after the codes' writes
+  const uint2* rec = reinterpret_cast<const uint2*>(a.ar + a.off_rec);
+  for (uint32_t i = a.rec_start[b] + threadIdx.x; i < a.rec_start[b + 1]; i += kRecThreads) {
+    const uint2 kv = rec[i];
+    if ((kv.x & 1u) == 0) q[elem((kv.x >> 1) % kSlots)] = (int32_t)kv.y;
+  }
+}
+
+// Exclusive prefix, for a segmented scan, of the tiles before `tile`: the aggregates
+// back to the nearest tile that published an inclusive value (a tile holding a segment
+// start), summed modulo 2^62 and read back as a signed value.  One full warp calls;
+// the wait is bounded (ERR_TIMEOUT and 0 on expiry).
+__device__ int64_t seg_lookback_warp(const uint64_t* state, uint32_t tile, uint32_t* status, uint32_t spin_limit) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) return 0;
+  uint64_t excl = 0;
+  int64_t base = (int64_t)tile - 1;
+  uint32_t spins = 0;
+  while (true) {
+    const int64_t idx = base - lane;
+    const uint64_t v = idx >= 0 ? ld_relaxed(&state[idx]) : LB_INC;
+    const uint32_t inc = __ballot_sync(~0u, (v & LB_INC) != 0);
+    const uint32_t bad = __ballot_sync(~0u, (v & (LB_INC | LB_AGG)) == 0);
+    const int first = inc ? __ffs(inc) : 32;
+    const uint32_t upto = first >= 32 ? ~0u : ((1u << first) - 1u);
+    if (bad & upto) {
+      if (++spins > spin_limit) {
+        if (lane == 0) atomicOr(status, ERR_TIMEOUT);
+        return 0;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    const uint64_t add = warp_sum(((1u << lane) & upto) ? (v & LB_VAL) : 0ull);
+    excl = (excl + add) & LB_VAL;
+    if (inc) break;
+    base -= 32;
+  }
+  return (int64_t)(excl << 2) >> 2;
+}
+
+__device__ __forceinline__ void seg_publish(uint64_t* state, uint32_t tile, bool inclusive, int64_t v) {
+  st_relaxed(&state[tile], (inclusive ? LB_INC : LB_AGG) | ((uint64_t)v & LB_VAL));
+}
+
+// Pass along x: an inclusive scan of the flattened field restarted at every row start
+// (a segment of n[2] elements), one tile of 4096 elements per CTA in ticket order;
+// tiles chain their carries by decoupled look-back.  `last`: scale to FP32 in place.
+__global__ __launch_bounds__(256) void gscan_x_kernel(DecodeArgs a, uint64_t* state, int last) {
+  __shared__ uint32_t s_tile;
+  __shared__ int s_go;
+  __shared__ int s_wf[8];
+  __shared__ int32_t s_ws[8];
+  __shared__ int32_t s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    s_go = !(a.st->status & ERR_CORRUPT);
+    s_tile = atomicAdd(&a.st->ticket_construct, 1u);
+  }
+  __syncthreads();
+  if (!s_go) return;  // every CTA leaves: no tile waits on another
+  const uint32_t tile = s_tile;
+  const uint64_t n = a.g.nelem, seg = a.g.n[2];
+  int32_t* q = reinterpret_cast<int32_t*>(a.out);
+  const uint64_t base = (uint64_t)tile * kScanTile + 16u * tid;
+  int32_t v[16];
+  uint32_t heads = 0;
+  uint64_t rpos = base % seg;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    const uint64_t idx = base + i;
+    v[i] = idx < n ? q[idx] : 0;
+    if (idx < n && rpos == 0) heads |= 1u << i;
+    rpos = rpos + 1 == seg ? 0 : rpos + 1;
+  }
+  // the thread's own segmented inclusive scan, and its pair (head seen, sum since it)
+  bool f = false;
+  int32_t run = 0;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    if ((heads >> i) & 1u) {
+      run = v[i];
+      f = true;
+    } else {
+      run += v[i];
+    }
+    v[i] = run;
+  }
+  // warp scan of the pairs (combine a then b: (fa | fb, fb ? sb : sa + sb))
+  bool F = f;
+  int32_t S = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const bool fu = __shfl_up_sync(~0u, (int)F, o) != 0;
+    const int32_t su = __shfl_up_sync(~0u, S, o);
+    if (lane >= o) {
+      if (!F) S += su;
+      F = F || fu;
+    }
+  }
+  bool Fe = __shfl_up_sync(~0u, (int)F, 1) != 0;
+  int32_t Se = __shfl_up_sync(~0u, S, 1);
+  if (lane == 0) {
+    Fe = false;
+    Se = 0;
+  }
+  if (lane == 31) {
+    s_wf[wid] = F;
+    s_ws[wid] = S;
+  }
+  __syncthreads();
+  bool Fw = false;
+  int32_t Sw = 0;
+  for (int ww = 0; ww < wid; ww++) {
+    Sw = s_wf[ww] ? s_ws[ww] : Sw + s_ws[ww];
+    Fw = Fw || s_wf[ww];
+  }
+  const bool Ft = Fw || Fe;               // a segment starts before this thread, in the tile
+  const int32_t St = Fe ? Se : Sw + Se;   // and the sum since the latest such start
+  if (wid == 0) {
+    bool TF = false;
+    int32_t TS = 0;
+    for (int ww = 0; ww < 8; ww++) {
+      TS = s_wf[ww] ? s_ws[ww] : TS + s_ws[ww];
+      TF = TF || s_wf[ww];
+    }
+    if (lane == 0) seg_publish(state, tile, TF, TS);  // a tile with a segment start needs no carry
+    int64_t c = 0;
+    if ((uint64_t)tile * kScanTile % seg != 0) c = seg_lookback_warp(state, tile, &a.st->status, kSpinLimit);
+    if (lane == 0) {
+      if (!TF) seg_publish(state, tile, true, c + TS);
+      s_carry = (int32_t)c;
+    }
+  }
+  __syncthreads();
+  const int32_t pre = Ft ? St : s_carry + St;  // what precedes the thread's first element
+  const float ebx2 = a.ebx2_f;
+  float* out = a.out;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    const uint64_t idx = base + i;
+    // elements before the thread's first head add what precedes the thread
+    const bool own = (heads & ((2u << i) - 1u)) != 0;
+    const int32_t k = own ? v[i] : pre + v[i];
+    if (idx < n) {
+      if (last) out[idx] = scale(k, ebx2);
+      else q[idx] = k;
+    }
+  }
+}
+
+// Pass along y (or z): thread (outer, x) runs down its column; `last`: scale in place.
+__global__ __launch_bounds__(256) void gscan_col_kernel(DecodeArgs a, int axis, int last) {
+  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
+  const uint64_t nz = a.g.n[0], ny = a.g.n[1], nx = a.g.n[2];
+  // axis 1 (y): columns (z, x), stride nx, length ny; axis 0 (z): columns (y, x), stride ny nx, length nz
+  const uint64_t ncol = axis == 1 ? nz * nx : ny * nx;
+  const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  const uint64_t stride = axis == 1 ? nx : ny * nx, len = axis == 1 ? ny : nz;
+  const uint64_t start = axis == 1 ? (c / nx) * ny * nx + c % nx : c;
+  int32_t* q = reinterpret_cast<int32_t*>(a.out);
+  float* out = a.out;
+  const float ebx2 = a.ebx2_f;
+  int32_t acc = 0;
+  uint64_t i = 0;
+  for (; i + 4 <= len; i += 4) {
+    int32_t t[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) t[u] = q[start + (i + u) * stride];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      acc += t[u];
+      if (last) out[start + (i + u) * stride] = scale(acc, ebx2);
+      else q[start + (i + u) * stride] = acc;
+    }
+  }
+  for (; i < len; i++) {
+    acc += q[start + i * stride];
+    if (last) out[start + i * stride] = scale(acc, ebx2);
+    else q[start + i * stride] = acc;
+  }
+}
+
+// Verbatim patches (after the last pass).
+__global__ void gpatch_kernel(DecodeArgs a) {
+  if (a.dead || (a.st->status & ERR_CORRUPT)) return;
+  const uint2* rec = reinterpret_cast<const uint2*>(a.ar + a.off_rec);
+  const uint64_t ny = a.g.n[1], nx = a.g.n[2];
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n_rec; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint2 kv = rec[i];
+    if ((kv.x & 1u) == 0) continue;
+    const uint32_t slot = kv.x >> 1, b = slot / kSlots, j = slot % kSlots;
+    uint32_t org[3], w[3];
+    block_box(a.g, b, org, w);
+    const uint32_t pl = w[1] * w[2], zz = j / pl, rr = j - zz * pl, yy = rr / w[2], xx = rr - yy * w[2];
+    a.out[((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx] = __uint_as_float(kv.y);
+  }
+}
+
+// The global reconstruction's launches (after set-up, decoding and run expansion).
+cudaError_t launch_global_reconstruct(const DecodeArgs& a, cudaStream_t s) {
+  trace_begin(K_RECONSTRUCT, s);
+  gfuse_kernel<<<a.g.nblk, kRecThreads, 0, s>>>(a);
+  const int nd = a.g.ndim;
+  const uint64_t ntiles = (a.g.nelem + kScanTile - 1) / kScanTile;
+  gscan_x_kernel<<<(unsigned)ntiles, 256, 0, s>>>(a, a.scan_state, nd == 1 ? 1 : 0);
+  if (nd >= 2) {
+    const uint64_t cy = (uint64_t)a.g.n[0] * a.g.n[2];
+    gscan_col_kernel<<<(unsigned)((cy + 255) / 256), 256, 0, s>>>(a, 1, nd == 2 ? 1 : 0);
+  }
+  if (nd == 3) {
+    const uint64_t cz = (uint64_t)a.g.n[1] * a.g.n[2];
+    gscan_col_kernel<<<(unsigned)((cz + 255) / 256), 256, 0, s>>>(a, 0, 1);
+  }
+  if (a.n_rec) gpatch_kernel<<<(unsigned)((a.n_rec + 255) / 256 < 1024 ? (a.n_rec + 255) / 256 : 1024), 256, 0, s>>>(a);
+  trace_end(K_RECONSTRUCT, s);
+  return cudaGetLastError();
 }
 
 // =================================================================================
@@ -875,7 +1495,7 @@ __global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_batch_kernel(
   const DecodeArgs& a = tasks[f];
   const uint32_t b0 = (blockIdx.x - chunk0[f]) * (kStreamWarps / 2);
   const uint32_t b1 = min(a.g.nblk, b0 + kStreamWarps / 2);
-  stream_decode_body(a, b0, b1);
+  stream_decode_body<0, float>(a, b0, b1);
 }
 
 // Reconstruction of a batch, one CTA per codec block of every field.  A run block's
@@ -906,9 +1526,9 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_batch_kernel(const De
     __syncthreads();
     codes = s_codes;
   }
-  if (a.g.ndim == 1) reconstruct_body<1>(a, b, s_q, codes);
-  else if (a.g.ndim == 2) reconstruct_body<2>(a, b, s_q, codes);
-  else reconstruct_body<3>(a, b, s_q, codes);
+  if (a.g.ndim == 1) reconstruct_body<1, float>(a, b, s_q, codes);
+  else if (a.g.ndim == 2) reconstruct_body<2, float>(a, b, s_q, codes);
+  else reconstruct_body<3, float>(a, b, s_q, codes);
 }
 
 cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
@@ -966,33 +1586,32 @@ cudaError_t launch_dec_status(const DevState* st, uint32_t* d_status, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
-  const uint64_t n = (a.n_rec > (uint64_t)a.g.nblk + 1 ? a.n_rec : (uint64_t)a.g.nblk + 1);
-  uint64_t rec_ctas = (n + 1023) / 1024;
-  if (rec_ctas > 1024) rec_ctas = 1024;
-  trace_begin(K_DEC_SETUP, s);
-  dec_setup_kernel<<<(unsigned)(4 + rec_ctas), 1024, 0, s>>>(a);
-  trace_end(K_DEC_SETUP, s);
+// The entropy decoding and reconstruction launches of one field, for element type E.
+template <typename E>
+cudaError_t launch_decode_stages(const DecodeArgs& a, cudaStream_t s) {
+  const int nd = a.g.ndim;
   const int nluts = ((a.flags & 1u) ? 1 : 0) + ((a.flags & 2u) ? 2 : 0);
   if (nluts) {
     const size_t lut_bytes = (size_t)nluts * (1u << kLutBits) * sizeof(uint32_t);
-    static int sms = 0, occ[4] = {0, 0, 0, 0};
+    static int sms = 0, occ[4][4] = {};
+    auto k = nd == 1 ? stream_decode_kernel<1, E> : (nd == 2 ? stream_decode_kernel<2, E> : stream_decode_kernel<3, E>);
     if (sms == 0) {
       int dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaFuncSetAttribute(stream_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(3 * (1u << kLutBits) * sizeof(uint32_t)));
+      for (auto kk : {stream_decode_kernel<1, E>, stream_decode_kernel<2, E>, stream_decode_kernel<3, E>})
+        cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(3 * (1u << kLutBits) * sizeof(uint32_t)));
     }
-    if (occ[nluts] == 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[nluts], stream_decode_kernel, 32 * kStreamWarps, lut_bytes);
-      if (occ[nluts] <= 0) occ[nluts] = 1;
+    if (occ[nd][nluts] == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[nd][nluts], k, 32 * kStreamWarps, lut_bytes);
+      if (occ[nd][nluts] <= 0) occ[nd][nluts] = 1;
     }
     const uint64_t want = (2ull * a.g.nblk + kStreamWarps - 1) / kStreamWarps;
-    const uint64_t cap = (uint64_t)sms * occ[nluts];
+    const uint64_t cap = (uint64_t)sms * occ[nd][nluts];
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     trace_begin(K_STREAM_DECODE, s);
-    stream_decode_kernel<<<grid, 32 * kStreamWarps, lut_bytes, s>>>(a);
+    k<<<grid, 32 * kStreamWarps, lut_bytes, s>>>(a);
     trace_end(K_STREAM_DECODE, s);
   }
   if (a.n_codec[CODEC_RLE] + a.n_codec[CODEC_RLE_HUFF]) {  // run blocks present
@@ -1000,26 +1619,50 @@ cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
     rle_expand_kernel<<<a.n_codec[CODEC_RLE] + a.n_codec[CODEC_RLE_HUFF], kRleThreads, 0, s>>>(a);
     trace_end(K_RLE_EXPAND, s);
   }
-  {
+  if (a.global) return launch_global_reconstruct(a, s);
+  // blocks left to the reconstruction kernel: with fusion at most the edge blocks and
+  // the run blocks (the header's counts, which the set-up checks); none, and the launch
+  // is skipped
+  uint64_t work = a.g.nblk;
+  if (a.fuse) {
+    uint64_t full = 1;
+    for (int d = 0; d < 3; d++) full *= a.g.n[d] / a.g.blk[d];
+    work = (a.g.nblk - full) + a.n_codec[CODEC_RLE] + a.n_codec[CODEC_RLE_HUFF];
+    if (work > a.g.nblk) work = a.g.nblk;
+  }
+  if (work) {
     static int sms = 0, occ[4] = {0, 0, 0, 0};
-    auto k = a.g.ndim == 1 ? reconstruct_kernel<1> : (a.g.ndim == 2 ? reconstruct_kernel<2> : reconstruct_kernel<3>);
+    auto k = nd == 1 ? reconstruct_kernel<1, E> : (nd == 2 ? reconstruct_kernel<2, E> : reconstruct_kernel<3, E>);
     if (sms == 0) {
       int dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    if (occ[a.g.ndim] == 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[a.g.ndim], k, kRecThreads, 0);
-      if (occ[a.g.ndim] <= 0) occ[a.g.ndim] = 1;
+    if (occ[nd] == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[nd], k, kRecThreads, 0);
+      if (occ[nd] <= 0) occ[nd] = 1;
     }
     // persistent only when every CTA gets several blocks to prefetch
-    const uint64_t cap = (uint64_t)sms * occ[a.g.ndim];
-    const unsigned grid = (unsigned)(a.g.nblk <= 3 * cap ? a.g.nblk : cap);
+    const uint64_t cap = (uint64_t)sms * occ[nd];
+    const unsigned grid = (unsigned)(work <= 3 * cap ? work : cap);
     trace_begin(K_RECONSTRUCT, s);
     k<<<grid, kRecThreads, 0, s>>>(a);
     trace_end(K_RECONSTRUCT, s);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s) {
+  const uint64_t n = (a.n_rec > (uint64_t)a.g.nblk + 1 ? a.n_rec : (uint64_t)a.g.nblk + 1);
+  uint64_t rec_ctas = (n + 1023) / 1024;
+  if (rec_ctas > 1024) rec_ctas = 1024;
+  const uint32_t nchunks = (a.g.nblk + 1023) / 1024;
+  trace_begin(K_DEC_SETUP, s);
+  dec_setup_kernel<<<(unsigned)(nchunks + 3 + rec_ctas), 1024, 0, s>>>(a, nchunks);
+  trace_end(K_DEC_SETUP, s);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return a.f64 ? launch_decode_stages<double>(a, s) : launch_decode_stages<float>(a, s);
 }
 
 }  // namespace cszp

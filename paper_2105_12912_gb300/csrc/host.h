@@ -39,14 +39,16 @@ inline bool make_geom(int ndim, const uint64_t* dims, Geom& g) {
   return true;
 }
 
-// Workspace: [DevState | histograms | look-back states] (zeroed per compression),
-// books, decode tables and offsets, block-major code stream, decoded run lengths
+// Workspace: [DevState | set-up look-back states | histograms | look-back states]
+// (zeroed per compression; decompression zeroes the first two),
+// books, decode tables and offsets, block-major code stream, decoded run lengths,
+// the lists of run blocks and of blocks reconstructed apart from their decoding
 // (the part decompression needs ends at dec_total), then compression-only scratch:
 // per-block record counts, patch / outlier bit masks, outlier residuals and record
 // offsets.
 struct Layout {
-  uint64_t st, hist_code, hist_val, hist_len, lb_e, zero_end;
-  uint64_t lens, bcodes, blk_off, rec_start, tabs, codes, runl, runblk, dec_total;
+  uint64_t st, prep_lb, hist_code, hist_val, hist_len, lb_e, zero_end;
+  uint64_t lens, bcodes, blk_off, rec_start, tabs, codes, runl, runblk, slowblk, dec_total;
   uint64_t counts, masks, deltas, rec_off, runs, total;
 };
 
@@ -55,6 +57,8 @@ inline Layout layout(const Geom& g) {
   uint64_t o = 0;
   L.st = o;
   o += a256(sizeof(DevState));
+  L.prep_lb = o;  // decompression set-up: two look-back states per 1024 blocks
+  o += a256(16ull * ((g.nblk + 1023) / 1024));
   L.hist_code = o;
   o += kNsymCode * 4;
   L.hist_val = o;
@@ -80,6 +84,8 @@ inline Layout layout(const Geom& g) {
   L.runl = o;
   o += a256(2ull * kSlots * g.nblk);
   L.runblk = o;
+  o += a256(4ull * g.nblk);
+  L.slowblk = o;
   o += a256(4ull * g.nblk);
   L.dec_total = o;
   L.counts = o;

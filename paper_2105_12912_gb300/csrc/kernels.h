@@ -12,6 +12,7 @@ namespace cszp {
 
 struct ConstructArgs {
   const float* x;
+  const double* x64;   // double-precision field (x is null then)
   Geom g;
   DevState* st;
   uint32_t radius;
@@ -25,6 +26,7 @@ struct ConstructArgs {
   uint16_t* block_runs;  // [nblk] runs of equal codes in each block
   uint32_t spin_limit;
   int all_runs;        // every block's runs feed the run books (forced run codecs)
+  int global;          // global (unchunked) Lorenzo: halo'd tiles (single-field launches)
 };
 
 // Value range / error bound of one field of a batch.
@@ -72,6 +74,8 @@ struct BookArgs {
 
 struct FinalizeArgs {
   DevState* st;
+  int f64;     // double-precision field
+  int global;  // global (unchunked) Lorenzo
   uint8_t* ar;
   uint64_t cap;
   int ndim, eb_mode;
@@ -141,7 +145,16 @@ struct DecodeArgs {
   uint16_t* runv;      // decoded run values of RLE+Huffman blocks (may alias codes)
   uint16_t* runl;      // nblk * 4096 decoded run lengths
   uint32_t* runblk;    // indices of the RLE / RLE+Huffman blocks, ascending (null: not listed)
+  uint32_t* slowblk;   // fused decoding: blocks the entropy decoder does not reconstruct
+                       // itself (not Huffman, or not of full block extent), ascending
+  int fuse;            // full Huffman blocks are reconstructed by the warps that decode them
   float* out;
+  double* out64;       // double-precision archives (f64): the output, and the step
+  double step_d;
+  int f64;
+  uint64_t* prep_lb;   // set-up chunks' look-back states (2 per 1024 blocks), zeroed per call
+  int global;          // global (unchunked) Lorenzo archive: reconstruction by per-axis passes
+  uint64_t* scan_state;  // their look-back states (one per 4096 elements), zeroed per call
   int dead;            // batches: the header failed validation, do nothing
   int check_hdr;       // the arguments come from a host copy of the header (hdr): the
   uint32_t hdr[32];    // set-up compares the device archive's header with it
@@ -177,6 +190,8 @@ void trace_count_decode_batch();  // the same for a decompression batch graph
 // ---- launchers (return cudaGetLastError of the launch) ---------------------------
 cudaError_t launch_abs_params(DevState* st, double eb, cudaStream_t s);
 cudaError_t launch_range(const float* x, uint64_t n, DevState* st, int mode, double eb, cudaStream_t s);
+// double-precision fields: value range (REL) or the bound alone (ABS), and the step
+cudaError_t launch_range_d(const double* x, uint64_t n, DevState* st, int mode, double eb, cudaStream_t s);
 void prepare_construct_task(ConstructTask& t);  // tensor map when TMA applies
 size_t construct_smem_bytes();
 int construct_grid(uint32_t ntiles);  // persistent grid: all resident CTAs, at most ntiles

@@ -234,3 +234,39 @@ def test_batch_of_one_dimensionality(gpu, nd):
         st, ref = _single(gpu, x, 1e-3, "rel")
         assert stats[i] == 0 and st == 0
         assert np.array_equal(bc.archives[i][:sizes[i]].cpu().numpy(), ref), i
+
+
+def test_batch256_matches_single_field_calls_and_oracle(gpu, orc):
+    """The real mixed batch (256 fields, seeds 100-355, 2.65e9 elements, 10.6 GB): every
+    archive of the batched path equals the single-field call's byte for byte, and the
+    largest 1-D, 2-D and 3-D fields equal the oracle's archives, with reconstructions
+    bit-identical to the oracle's recurrence."""
+    from paper_2105_12912_gb300 import synth
+    specs = synth.workload_batch(256)
+    xs = [synth.make_field(sp, "cuda") for sp in specs]
+    caps = [min(gpu.max_archive_bytes(tuple(x.shape)), 6 * x.numel() + (1 << 20)) for x in xs]
+    bc = gpu.BatchCompressor(xs, [sp.eb for sp in specs], [sp.eb_mode for sp in specs], archive_caps=caps)
+    bc.run()
+    sizes, stats = bc.results()
+    assert all(s == 0 for s in stats), stats
+    ws = gpu.Workspace(xs[0].device)
+    arc = torch.empty(max(caps), dtype=torch.uint8, device="cuda")
+    for i, (x, sp) in enumerate(zip(xs, specs)):
+        ar, nb, _ = gpu.compress(x, sp.eb, sp.eb_mode, out=arc[:caps[i]], workspace=ws)
+        assert nb == sizes[i], i
+        assert torch.equal(ar[:nb], bc.archives[i][:nb]), i
+    del arc, ws
+    largest = {}
+    for i, x in enumerate(xs):
+        nd = x.dim()
+        if nd not in largest or x.numel() > xs[largest[nd]].numel():
+            largest[nd] = i
+    for nd, i in sorted(largest.items()):
+        xh = xs[i].cpu().numpy()
+        sp = specs[i]
+        st, ref = orc.compress(xh, orc.EB_REL, sp.eb)
+        assert st == 0
+        assert ref.size == sizes[i] and np.array_equal(bc.archives[i][:sizes[i]].cpu().numpy(), ref), (nd, i)
+        y, _ = gpu.decompress(bc.archives[i], sizes[i])
+        st, yr = orc.decompress(ref, xh.size)
+        assert np.array_equal(y.cpu().numpy().ravel().view(np.uint32), yr.view(np.uint32)), (nd, i)

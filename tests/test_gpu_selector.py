@@ -137,3 +137,33 @@ def test_training_gains_over_heuristic(gpu):
     assert l1 < l0
     assert rep["bytes"]["learned"] < rep["bytes"]["heuristic"], rep
     assert rep["regret_vs_exhaustive"] <= 0.01, rep
+
+
+def test_fullsize_selector_workload(gpu, orc):
+    """The learned-selector configuration at full size: 3-D 100x500x500 GRF k^-3 fields
+    with 0-60% zero 16^3 blocks, rel eb 1e-3; trained on the method's own sizes from
+    64 fields (seeds 1000-1063), evaluated on 16 held-out fields (seeds 2000-2015).
+    LEARNED archives of two held-out fields are byte-identical to the oracle's; over
+    all 16 the size regret against exhaustive selection is at most 1% and the archives
+    are smaller than the paper's heuristic's."""
+    from paper_2105_12912_gb300 import selector, synth
+
+    def fields(seeds):
+        return [(lambda s=s: synth.make_field(synth.workload_selector(s), "cuda"), 1e-3, "rel") for s in seeds]
+    rows = selector.collect_rows(fields(range(1000, 1064)))
+    assert rows["feat"].shape[0] == 64 * 7 * 32 * 32
+    w, l0, l1 = selector.train(rows, seed=0, steps=3000, lr=1e-2)
+    assert l1 < 0.5 * l0
+    del rows
+    for s in (2000, 2007):
+        xh = synth.make_field(synth.workload_selector(s), "cpu")
+        ar, nb, _ = gpu.compress(xh.cuda(), 1e-3, "rel", select="learned", weights=w)
+        st, ref = orc.compress(xh.numpy(), orc.EB_REL, 1e-3, select=orc.SEL_LEARNED, mlp_w=w.cpu().numpy())
+        assert st == 0
+        assert ref.size == nb and np.array_equal(ar[:nb].cpu().numpy(), ref), s
+        y, _ = gpu.decompress(ar, nb)
+        st, yr = orc.decompress(ref, xh.numel())
+        assert np.array_equal(y.cpu().numpy().ravel().view(np.uint32), yr.view(np.uint32)), s
+    rep = selector.evaluate(w, fields(range(2000, 2016)))
+    assert rep["regret_vs_exhaustive"] <= 0.01, rep
+    assert rep["bytes"]["learned"] < rep["bytes"]["heuristic"], rep

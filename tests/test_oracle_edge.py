@@ -78,7 +78,7 @@ def test_truncated_archives_rejected(orc):
 
 def test_header_damage_rejected(orc):
     for x, ar in _archives(orc):
-        for off, val in [(0, 0x00), (4, 9), (6, 4), (7, 5), (52, 0), (56, 7), (60, 9), (64, 3)]:
+        for off, val in [(0, 0x00), (4, 9), (6, 4), (7, 5), (52, 0), (56, 7), (60, 16), (64, 3)]:
             bad = ar.copy()
             bad[off] = val
             st, _ = orc.decompress(bad, x.size, raise_on_error=False)

@@ -407,7 +407,10 @@ def test_features_special_cases(orc):
     assert abs(f[1] - (-(p * np.log2(p)).sum())) < 1e-3
 
 
-MADO_DISTANCES = [1, 26, 51, 76, 101, 126, 151, 176]  # every 25th distance of 1..200 (Sec. III-B)
+def _mado_d(i):
+    """Madogram pair distance of position i: 1, 26, ..., 176 (every 25th distance of
+    the paper's 1..200, Sec. III-B) by i mod 8."""
+    return 1 + 25 * (i % 8)
 
 
 def _hand_block(r=512):
@@ -438,8 +441,9 @@ def test_features_hand_computed_block(orc):
     counts = {}
     for v in c:
         counts[v] = counts.get(v, 0) + 1
-    mism = sum(1 for d in MADO_DISTANCES for i in range(m - d) if c[i] != c[i + d])
-    pairs = sum(m - d for d in MADO_DISTANCES)
+    pairs = [i for i in range(m) if i + _mado_d(i) < m]
+    mism = sum(1 for i in pairs if c[i] != c[i + _mado_d(i)])
+    pairs = len(pairs)
     assert f[0] == np.float32(zero) / np.float32(m)
     assert f[2] == np.float32(max(counts.values())) / np.float32(m)
     assert max(counts, key=counts.get) == r  # the zero residual is the top code
@@ -453,24 +457,26 @@ def test_features_hand_computed_block(orc):
 
 
 def test_features_closed_forms(orc):
-    """Closed forms: a pure period-8 block changes code at every sampled distance but
-    176 (a multiple of 8); a block that is one code repeated never changes; a block
-    shorter than a distance has no pairs at that distance; log2(1 + max|delta|) is 0
-    for all-zero residuals and log2(5) for max |delta| = 4."""
+    """Closed forms: in a pure period-8 block every sampled pair differs except those
+    at distance 176 (a multiple of 8, taken by positions 7 mod 8): 7/8 of the pairs,
+    whose count is 4096 - 8 = 4088 less the tail of each distance class; a block
+    shorter than a distance has no pairs at it; log2(1 + max|delta|) is log2(5) for
+    max |delta| = 4."""
     r, m = 512, 4096
     c = np.array([r + (i % 8) - 3 for i in range(m)], np.uint16)
     f = orc.block_features(c, (m,), r)[0]
-    want = sum(m - d for d in MADO_DISTANCES if d % 8) / sum(m - d for d in MADO_DISTANCES)
-    assert f[7] == np.float32(sum(m - d for d in MADO_DISTANCES if d % 8)) / np.float32(
-        sum(m - d for d in MADO_DISTANCES))
-    assert abs(f[7] - want) < 1e-7
+    # class k (positions k mod 8) has (m - d_k - k + 7) // 8 pairs, d_k = 1 + 25 k
+    per_class = [(m - (1 + 25 * k) - k + 7) // 8 for k in range(8)]
+    assert f[7] == np.float32(sum(per_class[:7])) / np.float32(sum(per_class))
     assert abs(f[3] - math.log2(5)) < 2 ** -15
     assert f[4] == 1.0  # every element starts a run
     assert f[0] == np.float32(m // 8) / np.float32(m)
-    # a 40-element 1-D field: one partial block; only d = 1 and d = 26 have pairs
+    # a 40-element 1-D field alternating two codes: only distances 1 (positions
+    # 0, 8, ..., 32: 5 pairs, all differing) and 26 (positions 1, 9: 2 pairs, equal
+    # codes since 26 is even) fit inside it
     c = np.array([r + (i % 2) for i in range(40)], np.uint16)
     f = orc.block_features(c, (40,), r)[0]
-    assert f[7] == np.float32((40 - 1) + (40 - 26) * 0) / np.float32((40 - 1) + (40 - 26))
+    assert f[7] == np.float32(5) / np.float32(7)
     assert f[3] == np.float32(1.0)  # log2(1 + 1)
 
 
