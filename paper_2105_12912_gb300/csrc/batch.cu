@@ -494,10 +494,13 @@ DecFieldLayout dec_field_layout(const Geom& g) {
 }
 
 struct DecBatchLayout {
-  uint64_t states, zero_end, tasks, setup0, chunk0, tile0;
-  std::vector<uint64_t> field_at;
+  uint64_t states, prep, zero_end, tasks, setup0, chunk0, tile0;
+  std::vector<uint64_t> field_at, prep_at;
   uint64_t total;
 };
+
+// set-up chunks of a field (one CTA per 1024 codec blocks)
+inline uint32_t prep_chunks(const Geom& g) { return (g.nblk + 1023) / 1024; }
 
 DecBatchLayout dec_batch_layout(const std::vector<Geom>& gs) {
   const uint64_t F = gs.size();
@@ -505,6 +508,13 @@ DecBatchLayout dec_batch_layout(const std::vector<Geom>& gs) {
   uint64_t o = 0;
   B.states = o;
   o += kStateStride * F;
+  // the set-up chunks' look-back states (two per chunk), zeroed with the states
+  B.prep = o;
+  B.prep_at.resize(F);
+  for (uint64_t f = 0; f < F; f++) {
+    B.prep_at[f] = o;
+    o += 16ull * prep_chunks(gs[f]);
+  }
   B.zero_end = o;
   o = a256(o);
   B.tasks = o;
@@ -578,6 +588,10 @@ csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_w
   std::vector<DecodeArgs> tasks(nfields);
   std::vector<uint32_t> setup0(nfields + 1), chunk0(nfields + 1), tile0(nfields + 1);
   uint32_t nsetup = 0, nchunks = 0, ntiles = 0;
+  // fields that share their dimensionality decode with the fused reconstruction
+  int common_nd = gs[0].ndim;
+  for (int f = 1; f < nfields; f++)
+    if (gs[f].ndim != common_nd) common_nd = 0;
   for (int f = 0; f < nfields; f++) {
     const Geom& g = gs[f];
     const DecFieldLayout FL = dec_field_layout(g);
@@ -595,12 +609,14 @@ csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_w
     a.runv = a.codes;
     a.runl = at<uint16_t>(fw, FL.runl);
     a.out = fields[f].d_out;
+    a.fuse = common_nd != 0 ? 1 : 0;
+    a.prep_lb = at<uint64_t>(ws, B.prep_at[f]);
     a.dead = 1;  // until the header pass accepts the field
     setup0[f] = nsetup;
     uint64_t rec_ctas = (g.nelem + 32767) / 32768;
     if (rec_ctas < 1) rec_ctas = 1;
     if (rec_ctas > 256) rec_ctas = 256;
-    nsetup += 4 + (uint32_t)rec_ctas;
+    nsetup += prep_chunks(g) + 3 + (uint32_t)rec_ctas;
     chunk0[f] = nchunks;
     nchunks += (g.nblk + kStreamWarpsPerCta / 2 - 1) / (kStreamWarpsPerCta / 2);
     tile0[f] = ntiles;
@@ -619,7 +635,7 @@ csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_w
     return CSZ_E_CUDA;
   }
   b->launch = DecodeBatchLaunch{b->d_tasks, nfields, at<uint32_t>(ws, B.setup0), nsetup,
-                                at<uint32_t>(ws, B.chunk0), nchunks, at<uint32_t>(ws, B.tile0), ntiles};
+                                at<uint32_t>(ws, B.chunk0), nchunks, at<uint32_t>(ws, B.tile0), ntiles, common_nd};
   // capture once on a private stream
   const bool tracing = trace_suspend();
   cudaGraph_t graph = nullptr;

@@ -511,10 +511,13 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t*
         if (xx & 7) k[i] -= left;  // x difference
       }
       const bool anyp = __any_sync(~0u, pm != 0);
-      __syncthreads();  // every thread has read the box: it carries k from here
+      // the box carries k from here: each thread overwrites only its own column, which
+      // only it has read, so no barrier comes first; the y difference reads the row
+      // below in the same 8-row chunk, and rows 0-7 (8-15) belong to warps 0-3 (4-7),
+      // so each group of four warps waits only for itself (named barriers 1 and 2)
 #pragma unroll
       for (int i = 0; i < 16; i++) s_k[(i * 16 + yy) * 16 + xx] = k[i];
-      __syncthreads();
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + (tid >> 7)), "r"(128) : "memory");
 #pragma unroll
       for (int i = 0; i < 16; i++) {
         const uint32_t j = (i * 16 + yy) * 16 + xx;

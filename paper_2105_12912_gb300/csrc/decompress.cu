@@ -82,6 +82,7 @@ __device__ void dec_prep_body(const DecodeArgs& a) {
 // the reconstruction kernel takes, per-codec counts.  The chunk counted last checks
 // the totals against the header.
 __device__ void dec_prep_chunk_body(const DecodeArgs& a, uint32_t nchunks) {
+  if (a.dead) return;  // (a batch field whose header failed: all its chunks leave)
   __shared__ uint64_t s_scan[33];
   __shared__ uint32_t s_scan32[33];
   __shared__ uint32_t s_nc[3];
@@ -1476,26 +1477,30 @@ __device__ __forceinline__ int field_of(const uint32_t* prefix, int nfields, uin
   return lo;
 }
 
-// set-up: per field 1 prep CTA, 3 table CTAs, then its record CTAs (setup0 prefix)
+// set-up: per field its prep chunks (one CTA per 1024 blocks, chained by look-back),
+// 3 table CTAs, then its record CTAs (setup0 prefix)
 __global__ __launch_bounds__(1024) void dec_setup_batch_kernel(const DecodeArgs* __restrict__ tasks,
                                                                const uint32_t* __restrict__ setup0, int nfields) {
   const int f = field_of(setup0, nfields, blockIdx.x);
   const DecodeArgs& a = tasks[f];
   const uint32_t role = blockIdx.x - setup0[f], nroles = setup0[f + 1] - setup0[f];
-  if (role == 0) dec_prep_body(a);
-  else if (role <= 3) dec_tables_body(a, (int)role - 1);
-  else dec_records_body(a, role - 4, nroles - 4);
+  const uint32_t nprep = (a.g.nblk + 1023) / 1024;
+  if (role < nprep) dec_prep_chunk_body(a, nprep);
+  else if (role < nprep + 3) dec_tables_body(a, (int)(role - nprep));
+  else dec_records_body(a, role - nprep - 3, nroles - nprep - 3);
 }
 
-// entropy decoding: per field ceil(nblk / (kStreamWarps / 2)) CTAs, one stream per warp
-__global__ __launch_bounds__(32 * kStreamWarps) void stream_decode_batch_kernel(const DecodeArgs* __restrict__ tasks,
-                                                                                const uint32_t* __restrict__ chunk0,
-                                                                                int nfields) {
+// entropy decoding: per field ceil(nblk / (kStreamWarps / 2)) CTAs, one stream per warp;
+// ND != 0 (the batch's common dimensionality): full Huffman blocks reconstructed in
+// the decoding warps, as for single fields
+template <int ND>
+__global__ __launch_bounds__(32 * kStreamWarps, 2) void stream_decode_batch_kernel(
+    const DecodeArgs* __restrict__ tasks, const uint32_t* __restrict__ chunk0, int nfields) {
   const int f = field_of(chunk0, nfields, blockIdx.x);
   const DecodeArgs& a = tasks[f];
   const uint32_t b0 = (blockIdx.x - chunk0[f]) * (kStreamWarps / 2);
   const uint32_t b1 = min(a.g.nblk, b0 + kStreamWarps / 2);
-  stream_decode_body<0, float>(a, b0, b1);
+  stream_decode_body<ND, float>(a, b0, b1);
 }
 
 // Reconstruction of a batch, one CTA per codec block of every field.  A run block's
@@ -1513,6 +1518,8 @@ __global__ __launch_bounds__(kRecThreads) void reconstruct_batch_kernel(const De
   const DecodeArgs& a = tasks[f];
   const uint32_t b = blockIdx.x - tile0[f];
   if (a.dead) return;
+  // full Huffman blocks were reconstructed by the decoding warps (fused batches)
+  if (a.fuse && a.ar[a.off_codec + b] == CODEC_HUFF && block_is_full(a.g, b)) return;
   // the status is read once, by thread 0 (run expansions in other CTAs may flag
   // corruption meanwhile), so every thread takes the same path
   if (threadIdx.x == 0) s_go = !(a.st->status & ERR_CORRUPT);
@@ -1542,10 +1549,13 @@ cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
   trace_end(K_DEC_SETUP, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t lut_bytes = 3 * (1u << kLutBits) * sizeof(uint32_t);
-  e = cudaFuncSetAttribute(stream_decode_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lut_bytes);
+  auto k = L.nd == 1 ? stream_decode_batch_kernel<1>
+                     : (L.nd == 2 ? stream_decode_batch_kernel<2>
+                                  : (L.nd == 3 ? stream_decode_batch_kernel<3> : stream_decode_batch_kernel<0>));
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lut_bytes);
   if (e != cudaSuccess) return e;
   trace_begin(K_STREAM_DECODE, s);
-  stream_decode_batch_kernel<<<L.nchunks, 32 * kStreamWarps, lut_bytes, s>>>(L.tasks, L.chunk0, L.nfields);
+  k<<<L.nchunks, 32 * kStreamWarps, lut_bytes, s>>>(L.tasks, L.chunk0, L.nfields);
   trace_end(K_STREAM_DECODE, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // (run blocks are expanded inside the reconstruction)

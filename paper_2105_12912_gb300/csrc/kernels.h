@@ -226,6 +226,7 @@ struct DecodeBatchLaunch {
   uint32_t nchunks;
   const uint32_t* tile0;   // nfields + 1: codec blocks
   uint32_t ntiles;
+  int nd;                  // the fields' common dimensionality (fused decoding), 0 if mixed
 };
 constexpr int kStreamWarpsPerCta = 16;
 cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s);

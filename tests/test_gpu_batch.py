@@ -160,6 +160,39 @@ def test_batch_round_trip(gpu, orc):
             assert float((x.double() - bd.outs[i].double()).abs().max()) <= eb_f
 
 
+@pytest.mark.parametrize("nd", [1, 2, 3])
+def test_batch_round_trip_common_dimensionality(gpu, orc, nd):
+    """Batches whose fields share a dimensionality decode full Huffman blocks with the
+    fused reconstruction (and the chunked set-up): bit-identical to the oracle's
+    decompression of each archive, including edge blocks, run blocks, outliers and a
+    field with more than 1024 codec blocks (several set-up chunks)."""
+    rng = np.random.default_rng(40 + nd)
+    shapes = {1: [(5000,), (4096 * 1100 + 17,), (1,), (70000,)],
+              2: [(70, 131), (64, 64), (2200, 2100), (300, 301)],
+              3: [(19, 23, 37), (16, 16, 16), (160, 130, 70), (40, 64, 64)]}[nd]
+    xs, ebs, modes = [], [], []
+    for i, sh in enumerate(shapes):
+        x = rng.standard_normal(sh).astype(np.float32)
+        for ax in range(len(sh)):
+            x = np.cumsum(x, axis=ax).astype(np.float32)
+        if i % 2 == 0:
+            x[tuple(slice(0, max(1, s // 2)) for s in sh)] = 0.0
+        xs.append(torch.from_numpy(x).cuda())
+        ebs.append(1e-3 if x.size > 1 else 0.1)
+        modes.append("rel" if x.size > 1 else "abs")
+    bc = gpu.BatchCompressor(xs, ebs, modes, radius=64, autotune=False)  # small radius: outliers
+    bc.run()
+    sizes, stats = bc.results()
+    assert all(v == 0 for v in stats)
+    bd = gpu.BatchDecompressor(bc.archives, [tuple(x.shape) for x in xs], archive_bytes=sizes)
+    bd.run()
+    assert bd.results() == [0] * len(xs)
+    for i, x in enumerate(xs):
+        st, yr = orc.decompress(bc.archives[i][:sizes[i]].cpu().numpy(), x.numel())
+        assert st == 0
+        assert np.array_equal(bd.outs[i].cpu().numpy().ravel().view(np.uint32), yr.view(np.uint32)), i
+
+
 def test_batch_decompress_bad_header_isolated(gpu):
     fields = _mixed_fields(8)[:6]
     xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
