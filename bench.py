@@ -321,6 +321,7 @@ def batched_comparison(args, dev, flush):
             raise RuntimeError(f"batched {sel}: field status {stats}")
         t_b = [t for t, _ in timed(bc.run, 5)]
         bd = api.BatchDecompressor(bc.archives, [tuple(x.shape) for x in xs], archive_bytes=caps, outs=outs)
+        res_warps, _ = bd.tune()
         bd.run()
         dstats = bd.results()
         if any(dstats):
@@ -336,7 +337,7 @@ def batched_comparison(args, dev, flush):
             raise RuntimeError("batched round trip outside the error bound")
         res[sel] = {"gbs": n_in / (np.mean(t_b) * 1e-3) / 1e9, "ms": float(np.mean(t_b)),
                     "rt_gbs": n_in / (np.mean(t_rt) * 1e-3) / 1e9,
-                    "bytes": int(sum(sizes)), "tuning": bc.info()}
+                    "bytes": int(sum(sizes)), "tuning": bc.info(), "decoder_warps": res_warps}
         del bd, bc
     plain_gbs = n_in / (np.mean(t_plain) * 1e-3) / 1e9
     plain_rt_gbs = n_in / (np.mean(t_plain_rt) * 1e-3) / 1e9
@@ -353,6 +354,7 @@ def batched_comparison(args, dev, flush):
         "speedup_round_trip_learned_batched_vs_plain": res["learned"]["rt_gbs"] / plain_rt_gbs,
         "cr_loss_learned_vs_plain": res["learned"]["bytes"] / plain_bytes - 1.0,
         "construct_grid": res["learned"]["tuning"]["construct_grid"],
+        "decoder_warps_per_cta": res["learned"]["decoder_warps"],
         "autotune_ms": res["learned"]["tuning"]["tuned_ms"],
         "note": "GB/s of FP32 input; every timed pass is preceded by a 256 MiB L2 flush; the plain path "
                 "synchronises once per call (it returns each size / status to the host); round trips "
@@ -500,6 +502,7 @@ def run_ours(args):
     gsizes, gstat = bc.results()
     assert gstat == [0] and gsizes[0] == nb and torch.equal(bc.archives[0][:nb], arc[:nb])
     bd = api.BatchDecompressor(bc.archives, [dims], archive_bytes=[nb])
+    dec_warps, _ = bd.tune()
     bd.run()
     assert bd.results() == [0] and torch.equal(bd.outs[0].view(torch.int32), rec.view(torch.int32))
 
@@ -636,7 +639,8 @@ def run_ours(args):
                          "timed step, outside the step's events"},
         "compress_gbs": world * bytes_in / (np.mean(t_c) * 1e-3) / 1e9,
         "decompress_gbs": world * bytes_in / (np.mean(t_d) * 1e-3) / 1e9,
-        "graph_replay": {"note": "the same round trip as CUDA graph replays of the batch calls with one field",
+        "graph_replay": {"note": "the same round trip as CUDA graph replays of the batch calls with one field "
+                                 f"(decoder CTAs of {dec_warps} warps, tuned)",
                          "gbs": world * bytes_in / (np.mean(t_graph) * 1e-3) / 1e9,
                          "compress_gbs": world * bytes_in / (np.mean(t_gc) * 1e-3) / 1e9,
                          "decompress_gbs": world * bytes_in / (np.mean(t_gd) * 1e-3) / 1e9},

@@ -258,6 +258,14 @@ size_t csz_batch_dec_workspace_bytes(int nfields, const csz_dfield* fields);
 csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_workspace,
                                 size_t workspace_bytes, void* stream, csz_batch_dec** batch);
 csz_status csz_batch_decompress(csz_batch_dec* batch, void* stream);
+/* Autotuner of the batch decoder's CTA shape: times the batch (three replays each)
+   with entropy-decoding CTAs of 8, 16 and 32 warps (4, 8 and 16 codec blocks per
+   CTA), keeps the fastest and re-captures the graph with it.  The shape never
+   changes the output.  Call it once the archive buffers hold archives of the
+   planned shapes (a tuning run decompresses them); it synchronises `stream`.
+   h_warps (may be NULL) receives the chosen warps per CTA, h_ms[3] (may be NULL)
+   the mean milliseconds of each shape. */
+csz_status csz_batch_dec_tune(csz_batch_dec* batch, void* stream, int* h_warps, double* h_ms);
 csz_status csz_batch_dec_results(csz_batch_dec* batch, int* h_status, void* stream);
 void csz_batch_dec_destroy(csz_batch_dec* batch);
 

@@ -366,6 +366,14 @@ class BatchDecompressor:
         L.lib().csz_batch_dec_results(self._h, stats, _stream_ptr(stream))
         return [int(v) for v in stats]
 
+    def tune(self, stream=None):
+        """Times the decoder's CTA shapes on the archives now in the buffers, keeps the
+        fastest (csz_batch_dec_tune).  Returns (warps per CTA, [ms of 8, 16, 32 warps])."""
+        warps = C.c_int()
+        ms = (C.c_double * 3)()
+        _check(L.lib().csz_batch_dec_tune(self._h, _stream_ptr(stream), C.byref(warps), ms), "csz_batch_dec_tune")
+        return int(warps.value), [float(v) for v in ms]
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:

@@ -460,6 +460,10 @@ csz_status csz_batch_info(const csz_batch* b, int* construct_grid, double* tuned
 // ---------------------------------------------------------------------------------
 }  // extern "C"
 
+// Stream-decode CTA shapes the batch's tuner chooses among (warps per CTA; a CTA
+// decodes warps / 2 codec blocks).  None changes the output.
+constexpr int kDecShapes[3] = {8, 16, 32};
+
 struct csz_batch_dec {
   int nfields = 0;
   unsigned char* zero_base = nullptr;
@@ -468,6 +472,8 @@ struct csz_batch_dec {
   DecodeBatchLaunch launch{};
   DecodeArgs* d_tasks = nullptr;
   cudaGraphExec_t exec = nullptr;
+  const uint32_t* chunk0[3] = {nullptr, nullptr, nullptr};  // per shape: stream-decode CTA prefix
+  uint32_t nchunks[3] = {0, 0, 0};
 };
 
 namespace {
@@ -522,7 +528,7 @@ DecBatchLayout dec_batch_layout(const std::vector<Geom>& gs) {
   B.setup0 = o;
   o += a256(4 * (F + 1));
   B.chunk0 = o;
-  o += a256(4 * (F + 1));
+  o += 3 * a256(4 * (F + 1));  // one prefix per CTA shape
   B.tile0 = o;
   o += a256(4 * (F + 1));
   B.field_at.resize(F);
@@ -545,6 +551,8 @@ csz_status check_dfields(int n, const csz_dfield* fields, std::vector<Geom>& gs)
   if (tiles >= (1ull << 32)) return CSZ_E_ARG;
   return CSZ_OK;
 }
+
+cudaError_t dec_capture(csz_batch_dec* b);
 
 cudaError_t dec_enqueue(const csz_batch_dec* b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, s);
@@ -586,8 +594,10 @@ csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_w
   b->states = at<DevState>(ws, B.states);
   b->d_tasks = at<DecodeArgs>(ws, B.tasks);
   std::vector<DecodeArgs> tasks(nfields);
-  std::vector<uint32_t> setup0(nfields + 1), chunk0(nfields + 1), tile0(nfields + 1);
-  uint32_t nsetup = 0, nchunks = 0, ntiles = 0;
+  std::vector<uint32_t> setup0(nfields + 1), tile0(nfields + 1);
+  std::vector<uint32_t> chunk0s[3];
+  for (auto& c : chunk0s) c.resize(nfields + 1);
+  uint32_t nsetup = 0, ntiles = 0, nchunks_v[3] = {0, 0, 0};
   // fields that share their dimensionality decode with the fused reconstruction
   int common_nd = gs[0].ndim;
   for (int f = 1; f < nfields; f++)
@@ -617,26 +627,51 @@ csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_w
     if (rec_ctas < 1) rec_ctas = 1;
     if (rec_ctas > 256) rec_ctas = 256;
     nsetup += prep_chunks(g) + 3 + (uint32_t)rec_ctas;
-    chunk0[f] = nchunks;
-    nchunks += (g.nblk + kStreamWarpsPerCta / 2 - 1) / (kStreamWarpsPerCta / 2);
+    for (int v = 0; v < 3; v++) {
+      const uint32_t per = (uint32_t)kDecShapes[v] / 2;
+      chunk0s[v][f] = nchunks_v[v];
+      nchunks_v[v] += (g.nblk + per - 1) / per;
+    }
     tile0[f] = ntiles;
     ntiles += g.nblk;
   }
   setup0[nfields] = nsetup;
-  chunk0[nfields] = nchunks;
+  for (int v = 0; v < 3; v++) chunk0s[v][nfields] = nchunks_v[v];
   tile0[nfields] = ntiles;
   cudaError_t e = upload(b->d_tasks, tasks, s);
   if (e == cudaSuccess) e = upload(at<uint32_t>(ws, B.setup0), setup0, s);
-  if (e == cudaSuccess) e = upload(at<uint32_t>(ws, B.chunk0), chunk0, s);
+  for (int v = 0; v < 3; v++) {
+    b->chunk0[v] = at<uint32_t>(ws, B.chunk0 + (uint64_t)v * a256(4 * (nfields + 1)));
+    b->nchunks[v] = nchunks_v[v];
+    if (e == cudaSuccess) e = upload(const_cast<uint32_t*>(b->chunk0[v]), chunk0s[v], s);
+  }
   if (e == cudaSuccess) e = upload(at<uint32_t>(ws, B.tile0), tile0, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (failed(e, "decompression table upload")) {
     delete b;
     return CSZ_E_CUDA;
   }
-  b->launch = DecodeBatchLaunch{b->d_tasks, nfields, at<uint32_t>(ws, B.setup0), nsetup,
-                                at<uint32_t>(ws, B.chunk0), nchunks, at<uint32_t>(ws, B.tile0), ntiles, common_nd};
-  // capture once on a private stream
+  b->launch = DecodeBatchLaunch{b->d_tasks, nfields, at<uint32_t>(ws, B.setup0), nsetup, b->chunk0[1],
+                                b->nchunks[1], at<uint32_t>(ws, B.tile0), ntiles, common_nd, kDecShapes[1]};
+  if (dec_capture(b) != cudaSuccess) {
+    delete b;
+    return CSZ_E_CUDA;
+  }
+  *out = b;
+  return CSZ_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// (Re)captures the batch's decompression graph with its current launch shape.
+cudaError_t dec_capture(csz_batch_dec* b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  cudaError_t e;
   const bool tracing = trace_suspend();
   cudaGraph_t graph = nullptr;
   cudaStream_t cap = nullptr;
@@ -664,11 +699,56 @@ csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_w
   trace_resume(tracing);
   if (failed(e, step)) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
-    delete b;
+    b->exec = nullptr;
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+csz_status csz_batch_dec_tune(csz_batch_dec* b, void* stream, int* h_warps, double* h_ms) {
+  if (!b || !b->exec) return CSZ_E_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool tracing = trace_suspend();
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  double best = -1.0;
+  int pick = 1;
+  for (int v = 0; v < 3 && e == cudaSuccess; v++) {
+    b->launch.warps = kDecShapes[v];
+    b->launch.chunk0 = b->chunk0[v];
+    b->launch.nchunks = b->nchunks[v];
+    e = dec_enqueue(b, s);  // warm-up
+    float ms = 0.0f, tot = 0.0f;
+    for (int r = 0; r < 3 && e == cudaSuccess; r++) {
+      e = cudaEventRecord(t0, s);
+      if (e == cudaSuccess) e = dec_enqueue(b, s);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+      tot += ms;
+    }
+    if (h_ms) h_ms[v] = tot / 3.0;
+    if (e == cudaSuccess && (best < 0.0 || tot < best)) {
+      best = tot;
+      pick = v;
+    }
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  trace_resume(tracing);
+  b->launch.warps = kDecShapes[pick];
+  b->launch.chunk0 = b->chunk0[pick];
+  b->launch.nchunks = b->nchunks[pick];
+  if (h_warps) *h_warps = kDecShapes[pick];
+  if (e != cudaSuccess) {
+    failed(e, "decompression tuning");
     return CSZ_E_CUDA;
   }
-  *out = b;
-  return CSZ_OK;
+  return dec_capture(b) == cudaSuccess ? CSZ_OK : CSZ_E_CUDA;
 }
 
 csz_status csz_batch_decompress(csz_batch_dec* b, void* stream) {

@@ -667,6 +667,7 @@ __device__ bool fused_decode_reconstruct(const DecodeArgs& a, uint32_t b, uint32
 }
 
 constexpr int kStreamWarps = kStreamWarpsPerCta;
+constexpr int kRecTabWords = 288;  // per decoding warp of a fused stream: record table 32 + 3-D sums 256
 
 // Entropy decoding, persistent: each CTA stages the lookup tables of the books the
 // archive uses in shared memory once, then its warps take (block, stream) slots from
@@ -682,8 +683,6 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
   extern __shared__ __align__(16) uint32_t s_luts[];  // the present books' tables
   __shared__ unsigned long long s_first[kMaxLen + 1], s_limit[kMaxLen + 1];
   __shared__ uint32_t s_off[kMaxLen + 1], s_count[kMaxLen + 1];
-  // fused streams: per warp a record table (32 words) and the 3-D running sums (256)
-  __shared__ uint32_t s_rectab[ND != 0 ? kStreamWarps * 288 : 1];
   __shared__ int s_go;
   if (a.dead) return;
   // the status is read once, by thread 0, and acted on after the staging barrier, so
@@ -693,6 +692,9 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
   uint32_t* lut_code = s_luts;
   uint32_t* lut_val = s_luts + (huff ? (1 << kLutBits) : 0);
   uint32_t* lut_len = lut_val + (1 << kLutBits);
+  // fused streams: after the tables, per warp a record table (32 words) and the 3-D
+  // running sums (256 words); the launch sizes the dynamic shared memory for them
+  uint32_t* s_rectab = s_luts + (huff ? (1 << kLutBits) : 0) + (rle ? 2 * (1 << kLutBits) : 0);
   // a chunk of blocks (batches) copies only the tables its own blocks use
   bool need_code = huff, need_runs = rle;
   if (b_end != 0) {
@@ -753,11 +755,11 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
       const BookView bk{lut_code, s_first, s_limit, s_count, s_off, t->sorted, (int)t->maxlen, t->fullmask};
       if (ND != 0 && a.fuse && m == (uint32_t)kSlots) {
         if (which == 0) {
-          ok = fused_decode_reconstruct<ND, E>(a, b, 0, u + 1, na, bk, &used, s_rectab + 288 * (threadIdx.x >> 5));
+          ok = fused_decode_reconstruct<ND, E>(a, b, 0, u + 1, na, bk, &used, s_rectab + kRecTabWords * (threadIdx.x >> 5));
           ok = ok && used == na;
         } else {
           ok = fused_decode_reconstruct<ND, E>(a, b, 1, u + 1 + na, nu - 1 - na, bk, &used,
-                                            s_rectab + 288 * (threadIdx.x >> 5));
+                                            s_rectab + kRecTabWords * (threadIdx.x >> 5));
           ok = ok && ((2ull * (1ull + na + used) + 3) & ~3ull) == bytes;
         }
       } else if (which == 0) {
@@ -1490,16 +1492,18 @@ __global__ __launch_bounds__(1024) void dec_setup_batch_kernel(const DecodeArgs*
   else dec_records_body(a, role - nprep - 3, nroles - nprep - 3);
 }
 
-// entropy decoding: per field ceil(nblk / (kStreamWarps / 2)) CTAs, one stream per warp;
-// ND != 0 (the batch's common dimensionality): full Huffman blocks reconstructed in
-// the decoding warps, as for single fields
+// entropy decoding: per field ceil(nblk / (W / 2)) CTAs of W warps (W = blockDim.x / 32,
+// chosen by the batch's tuner: 8, 16 or 32), one stream per warp; ND != 0 (the
+// batch's common dimensionality): full Huffman blocks reconstructed in the decoding
+// warps, as for single fields
 template <int ND>
-__global__ __launch_bounds__(32 * kStreamWarps, 2) void stream_decode_batch_kernel(
-    const DecodeArgs* __restrict__ tasks, const uint32_t* __restrict__ chunk0, int nfields) {
+__global__ __launch_bounds__(1024) void stream_decode_batch_kernel(const DecodeArgs* __restrict__ tasks,
+                                                                   const uint32_t* __restrict__ chunk0, int nfields) {
   const int f = field_of(chunk0, nfields, blockIdx.x);
   const DecodeArgs& a = tasks[f];
-  const uint32_t b0 = (blockIdx.x - chunk0[f]) * (kStreamWarps / 2);
-  const uint32_t b1 = min(a.g.nblk, b0 + kStreamWarps / 2);
+  const uint32_t per = blockDim.x / 64;  // blocks per CTA: two streams each
+  const uint32_t b0 = (blockIdx.x - chunk0[f]) * per;
+  const uint32_t b1 = min(a.g.nblk, b0 + per);
   stream_decode_body<ND, float>(a, b0, b1);
 }
 
@@ -1548,14 +1552,15 @@ cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
   dec_setup_batch_kernel<<<L.nsetup, 1024, 0, s>>>(L.tasks, L.setup0, L.nfields);
   trace_end(K_DEC_SETUP, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t lut_bytes = 3 * (1u << kLutBits) * sizeof(uint32_t);
+  const int warps = L.warps ? L.warps : kStreamWarps;
+  const size_t smem = 3 * (1u << kLutBits) * sizeof(uint32_t) + (L.nd ? (size_t)warps * kRecTabWords * 4 : 0);
   auto k = L.nd == 1 ? stream_decode_batch_kernel<1>
                      : (L.nd == 2 ? stream_decode_batch_kernel<2>
                                   : (L.nd == 3 ? stream_decode_batch_kernel<3> : stream_decode_batch_kernel<0>));
-  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lut_bytes);
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   trace_begin(K_STREAM_DECODE, s);
-  k<<<L.nchunks, 32 * kStreamWarps, lut_bytes, s>>>(L.tasks, L.chunk0, L.nfields);
+  k<<<L.nchunks, 32 * warps, smem, s>>>(L.tasks, L.chunk0, L.nfields);
   trace_end(K_STREAM_DECODE, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // (run blocks are expanded inside the reconstruction)
@@ -1602,7 +1607,8 @@ cudaError_t launch_decode_stages(const DecodeArgs& a, cudaStream_t s) {
   const int nd = a.g.ndim;
   const int nluts = ((a.flags & 1u) ? 1 : 0) + ((a.flags & 2u) ? 2 : 0);
   if (nluts) {
-    const size_t lut_bytes = (size_t)nluts * (1u << kLutBits) * sizeof(uint32_t);
+    const size_t lut_bytes =
+        (size_t)nluts * (1u << kLutBits) * sizeof(uint32_t) + (size_t)kStreamWarps * kRecTabWords * 4;
     static int sms = 0, occ[4][4] = {};
     auto k = nd == 1 ? stream_decode_kernel<1, E> : (nd == 2 ? stream_decode_kernel<2, E> : stream_decode_kernel<3, E>);
     if (sms == 0) {
@@ -1611,7 +1617,7 @@ cudaError_t launch_decode_stages(const DecodeArgs& a, cudaStream_t s) {
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       for (auto kk : {stream_decode_kernel<1, E>, stream_decode_kernel<2, E>, stream_decode_kernel<3, E>})
         cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(3 * (1u << kLutBits) * sizeof(uint32_t)));
+                             (int)(3 * (1u << kLutBits) * sizeof(uint32_t) + kStreamWarps * kRecTabWords * 4));
     }
     if (occ[nd][nluts] == 0) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[nd][nluts], k, 32 * kStreamWarps, lut_bytes);

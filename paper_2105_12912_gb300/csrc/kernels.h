@@ -227,6 +227,7 @@ struct DecodeBatchLaunch {
   const uint32_t* tile0;   // nfields + 1: codec blocks
   uint32_t ntiles;
   int nd;                  // the fields' common dimensionality (fused decoding), 0 if mixed
+  int warps;               // stream-decode warps per CTA (8, 16 or 32; 0 = 16)
 };
 constexpr int kStreamWarpsPerCta = 16;
 cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s);

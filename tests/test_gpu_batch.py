@@ -193,6 +193,26 @@ def test_batch_round_trip_common_dimensionality(gpu, orc, nd):
         assert np.array_equal(bd.outs[i].cpu().numpy().ravel().view(np.uint32), yr.view(np.uint32)), i
 
 
+def test_batch_decoder_tuning(gpu):
+    """The decoder's CTA shape (8, 16 or 32 warps) never changes the output: after
+    tuning, the batch decompression equals the single-field decompressions bit for
+    bit, for a mixed batch and for one of a common dimensionality."""
+    for fields in (_mixed_fields(11), _mixed_fields(12)[8:12]):
+        xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
+        bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields], autotune=False)
+        bc.run()
+        sizes, stats = bc.results()
+        assert all(v == 0 for v in stats)
+        bd = gpu.BatchDecompressor(bc.archives, [tuple(x.shape) for x in xs], archive_bytes=sizes)
+        warps, ms = bd.tune()
+        assert warps in (8, 16, 32) and all(t > 0 for t in ms)
+        bd.run()
+        assert bd.results() == [0] * len(xs)
+        for i in range(len(xs)):
+            y, _ = gpu.decompress(bc.archives[i], sizes[i])
+            assert torch.equal(bd.outs[i].view(torch.int32), y.view(torch.int32)), (warps, i)
+
+
 def test_batch_decompress_bad_header_isolated(gpu):
     fields = _mixed_fields(8)[:6]
     xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
