@@ -316,18 +316,9 @@ struct BookView {
 // ones from the smallest length whose left-justified end exceeds bb, which is the
 // true length whenever it is <= nb (zero bits below nb cannot complete a shorter
 // codeword).
-__device__ __forceinline__ int ihs_match(uint64_t bb, int nb, const BookView& bk, int& sym) {
-  if (nb <= 0) return 0;
-  const uint32_t e = bk.lut[bb >> (64 - kLutBits)];
-  const int l = (int)(e & 0xffu);
-  if (l) {
-    if (l <= nb) {
-      sym = (int)(e >> 8);
-      return l;
-    }
-    return 0;
-  }
-  if (nb <= kLutBits) return 0;
+// Codes longer than the lookup table's 12 bits: the smallest length whose codes end
+// above bb (a binary search over the canonical limits), checked to be a codeword.
+__device__ __forceinline__ int ihs_match_long(uint64_t bb, int nb, const BookView& bk, int& sym) {
   int lo = kLutBits + 1, hi = bk.maxlen + 1;  // smallest k whose codes end above bb
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
@@ -339,6 +330,19 @@ __device__ __forceinline__ int ihs_match(uint64_t bb, int nb, const BookView& bk
   if (c < bk.first[lo] || c - bk.first[lo] >= bk.count[lo]) return 0;  // not a codeword
   sym = (int)bk.sorted[bk.off[lo] + (uint32_t)(c - bk.first[lo])];
   return lo;
+}
+
+// The lookup-table hit needs no branch: a code of length l <= nb found among the
+// zero-padded top bits is the next codeword (no codeword is a prefix of another),
+// and nb <= 0 can never pass l <= nb.  Only a miss with more than 12 bits at hand
+// (a code longer than the table) takes the search.
+__device__ __forceinline__ int ihs_match(uint64_t bb, int nb, const BookView& bk, int& sym) {
+  const uint32_t e = bk.lut[bb >> (64 - kLutBits)];
+  const int l = (int)(e & 0xffu);
+  sym = (int)(e >> 8);
+  int ml = (l != 0 && l <= nb) ? l : 0;
+  if (l == 0 && nb > kLutBits) ml = ihs_match_long(bb, nb, bk, sym);
+  return ml;
 }
 
 // A warp's reader of one interleaved stream in[0..avail).  The warp reads the stream
