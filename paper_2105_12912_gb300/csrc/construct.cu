@@ -88,11 +88,40 @@ __device__ __forceinline__ void load16(const double* p, double (&f)[16]) {
   }
 }
 
+// ---- FP32 3-D tiles: 64-byte swizzled rows ------------------------------------------
+// A 16^3 FP32 box has 64-byte x rows.  Its TMA copy uses the 64-byte swizzle: the
+// 16-byte chunk c of row R lands at chunk c ^ ((R >> 1) & 3) of that row (the buffer
+// is 1024-byte aligned), so that eight threads reading one chunk of eight consecutive
+// rows touch all 32 banks.  Thread loads and every reader of such a box use the same
+// placement: element e of the box sits at swz64(e).
+__device__ __forceinline__ uint32_t swz64(uint32_t e) { return e ^ ((e >> 3) & 12u); }
+template <typename E>
+constexpr bool kRowSwizzled = false;
+template <>
+constexpr bool kRowSwizzled<float> = true;
+
+__device__ __forceinline__ void ld_row(const float* row, uint32_t key, float (&f)[16]) {
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    const float4 v = reinterpret_cast<const float4*>(row)[c ^ key];
+    f[4 * c] = v.x;
+    f[4 * c + 1] = v.y;
+    f[4 * c + 2] = v.z;
+    f[4 * c + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void st_row(int32_t* row, uint32_t key, const int32_t (&k)[16]) {
+#pragma unroll
+  for (int c = 0; c < 4; c++)
+    reinterpret_cast<int4*>(row)[c ^ key] = make_int4(k[4 * c], k[4 * c + 1], k[4 * c + 2], k[4 * c + 3]);
+}
+
 // ---- shared memory -----------------------------------------------------------------
 template <typename T, uint32_t NIN = kSlots>
 struct SmemT {
   T in[2][NIN];                 // TMA destinations (box layout); in 3-D the current
-                                // one then carries k for the y difference
+                                // one then carries the partly differenced k
+  int32_t zrow[16];             // zeros: the neighbour row of a chunk's first row / plane
   uint16_t c[kSlots];           // codes of the current tile (dense order)
   uint32_t hc[kNsymCode];       // code histogram (per CTA, current field)
   uint32_t hv[kNsymCode];       // run-value histogram
@@ -158,7 +187,8 @@ __device__ __forceinline__ const float* field_ptr<float>(const ConstructArgs& A)
 template <>
 __device__ __forceinline__ const double* field_ptr<double>(const ConstructArgs& A) { return A.x64; }
 
-// Thread-loaded tile (fields TMA cannot describe): box layout, zeros outside.
+// Thread-loaded tile (fields TMA cannot describe): box layout (FP32 3-D boxes
+// swizzled like their TMA copies), zeros outside.
 template <typename E>
 __device__ void load_tile_threads(const ConstructArgs& A, uint32_t b, E* buf) {
   const E* xs = field_ptr<E>(A);
@@ -183,7 +213,7 @@ __device__ void load_tile_threads(const ConstructArgs& A, uint32_t b, E* buf) {
     }
     E v = E(0);
     if (zz < w[0] && yy < w[1] && xx < w[2]) v = xs[((uint64_t)(org[0] + zz) * ny + (org[1] + yy)) * nx + org[2] + xx];
-    buf[p] = v;
+    buf[kRowSwizzled<E> && g.ndim == 3 ? swz64(p) : p] = v;
   }
 }
 
@@ -228,7 +258,8 @@ __device__ __noinline__ uint32_t edge_codes(const ConstructArgs& A, uint32_t b, 
         yy = rr / w[2];
         xx = rr - yy * w[2];
       }
-      const uint32_t box = ND == 1 ? xx : (ND == 2 ? yy * 64 + xx : (zz * 16 + yy) * 16 + xx);
+      uint32_t box = ND == 1 ? xx : (ND == 2 ? yy * 64 + xx : (zz * 16 + yy) * 16 + xx);
+      if (ND == 3 && kRowSwizzled<E>) box = swz64(box);
       bool p;
       err |= pq.full(in[box], kv[i], p);
       pm |= (uint32_t)p << i;
@@ -335,22 +366,25 @@ __device__ void tile_tail(const ConstructArgs& A, uint32_t b, SmemT<E, NIN>& S, 
   if (A.all_runs || 4 * nruns <= m) {
     if (tid < 32) run_head_index(S.head, m, S.woff, S.next);
     __syncthreads();
-    // single-element runs are counted in a register and added once per warp
+    // thread t: the run heads among slots 16t .. 16t + 15 (head bits are clear at and
+    // beyond m); a run ends at the next head in these bits, else at the next head after
+    // slot 16t + 15.  Single-element runs are counted in a register and added once per
+    // warp.
     uint32_t ones = 0;
-#pragma unroll 4
-    for (int i = 0; i < kPer; i++) {
-      const uint32_t j = tid + kThreads * i;
-      if (j < m && ((S.head[j >> 5] >> (j & 31)) & 1u)) {
-        const uint32_t v = S.c[j];
-        const uint32_t len = next_head(S.head, S.next, j, m) - j;
-        atomicAdd(&S.hv[v], 1u);
-        if (len == 1)
-          ones++;
-        else if (len <= (uint32_t)kHlShared)
-          atomicAdd(&S.hl[len - 1], 1u);
-        else
-          atomicAdd(&A.hist_len[len - 1], 1u);
-      }
+    const uint32_t j0 = 16u * tid;
+    uint32_t hb = (S.head[tid >> 1] >> (16 * (tid & 1))) & 0xffffu;
+    while (hb) {
+      const uint32_t j = j0 + (uint32_t)(__ffs(hb) - 1);
+      hb &= hb - 1;
+      const uint32_t end = hb ? j0 + (uint32_t)(__ffs(hb) - 1) : next_head(S.head, S.next, j0 + 15, m);
+      const uint32_t len = end - j;
+      atomicAdd(&S.hv[S.c[j]], 1u);
+      if (len == 1)
+        ones++;
+      else if (len <= (uint32_t)kHlShared)
+        atomicAdd(&S.hl[len - 1], 1u);
+      else
+        atomicAdd(&A.hist_len[len - 1], 1u);
     }
     ones = warp_sum(ones);
     if (lane == 0 && ones) atomicAdd(&S.hl[0], ones);
@@ -358,6 +392,47 @@ __device__ void tile_tail(const ConstructArgs& A, uint32_t b, SmemT<E, NIN>& S, 
   // the next block writes S.c, S.patch and S.outl again (after the caller's barrier)
   if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
   if (err) atomicOr(&A.st->status, err);
+}
+
+// Postquantization of one thread's 16 consecutive slots j0 .. j0 + 15 (j0 = 16 t) from
+// u = delta + r: codes (two 16-byte stores), outlier residuals, the slots' outlier /
+// patch / run-head bits (two threads fill one 32-bit word) and the code histogram (one
+// add when the 16 codes agree).  Head bit 0 of lane 0 compares with another warp's
+// slot: it is left clear here and set after the tile.
+template <typename SM>
+__device__ __forceinline__ void post16(SM& S, const uint32_t (&u)[16], uint32_t pm, int32_t r, int32_t* dglob) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t j0 = 16u * tid;
+  uint32_t q[16], om = 0, hm = 0;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    q[i] = u[i] - 1u < (uint32_t)(2 * r - 1) ? u[i] : 0u;  // |delta| < r
+    om |= (uint32_t)(q[i] == 0) << i;
+    if (i) hm |= (uint32_t)(q[i] != q[i - 1]) << i;
+  }
+  uint4* cw = reinterpret_cast<uint4*>(S.c + j0);
+  cw[0] = make_uint4(q[0] | q[1] << 16, q[2] | q[3] << 16, q[4] | q[5] << 16, q[6] | q[7] << 16);
+  cw[1] = make_uint4(q[8] | q[9] << 16, q[10] | q[11] << 16, q[12] | q[13] << 16, q[14] | q[15] << 16);
+  if (om) {
+#pragma unroll
+    for (int i = 0; i < 16; i++)
+      if ((om >> i) & 1u) dglob[j0 + i] = (int32_t)(u[i] - (uint32_t)r);
+  }
+  if ((hm >> 1) == 0) {
+    atomicAdd(&S.hc[q[0]], 16u);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; i++) atomicAdd(&S.hc[q[i]], 1u);
+  }
+  const uint32_t qb = __shfl_up_sync(~0u, q[15], 1);
+  if (lane != 0 && q[0] != qb) hm |= 1u;
+  const uint32_t om2 = __shfl_down_sync(~0u, om, 1), pm2 = __shfl_down_sync(~0u, pm, 1),
+                 hm2 = __shfl_down_sync(~0u, hm, 1);
+  if ((lane & 1) == 0) {
+    S.outl[tid >> 1] = om | (om2 << 16);
+    S.patch[tid >> 1] = pm | (pm2 << 16);
+    S.head[tid >> 1] = hm | (hm2 << 16);
+  }
 }
 
 // ---- one tile ------------------------------------------------------------------------
@@ -412,49 +487,29 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t*
     if (ND == 1) {
       // thread t: 16 consecutive elements (a warp covers two whole 256-chunks)
       int32_t k[16];
-      uint32_t pm = 0, slow = 0;
+      uint32_t pm = 0;
       E f[16];
       load16(in + 16 * tid, f);
+      bool ok = true;
 #pragma unroll
-      for (int i = 0; i < 16; i++) slow |= (uint32_t)!pq.fast(f[i], k[i]) << i;
-      if (__any_sync(~0u, slow != 0)) {
+      for (int i = 0; i < 16; i++) ok = pq.fast(f[i], k[i]) & ok;
+      if (!__all_sync(~0u, ok)) {
 #pragma unroll
         for (int i = 0; i < 16; i++) {
-          if ((slow >> i) & 1u) {
+          int32_t kk;
+          if (!pq.fast(f[i], kk)) {
             bool p;
-            err |= pq.full(in[16 * tid + i], k[i], p);
+            err |= pq.full(f[i], k[i], p);
             pm |= (uint32_t)p << i;
           }
         }
       }
-      const int32_t prev = __shfl_up_sync(~0u, k[15], 1);
-      uint32_t om = 0, hm = 0, qprev = 0, qfirst = 0;
+      const int32_t up = __shfl_up_sync(~0u, k[15], 1);
+      const int32_t prev = (tid & 15) ? up : 0;  // a 256-chunk is 16 threads
+      uint32_t u[16];
 #pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const uint32_t j = 16 * tid + i;
-        const int32_t left = i ? k[i - 1] : prev;
-        const int32_t delta = (j & 255) ? k[i] - left : k[i];
-        const uint32_t u = (uint32_t)(delta + r);
-        const uint32_t q = u - 1u < (uint32_t)(2 * r - 1) ? u : 0u;  // |delta| < r
-        S.c[j] = (uint16_t)q;
-        if (q == 0) dglob[j] = delta;
-        atomicAdd(&S.hc[q], 1u);
-        om |= (uint32_t)(q == 0) << i;
-        if (i == 0) qfirst = q;
-        else hm |= (uint32_t)(q != qprev) << i;
-        qprev = q;
-      }
-      // the first slot's left neighbour is the last slot of the lane below (lane 0:
-      // another warp's, set after the tile)
-      const uint32_t qbelow = __shfl_up_sync(~0u, qprev, 1);
-      if (lane != 0 && qfirst != qbelow) hm |= 1u;
-      const uint32_t om2 = __shfl_down_sync(~0u, om, 1), pm2 = __shfl_down_sync(~0u, pm, 1),
-                     hm2 = __shfl_down_sync(~0u, hm, 1);
-      if ((lane & 1) == 0) {
-        S.outl[tid >> 1] = om | (om2 << 16);
-        S.patch[tid >> 1] = pm | (pm2 << 16);
-        S.head[tid >> 1] = hm | (hm2 << 16);
-      }
+      for (int i = 0; i < 16; i++) u[i] = (uint32_t)(k[i] - (i ? k[i - 1] : prev) + r);
+      post16(S, u, pm, r, dglob);
     } else if (ND == 2) {
       // thread t: column xx = t & 63 of the 16-row chunk band t >> 6
       const uint32_t xx = tid & 63, ry = tid >> 6;
@@ -483,6 +538,56 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t*
         const uint32_t j = (16 * ry + i) * 64 + xx;
         post(delta, j, anyp, (pm >> i) & 1u);
       }
+    } else if constexpr (kRowSwizzled<E>) {
+      // FP32: thread t holds the x row (z, y) = (t >> 4, t & 15), two 8-chunks along x,
+      // i.e. the 16 consecutive slots 16t .. 16t + 15.  The x difference runs in
+      // registers; the y and z differences read the rows t - 1, t - 16 and t - 17 (the
+      // zero row at a chunk's first row or plane), which by then hold their x differences.
+      const uint32_t zz = tid >> 4, yy = tid & 15, key = (tid >> 1) & 3;
+      float f[16];
+      ld_row(in + 16 * tid, key, f);
+      int32_t k[16];
+      bool ok = true;
+#pragma unroll
+      for (int i = 0; i < 16; i++) ok = pq.fast(f[i], k[i]) & ok;
+      uint32_t pm = 0;
+      if (!__all_sync(~0u, ok)) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          int32_t kk;
+          if (!pq.fast(f[i], kk)) {
+            bool p;
+            err |= pq.full(f[i], k[i], p);
+            pm |= (uint32_t)p << i;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 15; i > 0; i--)
+        if (i & 7) k[i] -= k[i - 1];  // x difference within 8-chunks
+      // the box carries the x differences from here: each thread overwrites only its own
+      // row, which only it has read, so no barrier comes first; the neighbour rows lie
+      // in the same 8-plane chunk, and planes 0-7 (8-15) belong to threads 0-127
+      // (128-255), so each half of the CTA waits only for itself (named barriers 1, 2)
+      st_row(s_k + 16 * tid, key, k);
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + (tid >> 7)), "r"(128) : "memory");
+      const bool hy = (yy & 7) != 0, hz = (zz & 7) != 0;
+      const int ty = hy ? tid - 1 : 0, tz = hz ? tid - 16 : 0, tyz = hy && hz ? tid - 17 : 0;
+      const int4* ry = reinterpret_cast<const int4*>(hy ? s_k + 16 * ty : S.zrow);
+      const int4* rz = reinterpret_cast<const int4*>(hz ? s_k + 16 * tz : S.zrow);
+      const int4* ryz = reinterpret_cast<const int4*>(hy && hz ? s_k + 16 * tyz : S.zrow);
+      // rows t - 16 and t - 17 have the swizzle keys of rows t and t - 1
+      const uint32_t ky = ((uint32_t)(tid + 7) >> 1) & 3;  // = ((t - 1) >> 1) & 3 for t >= 1
+      uint32_t u[16];
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const int4 a = ry[c ^ ky], bz = rz[c ^ key], d = ryz[c ^ ky];
+        u[4 * c] = (uint32_t)(k[4 * c] - a.x - bz.x + d.x + r);
+        u[4 * c + 1] = (uint32_t)(k[4 * c + 1] - a.y - bz.y + d.y + r);
+        u[4 * c + 2] = (uint32_t)(k[4 * c + 2] - a.z - bz.z + d.z + r);
+        u[4 * c + 3] = (uint32_t)(k[4 * c + 3] - a.w - bz.w + d.w + r);
+      }
+      post16(S, u, pm, r, dglob);
     } else {
       // thread t: z column of (xx, yy) = (t & 15, t >> 4); z and x differences in
       // registers and shuffles, the y difference through shared memory
@@ -709,18 +814,22 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
                                                              const uint32_t* __restrict__ tile0, int nfields,
                                                              uint32_t ntiles, uint32_t* ticket,
                                                              uint32_t spin_limit) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   using SM = SmemT<E, G ? kHaloMax : kSlots>;
   SM& S = *reinterpret_cast<SM*>(smem_raw);
+  // the swizzled FP32 3-D copies assume 1024-byte aligned buffers: without that
+  // alignment every tile is loaded by the threads (same placement, no TMA)
+  const bool tma_ok = (smem_u32(smem_raw) & 1023u) == 0;
   __shared__ uint32_t s_t[2];
   __shared__ int s_f[2];
-  __shared__ uint32_t s_fail;
+  uint32_t n_rec_acc = 0, n_patch_acc = 0, pending = 0;  // thread 0: the field's counts, the next ticket
   const int tid = threadIdx.x;
   auto task = [&](int f) -> const ConstructTask* { return tasks ? &tasks[f] : &one; };
   auto base = [&](int f) -> uint32_t { return tasks ? tile0[f] : 0u; };
   // thread 0: ticket t goes to buffer `slot`: its field, its box, and its fetch.
   // Tickets are drawn one tile ahead of the fetches (`pending`), so the counter's
-  // round trip overlaps the work on the current tile.
+  // round trip overlaps the work on the current tile.  (A fixed stride over the tiles
+  // measured slower: tiles differ in cost, and the counter balances them.)
   auto claim = [&](int slot, uint32_t t, int hint) {
     const int f = t < ntiles ? (tasks ? find_field(tile0, nfields, t, hint) : 0) : -1;
     s_t[slot] = t;
@@ -728,28 +837,27 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
     if (f >= 0) {
       uint32_t* bx = S.box[slot];
       block_box(task(f)->a.g, t - base(f), bx, bx + 3);
-      if (task(f)->use_tma) {
+      if (task(f)->use_tma && tma_ok) {
         if (G) issue_tile_global(task(f), bx, S.in[slot], &S.bar[slot]);
         else issue_tile(task(f), bx, S.in[slot], &S.bar[slot]);
       }
     }
   };
-  uint32_t pending = 0;
 
   if (tid == 0) {
     mbar_init(&S.bar[0]);
     mbar_init(&S.bar[1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_fail = 0;
     claim(0, atomicAdd(ticket, 1u), 0);
     pending = atomicAdd(ticket, 1u);
   }
   for (int i = tid; i < kNsymCode + kNsymCode + kHlShared; i += kThreads) S.hc[i] = 0;  // hc, hv, hl
+  if (tid < 16) S.zrow[tid] = 0;
   __syncthreads();
 
   int cur = 0, field = -1;
-  uint32_t phase[2] = {0u, 0u};
-  uint32_t n_rec_acc = 0, n_patch_acc = 0;  // thread 0: the current field's counts
+  bool failed = false;
+  uint32_t phase = 0u;  // bit i: the phase awaited on buffer i
   auto flush_field = [&](int f) {
     const ConstructArgs& P = task(f)->a;
     flush_hist(S.hc, kNsymCode, P.hist_code);
@@ -758,8 +866,8 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
     if (tid == 0) {
       if (n_rec_acc) atomicAdd(&P.st->n_rec, (unsigned long long)n_rec_acc);
       if (n_patch_acc) atomicAdd(&P.st->n_patch, (unsigned long long)n_patch_acc);
+      n_rec_acc = n_patch_acc = 0;
     }
-    n_rec_acc = n_patch_acc = 0;
   };
   while (true) {
     const uint32_t t = s_t[cur];
@@ -777,27 +885,30 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
         flush_field(field);
         __syncthreads();
         for (int i = tid; i < kNsymCode + kNsymCode + kHlShared; i += kThreads) S.hc[i] = 0;
+        __syncthreads();
       }
       field = f;
     }
     const ConstructArgs& A = T->a;
     const uint32_t b = t - base(f);
-    if (T->use_tma) {
-      // every thread observes the completion itself (acquire of the TMA writes); the
-      // phase advances only when the wait succeeded, so that after a timeout the drain
-      // below still waits on the phase of the copy that did not complete
-      if (mbar_wait(&S.bar[cur], phase[cur], spin_limit)) {
-        phase[cur] ^= 1u;
+    bool late = false;
+    if (T->use_tma && tma_ok) {
+      // every thread observes the completion itself (acquire of the TMA writes), so no
+      // barrier follows; the phase advances only when the wait succeeded, so that after
+      // a timeout the drain below still waits on the phase of the copy that did not
+      // complete.  A thread that gave up works on whatever the buffer holds (every index
+      // stays in range whatever the data) and the CTA leaves after the tile.
+      if (mbar_wait(&S.bar[cur], (phase >> cur) & 1u, spin_limit)) {
+        phase ^= 1u << cur;
       } else {
         atomicOr(&A.st->status, ERR_TIMEOUT);
-        s_fail = 1;
+        late = true;
       }
     } else {
       if (G) load_halo_threads<ND == 0 ? 3 : ND, E>(A, S.box[cur], S.in[cur]);
       else load_tile_threads(A, b, S.in[cur]);
+      __syncthreads();
     }
-    __syncthreads();
-    if (s_fail) break;
     const uint32_t* bx = S.box[cur];
     if constexpr (G) {
       static_assert(ND != 0, "global tiles: one dimensionality per launch");
@@ -808,18 +919,22 @@ __global__ __launch_bounds__(kThreads, 4) void construct_kernel(const __grid_con
         process_tile<2, E>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
       else process_tile<3, E>(A, b, bx, S, S.in[cur], n_rec_acc, n_patch_acc);
     }
-    __syncthreads();
+    if (__syncthreads_or(late)) {
+      failed = true;
+      break;
+    }
     cur ^= 1;
   }
   if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-  if (s_fail) {
+  if (failed) {
     // a fetch did not complete in time: wait once more (bounded) for both buffers'
-    // copies so no transfer outlives the CTA, then leave (phase[cur] still names the
-    // phase of the copy that timed out; phase[cur ^ 1] that of the one issued after it)
+    // copies so no transfer outlives the CTA, then leave (bit cur of `phase` still
+    // names the phase of the copy that timed out, bit cur ^ 1 that of the one issued
+    // after it)
     if (tid == 0) {
-      mbar_wait(&S.bar[cur], phase[cur], spin_limit);
-      if (s_f[cur ^ 1] >= 0 && task(s_f[cur ^ 1])->use_tma)
-        mbar_wait(&S.bar[cur ^ 1], phase[cur ^ 1], spin_limit);
+      mbar_wait(&S.bar[cur], (phase >> cur) & 1u, spin_limit);
+      if (s_f[cur ^ 1] >= 0 && task(s_f[cur ^ 1])->use_tma && tma_ok)
+        mbar_wait(&S.bar[cur ^ 1], (phase >> (cur ^ 1)) & 1u, spin_limit);
     }
     return;
   }
@@ -893,7 +1008,7 @@ void prepare_construct_task(ConstructTask& T) {
   if (rank == 1 && g.nelem >= (1ull << 32)) return;
   const CUresult r = fn(&T.tmap, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                         (cuuint32_t)rank, xp, dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE,
+                        rank == 3 && !f64 && !T.a.global ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   T.use_tma = r == CUDA_SUCCESS ? 1 : 0;
 }
