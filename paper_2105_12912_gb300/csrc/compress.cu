@@ -616,6 +616,61 @@ __device__ __forceinline__ int learned_pick(const float* y, bool& fallback) {
   return c;
 }
 
+// The network's parameters staged in shared memory for one forward pass per block:
+// the weight matrices transposed (the 32 lanes' weights for one input are consecutive
+// words) and padded to 33 words per row, so each multiply-add step of the warp reads
+// one conflict-free row instead of 32 scattered cache lines of the packed layout.
+constexpr int kSwW1 = 0;                     // [8][33]  W1 transposed
+constexpr int kSwB1 = kSwW1 + kMlpIn * 33;   // [32]
+constexpr int kSwW2 = kSwB1 + kMlpHid;       // [32][33] W2 transposed
+constexpr int kSwB2 = kSwW2 + kMlpHid * 33;  // [32]
+constexpr int kSwW3 = kSwB2 + kMlpHid;       // [3][33]  W3 rows
+constexpr int kSwB3 = kSwW3 + kMlpOut * 33;  // [3]
+constexpr int kSwWords = kSwB3 + kMlpOut;
+
+__device__ __forceinline__ void stage_mlp(const float* __restrict__ w, float* sw) {
+  for (int i = threadIdx.x; i < kMlpParams; i += kEncThreads) {
+    const float v = __ldg(&w[i]);
+    int d;
+    if (i < kMlpB1) {
+      d = kSwW1 + (i % kMlpIn) * 33 + i / kMlpIn;
+    } else if (i < kMlpW2) {
+      d = kSwB1 + (i - kMlpB1);
+    } else if (i < kMlpB2) {
+      const int k = i - kMlpW2;
+      d = kSwW2 + (k % kMlpHid) * 33 + k / kMlpHid;
+    } else if (i < kMlpW3) {
+      d = kSwB2 + (i - kMlpB2);
+    } else if (i < kMlpB3) {
+      const int k = i - kMlpW3;
+      d = kSwW3 + (k / kMlpHid) * 33 + k % kMlpHid;
+    } else {
+      d = kSwB3 + (i - kMlpB3);
+    }
+    sw[d] = v;
+  }
+}
+
+// mlp_forward_warp on the staged parameters: the same operands in the same order, so
+// the same FP32 results.  f: the 8 features (same in every lane).
+__device__ __forceinline__ void mlp_forward_staged(const float* sw, const float (&f)[kMlpIn], float* y) {
+  const int lane = threadIdx.x & 31;
+  float acc = sw[kSwB1 + lane];
+#pragma unroll
+  for (int j = 0; j < kMlpIn; j++) acc = fmaf(sw[kSwW1 + 33 * j + lane], f[j], acc);
+  const float h1 = acc > 0.0f ? acc : 0.0f;
+  acc = sw[kSwB2 + lane];
+#pragma unroll
+  for (int j = 0; j < kMlpHid; j++) acc = fmaf(sw[kSwW2 + 33 * j + lane], __shfl_sync(~0u, h1, j), acc);
+  const float h2 = acc > 0.0f ? acc : 0.0f;
+  const int o = lane < kMlpOut ? lane : 0;
+  acc = sw[kSwB3 + o];
+#pragma unroll
+  for (int j = 0; j < kMlpHid; j++) acc = fmaf(sw[kSwW3 + 33 * o + j], __shfl_sync(~0u, h2, j), acc);
+#pragma unroll
+  for (int c = 0; c < kMlpOut; c++) y[c] = __shfl_sync(~0u, acc, c);
+}
+
 // smallest exact size; ties prefer HUFF, then RLE_HUFF, then RLE
 __device__ __forceinline__ int exhaustive_pick(uint64_t sh, uint64_t sr, uint64_t srh) {
   int c = CODEC_HUFF;
@@ -675,6 +730,14 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
     uint4* dst = reinterpret_cast<uint4*>(s_c);
     for (int i = tid; i < kSlots / 8; i += kEncThreads) dst[i] = __ldcs(&src[i]);
   }
+  // the block statistics' code histogram (the first 1024 words of s_buf, which holds
+  // no payload until assembly) starts at zero, and the learned selector's parameters
+  // sit after it; both are ready at the barrier after the records
+  const bool analyze = a.analyze != 0;
+  static_assert(kNsymCode == 4 * kEncThreads && 4 * (kNsymCode + kSwWords) <= kBufBytes, "s_buf layout");
+  if (analyze || sel == SEL_HEURISTIC || sel == SEL_LEARNED)
+    reinterpret_cast<uint4*>(s_buf)[tid] = make_uint4(0u, 0u, 0u, 0u);
+  if (sel == SEL_LEARNED && !analyze) stage_mlp(a.mlp_w, reinterpret_cast<float*>(s_buf) + kNsymCode);
 
   // this block's outlier and patch records, in slot order, at its record offset
   if (a.place_records && a.rec.counts[b] != 0) {
@@ -722,7 +785,6 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   // Analysis (selector training data): every size and every feature of every block,
   // no payload.  Otherwise runs are counted in every mode except forced Huffman and
   // extracted (values, lengths) only when a run codec or the statistics need them.
-  const bool analyze = a.analyze != 0;
   uint32_t nr = 0;
   bool have_runs = false;
   // the run count comes from construction; the run index is built only when runs
@@ -793,9 +855,7 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
   if ((sel == SEL_HEURISTIC || sel == SEL_LEARNED) && !eligible && !analyze) {
     if (tid == 0) s_codec = CODEC_HUFF;  // both pick between Huffman and RLE+Huffman
   } else if (statistics) {
-    uint32_t* s_hist = s_buf;  // 1024 words, before the payload is assembled
-    for (int i = tid; i < kNsymCode; i += kEncThreads) s_hist[i] = 0;
-    __syncthreads();
+    uint32_t* s_hist = s_buf;  // 1024 words (zeroed above), before the payload is assembled
     for (uint32_t i = tid; i < nr; i += kEncThreads) atomicAdd(&s_hist[s_rv[i]], (uint32_t)s_rl[i]);
     __syncthreads();
     // block statistics in one pass and one reduction: entropy sum, |delta| sum, top
@@ -836,21 +896,17 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
       s_scan64[4 * wid + 3] = mism;
     }
     __syncthreads();
-    if (tid == 0) {
-      S_ = absd = 0;
-      f1 = maxd = mism = 0;
-      for (int v = 0; v < kEncThreads / 32; v++) {
-        S_ += s_scan64[4 * v + 0];
-        absd += s_scan64[4 * v + 1];
-        f1 = max(f1, (uint32_t)(s_scan64[4 * v + 2] >> 32));
-        maxd = max(maxd, (uint32_t)s_scan64[4 * v + 2]);
-        mism += (uint32_t)s_scan64[4 * v + 3];
-      }
-    }
     const int64_t Lm = log2_q16_small(m);
-    const int64_t NH = (int64_t)m * Lm - (int64_t)S_;  // meaningful in thread 0
+    __shared__ bool s_fallback;
     if (sel == SEL_HEURISTIC && !analyze) {
       if (tid == 0) {
+        S_ = 0;
+        f1 = 0;
+        for (int v = 0; v < kEncThreads / 32; v++) {
+          S_ += s_scan64[4 * v + 0];
+          f1 = max(f1, (uint32_t)(s_scan64[4 * v + 2] >> 32));
+        }
+        const int64_t NH = (int64_t)m * Lm - (int64_t)S_;
         int64_t Rm = 0;
         if (10ll * f1 > 4ll * m) {
           const int64_t rest = (int64_t)m - f1;
@@ -862,24 +918,67 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
         s_codec = (100 * est <= 109ll * (int64_t)m * 65536) ? CODEC_RLE_HUFF : CODEC_HUFF;
       }
     } else {
-      if (tid == 0) {
-        const uint32_t zero = s_hist[r];
-        const uint32_t outl = s_hist[0];
-        // pairs inside the block: positions j < m - d for each residue class j mod 8
-        uint32_t pairs = 0;
-        for (uint32_t k = 0; k < kMadoN; k++) {
-          const uint32_t d = kMadoD0 + kMadoStep * k;
-          if (m > d + k) pairs += (m - d - k + kMadoN - 1) / kMadoN;
+      if (wid == 0) {
+        // warp 0: the block totals (lane v < 8 brings warp v's partials), one feature
+        // per lane k < 8, then the network on the staged parameters
+        const int lane = tid & 31;
+        uint64_t tS = 0, tA = 0, tM = 0;
+        uint32_t tF = 0, tD = 0;
+        if (lane < kEncThreads / 32) {
+          tS = s_scan64[4 * lane + 0];
+          tA = s_scan64[4 * lane + 1];
+          tF = (uint32_t)(s_scan64[4 * lane + 2] >> 32);
+          tD = (uint32_t)s_scan64[4 * lane + 2];
+          tM = s_scan64[4 * lane + 3];
+        }
+        tS = warp_sum(tS);
+        tA = warp_sum(tA);
+        tM = warp_sum(tM);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          tF = max(tF, __shfl_xor_sync(~0u, tF, o));
+          tD = max(tD, __shfl_xor_sync(~0u, tD, o));
         }
         const float fm = (float)m;
-        s_feat[0] = (float)zero / fm;
-        s_feat[1] = (float)NH / (float)((uint64_t)m * 65536ull);
-        s_feat[2] = (float)f1 / fm;
-        s_feat[3] = (float)log2_q16_small(1u + maxd) / 65536.0f;
-        s_feat[4] = (float)nr / fm;
-        s_feat[5] = (float)outl / fm;
-        s_feat[6] = (float)absd / (float)((uint64_t)m * r);
-        s_feat[7] = pairs ? (float)mism / (float)pairs : 0.0f;
+        float fk = 0.0f;
+        if (lane == 0) {
+          fk = (float)s_hist[r] / fm;  // zero residuals
+        } else if (lane == 1) {
+          const int64_t NH = (int64_t)m * Lm - (int64_t)tS;
+          fk = (float)NH / (float)((uint64_t)m * 65536ull);
+        } else if (lane == 2) {
+          fk = (float)tF / fm;
+        } else if (lane == 3) {
+          fk = (float)log2_q16_small(1u + tD) / 65536.0f;
+        } else if (lane == 4) {
+          fk = (float)nr / fm;
+        } else if (lane == 5) {
+          fk = (float)s_hist[0] / fm;  // outliers
+        } else if (lane == 6) {
+          fk = (float)tA / (float)((uint64_t)m * r);
+        } else if (lane == 7) {
+          // pairs inside the block: positions j < m - d for each residue class j mod 8
+          uint32_t pairs = 0;
+          for (uint32_t k = 0; k < kMadoN; k++) {
+            const uint32_t d = kMadoD0 + kMadoStep * k;
+            if (m > d + k) pairs += (m - d - k + kMadoN - 1) / kMadoN;
+          }
+          fk = pairs ? (float)(uint32_t)tM / (float)pairs : 0.0f;
+        }
+        if (analyze) {
+          if (lane < kMlpIn) s_feat[lane] = fk;
+        } else {
+          float f[kMlpIn], y[kMlpOut];
+#pragma unroll
+          for (int j = 0; j < kMlpIn; j++) f[j] = __shfl_sync(~0u, fk, j);
+          mlp_forward_staged(reinterpret_cast<const float*>(s_buf) + kNsymCode, f, y);
+          bool fb;
+          const int c = learned_pick(y, fb);
+          if (lane == 0) {
+            s_codec = (uint32_t)c;
+            s_fallback = fb;
+          }
+        }
       }
       __syncthreads();
       if (analyze) {
@@ -896,18 +995,6 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
         }
         return;
       }
-      __shared__ bool s_fallback;
-      if (tid < 32) {
-        float y[kMlpOut];
-        mlp_forward_warp(a.mlp_w, s_feat, y);
-        bool fb;
-        const int c = learned_pick(y, fb);
-        if (tid == 0) {
-          s_codec = (uint32_t)c;
-          s_fallback = fb;
-        }
-      }
-      __syncthreads();
       if (s_fallback) {
         // the network is unsure: exact sizes decide
         exact_sizes(true, true, true);
