@@ -311,13 +311,13 @@ struct BookView {
   unsigned long long fullmask;
 };
 
-// Length of the codeword that is a prefix of the nb valid top bits of bb (0 if none
-// fits in nb bits), and its symbol.  Short codes come from the lookup table; longer
-// ones from the smallest length whose left-justified end exceeds bb, which is the
-// true length whenever it is <= nb (zero bits below nb cannot complete a shorter
-// codeword).
-// Codes longer than the lookup table's 12 bits: the smallest length whose codes end
-// above bb (a binary search over the canonical limits), checked to be a codeword.
+// Matching the next codeword among the nb valid top bits of bb.  A table code of
+// length l <= nb found among the zero-padded top 12 bits is the next codeword (no
+// codeword is a prefix of another).  A table miss with more than 12 bits at hand is
+// a longer code: its length is the smallest one whose left-justified codes end above
+// bb (a binary search over the canonical limits), the true length whenever it is <= nb
+// (zero bits below nb cannot complete a shorter codeword), checked to be a codeword.
+// Returns that length (0 if none fits in nb bits) and sets sym.
 __device__ __forceinline__ int ihs_match_long(uint64_t bb, int nb, const BookView& bk, int& sym) {
   int lo = kLutBits + 1, hi = bk.maxlen + 1;  // smallest k whose codes end above bb
   while (lo < hi) {
@@ -330,19 +330,6 @@ __device__ __forceinline__ int ihs_match_long(uint64_t bb, int nb, const BookVie
   if (c < bk.first[lo] || c - bk.first[lo] >= bk.count[lo]) return 0;  // not a codeword
   sym = (int)bk.sorted[bk.off[lo] + (uint32_t)(c - bk.first[lo])];
   return lo;
-}
-
-// The lookup-table hit needs no branch: a code of length l <= nb found among the
-// zero-padded top bits is the next codeword (no codeword is a prefix of another),
-// and nb <= 0 can never pass l <= nb.  Only a miss with more than 12 bits at hand
-// (a code longer than the table) takes the search.
-__device__ __forceinline__ int ihs_match(uint64_t bb, int nb, const BookView& bk, int& sym) {
-  const uint32_t e = bk.lut[bb >> (64 - kLutBits)];
-  const int l = (int)(e & 0xffu);
-  sym = (int)(e >> 8);
-  int ml = (l != 0 && l <= nb) ? l : 0;
-  if (l == 0 && nb > kLutBits) ml = ihs_match_long(bb, nb, bk, sym);
-  return ml;
 }
 
 // A warp's reader of one interleaved stream in[0..avail).  The warp reads the stream
@@ -378,29 +365,34 @@ struct IhsReader {
 
   // One decoding step of the 32 lanes (every lane calls): each active lane tops up
   // its bits in rounds until a codeword is complete, then consumes it.  Returns the
-  // symbol, meaningful where the lane was active and is not bad.
+  // symbol, meaningful where the lane was active and is not bad.  Control flow is
+  // warp-uniform: a round's unit goes in by selects, and the search for codes longer
+  // than the table runs only when some lane has one.
   __device__ __forceinline__ int step(bool active, const BookView& bk) {
     const uint32_t lane = threadIdx.x & 31;
-    active = active && !bad;
-    int sym = 0, ml = active ? ihs_match(bb, nb, bk, sym) : 0;
-    bool need = active && ml == 0;
-    uint32_t ballot;
-    while ((ballot = __ballot_sync(~0u, need)) != 0u) {
-      const uint32_t pos = cur + __popc(ballot & ((1u << lane) - 1u));
-      const uint32_t rel = pos - wbase;  // < 64 while cur - wbase < 32
+    const uint32_t lt = (1u << lane) - 1u;
+    const bool live = active && !bad;
+    uint32_t e = bk.lut[(uint32_t)(bb >> (64 - kLutBits))];
+    int l = (int)(e & 0xffu);
+    int sym = (int)(e >> 8);
+    int ml = (live && (uint32_t)(l - 1) < (uint32_t)nb) ? l : 0;  // a table code within the bits
+    bool lng = live && l == 0 && nb > kLutBits;
+    if (__any_sync(~0u, lng)) {
+      if (lng) ml = ihs_match_long(bb, nb, bk, sym);
+    }
+    bool need = live && ml == 0;
+    uint32_t ballot = __ballot_sync(~0u, need);
+    while (ballot != 0u) {
+      const uint32_t before = __popc(ballot & lt);
+      const uint32_t rel = cur - wbase + before;  // < 64 while cur - wbase < 32
       const uint32_t u0 = __shfl_sync(~0u, w0, rel & 31);
       const uint32_t u1 = __shfl_sync(~0u, w1, rel & 31);
-      if (need) {
-        if (nb > 64 - 16 || pos >= avail) {
-          bad = true;
-          need = false;
-        } else {
-          bb |= (uint64_t)(rel < 32 ? u0 : u1) << (48 - nb);
-          nb += 16;
-          ml = ihs_match(bb, nb, bk, sym);  // only lanes that took a unit look again
-          need = ml == 0;
-        }
-      }
+      const bool over = nb > 64 - 16 || cur + before >= avail;
+      bad = bad || (need && over);
+      const bool take = need && !over;
+      const uint64_t unit = (uint64_t)(rel < 32 ? u0 : u1) << ((48 - nb) & 63);
+      bb |= take ? unit : 0ull;
+      nb += take ? 16 : 0;
       cur += __popc(ballot);
       if (cur - wbase >= 32) {
         w0 = w1;
@@ -408,12 +400,24 @@ struct IhsReader {
         wbase += 32;
         w2 = fetch(wbase + 64 + lane);
       }
+      // only lanes that took a unit look again (a predicated load: the others add no
+      // shared-memory traffic)
+      e = take ? bk.lut[(uint32_t)(bb >> (64 - kLutBits))] : 0u;
+      l = (int)(e & 0xffu);
+      if (take && (uint32_t)(l - 1) < (uint32_t)nb) {
+        ml = l;
+        sym = (int)(e >> 8);
+      }
+      lng = take && l == 0 && nb > kLutBits;
+      if (__any_sync(~0u, lng)) {
+        if (lng) ml = ihs_match_long(bb, nb, bk, sym);
+      }
+      need = take && ml == 0;
+      ballot = __ballot_sync(~0u, need);
     }
-    if (active && !bad) {
-      bb = ml >= 64 ? 0ull : bb << ml;
-      nb -= ml;
-    }
-    return sym;
+    bb = ml >= 64 ? 0ull : bb << ml;  // ml = 0 where the lane consumes nothing
+    nb -= ml;
+    return live ? sym : 0;
   }
 };
 
