@@ -400,9 +400,8 @@ struct IhsReader {
         wbase += 32;
         w2 = fetch(wbase + 64 + lane);
       }
-      // only lanes that took a unit look again (a predicated load: the others add no
-      // shared-memory traffic)
-      e = take ? bk.lut[(uint32_t)(bb >> (64 - kLutBits))] : 0u;
+      // only lanes that took a unit look again
+      e = bk.lut[(uint32_t)(bb >> (64 - kLutBits))];
       l = (int)(e & 0xffu);
       if (take && (uint32_t)(l - 1) < (uint32_t)nb) {
         ml = l;
@@ -579,17 +578,22 @@ __device__ bool fused_decode_reconstruct(const DecodeArgs& a, uint32_t b, uint32
   }
 #pragma unroll 1
   for (uint32_t t0 = 0; t0 < 64; t0 += 8) {
-    // the decoding step stays rolled (one copy of its code: unrolling it overflows the
-    // instruction cache); each step's q' shifts into an 8-register window
+    // the decoding step runs two copies per iteration (four overflow the instruction
+    // cache); each pair of steps' q' shifts into an 8-register window
     int32_t q[8];
 #pragma unroll 1
-    for (uint32_t s = 0; s < 8; s++) {
-      const int sym = rd.step(true, bk);
-      int32_t v = sym - r;
-      rc.step(key0 + 64u * (t0 + s), sym, v, bad, s_tab);
+    for (uint32_t s0 = 0; s0 < 8; s0 += 2) {
 #pragma unroll
-      for (int k = 0; k < 7; k++) q[k] = q[k + 1];
-      q[7] = v;
+      for (uint32_t u = 0; u < 2; u++) {
+        const int sym = rd.step(true, bk);
+        int32_t v = sym - r;
+        rc.step(key0 + 64u * (t0 + s0 + u), sym, v, bad, s_tab);
+        q[6 + u] = v;
+      }
+      if (s0 + 2 < 8) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) q[k] = q[k + 2];
+      }
     }
     if (ND == 1) {
       // 8 steps = one 256-element chunk: per-step warp scans, then the carries
