@@ -355,7 +355,12 @@ def batched_comparison(args, dev, flush):
         "cr_loss_learned_vs_plain": res["learned"]["bytes"] / plain_bytes - 1.0,
         "construct_grid": res["learned"]["tuning"]["construct_grid"],
         "decoder_warps_per_cta": res["learned"]["decoder_warps"],
+        # the compression plan the autotuner kept (one persistent launch, or one launch
+        # per stage) and the batch times it measured for each with 1..4 CTAs per SM
+        "plan": {sel: ("persistent" if res[sel]["tuning"]["persistent"] else "staged") for sel in res},
         "autotune_ms": res["learned"]["tuning"]["tuned_ms"],
+        "autotune_persistent_ms": {sel: res[sel]["tuning"]["persist_ms"] for sel in res},
+        "autotune_staged_ms": {sel: res[sel]["tuning"]["tuned_ms"] for sel in res},
         "note": "GB/s of FP32 input; every timed pass is preceded by a 256 MiB L2 flush; the plain path "
                 "synchronises once per call (it returns each size / status to the host); round trips "
                 "are compression then decompression",

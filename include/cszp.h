@@ -191,13 +191,20 @@ csz_status csz_decompress_static(const uint8_t* d_archive, size_t bytes, float* 
                                  uint64_t out_cap_elems, void* stream);
 
 /*
- * Batched compression.  Many fields of any shape and dimensionality are compressed
- * by one launch per stage (value range, construction, books and record offsets,
- * encoding), each kernel walking a per-field table; the construction and encoding
- * kernels take the codec blocks of all fields from one ticket.  csz_batch_create
- * validates the fields, lays out the workspace, uploads the tables, optionally
- * autotunes the construction kernel's persistent grid on the batch (running it a
- * few times), and captures the launch sequence into a CUDA graph.  Each
+ * Batched compression (the batching pattern the build adds beyond the paper; each
+ * field is compressed as csz_compress does it, Alg. 1 and Sec. III).  Many fields of
+ * any shape and dimensionality are compressed by one persistent kernel launch: every
+ * CTA runs the stages (value range, construction, books and record offsets,
+ * encoding) as phases, taking the items of each phase from one ticket over all
+ * fields and waiting, bounded, only for the field hand-overs an earlier phase
+ * releases.  The staged plan, one launch per stage, is the alternative.
+ * csz_batch_create validates the fields, lays out the workspace, uploads the tables,
+ * chooses the plan (`autotune` flags: CSZ_BATCH_AUTOTUNE times every allowed
+ * candidate -- either plan with 1..4 resident CTAs per SM -- on the batch, running it
+ * a few times, and keeps the fastest; CSZ_BATCH_PERSISTENT or CSZ_BATCH_STAGED alone
+ * restricts the candidates to one plan; with neither flag and no tuning the plan is
+ * the persistent launch on every resident CTA), and captures it into a CUDA graph.
+ * Each
  * csz_batch_compress replays the graph on `stream` without synchronising; the
  * archives then hold exactly what csz_compress would write for each field with the
  * same options.  csz_batch_results synchronises and reads every field's archive
@@ -219,6 +226,11 @@ typedef struct {
 
 typedef struct csz_batch csz_batch;
 
+/* csz_batch_create `autotune` flags */
+#define CSZ_BATCH_AUTOTUNE 1   /* time the candidate plans on the batch, keep the fastest */
+#define CSZ_BATCH_STAGED 2     /* candidates: the staged launches */
+#define CSZ_BATCH_PERSISTENT 4 /* candidates: the single persistent launch */
+
 /* Workspace for a batch (0 if any field is invalid). */
 size_t csz_batch_workspace_bytes(int nfields, const csz_field* fields);
 csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_options* opt,
@@ -228,9 +240,14 @@ csz_status csz_batch_compress(csz_batch* batch, void* stream);
 /* h_bytes[nfields] / h_status[nfields] (either may be NULL); returns the first
    failing field's status, or CSZ_OK. */
 csz_status csz_batch_results(csz_batch* batch, uint64_t* h_bytes, int* h_status, void* stream);
-/* The construction grid the autotuner chose and the batch times (ms) it measured
-   with 1..4 resident CTAs per SM (0 where not tried). */
+/* The staged plan's construction grid the autotuner chose and the batch times (ms)
+   it measured with 1..4 resident CTAs per SM (0 where not tried). */
 csz_status csz_batch_info(const csz_batch* batch, int* construct_grid, double* tuned_ms);
+/* The plan the graph holds: *persistent = 1 for the single persistent launch (0 for
+   the staged launches), *grid its CTAs (the construction grid when staged), and
+   persist_ms[4] the batch times (ms) of the persistent plan with 1..4 resident CTAs
+   per SM (0 where not tried).  Any pointer may be NULL. */
+csz_status csz_batch_plan(const csz_batch* batch, int* persistent, int* grid, double* persist_ms);
 /*
  * Batched decompression, the counterpart of the above: one launch per stage (header
  * checks, set-up, entropy decoding, run expansion, reconstruction) for all fields,

@@ -75,6 +75,7 @@ SIGNATURES = {
     "csz_batch_compress": (C.c_int, [C.c_void_p, C.c_void_p]),
     "csz_batch_results": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int), C.c_void_p]),
     "csz_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "csz_batch_plan": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "csz_batch_destroy": (None, [C.c_void_p]),
     "csz_batch_last_error": (C.c_char_p, []),
     "csz_batch_dec_workspace_bytes": (C.c_size_t, [C.c_int, C.POINTER(csz_dfield)]),

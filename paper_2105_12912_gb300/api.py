@@ -241,15 +241,20 @@ def header(archive) -> dict:
 # ---------------------------------------------------------------------------------
 # batched compression (one launch per stage for all fields, replayed as a CUDA graph)
 # ---------------------------------------------------------------------------------
+BATCH_AUTOTUNE, BATCH_STAGED, BATCH_PERSISTENT = 1, 2, 4
+BATCH_PLANS = {"auto": 0, "staged": BATCH_STAGED, "persistent": BATCH_PERSISTENT}
+
+
 class BatchCompressor:
     """Compresses a fixed list of device fields together.  Construction lays out the
-    workspace, uploads the per-field tables, optionally autotunes and captures the
-    launch graph; run() replays it (no host synchronisation); results() reads sizes
+    workspace, uploads the per-field tables, chooses the plan (one persistent launch,
+    or one launch per stage; plan="auto" lets the autotuner time both), and captures
+    it as a graph; run() replays it (no host synchronisation); results() reads sizes
     and statuses.  The field tensors are referenced, not copied: overwrite them in
     place between runs to compress new data of the same shapes."""
 
     def __init__(self, fields, ebs, eb_modes="rel", select="exhaustive", radius=512, weights=None,
-                 autotune=True, archive_caps=None, stream=None):
+                 autotune=True, archive_caps=None, stream=None, plan="auto"):
         n = len(fields)
         if n == 0:
             raise ValueError("empty batch")
@@ -289,7 +294,8 @@ class BatchCompressor:
             opt.selector_weights = C.c_void_p(weights.data_ptr())
         h = C.c_void_p()
         st = L.lib().csz_batch_create(n, arr, C.byref(opt), C.c_void_p(self.workspace.data_ptr()), wsb,
-                                      1 if autotune else 0, _stream_ptr(stream), C.byref(h))
+                                      (BATCH_AUTOTUNE if autotune else 0) | BATCH_PLANS[plan],
+                                      _stream_ptr(stream), C.byref(h))
         if st != L.OK:
             raise L.CszError(st, "csz_batch_create (" + L.lib().csz_batch_last_error().decode() + ")")
         self._h = h
@@ -309,7 +315,11 @@ class BatchCompressor:
         g = C.c_int()
         ms = (C.c_double * 4)()
         L.lib().csz_batch_info(self._h, C.byref(g), ms)
-        return {"construct_grid": int(g.value), "tuned_ms": [float(v) for v in ms]}
+        p, pg = C.c_int(), C.c_int()
+        pms = (C.c_double * 4)()
+        L.lib().csz_batch_plan(self._h, C.byref(p), C.byref(pg), pms)
+        return {"construct_grid": int(g.value), "tuned_ms": [float(v) for v in ms],
+                "persistent": bool(p.value), "grid": int(pg.value), "persist_ms": [float(v) for v in pms]}
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -118,7 +118,11 @@ bool trace_suspend() {
 void trace_resume(bool on) { g_trace.on = on; }
 bool trace_on() { return g_trace.on; }
 void trace_fold() { trace_collect(); }
-void trace_count_batch() {
+void trace_count_batch(bool persistent) {
+  if (persistent) {
+    g_trace.launches[K_BATCH]++;
+    return;
+  }
   for (int k : {K_RANGE, K_CONSTRUCT, K_CODEBOOK, K_ENCODE}) g_trace.launches[k]++;
 }
 void trace_count_decode_batch() {
@@ -131,7 +135,7 @@ extern "C" {
 static const char* const kKernelNames[K_COUNT] = {
     "range", "abs_params", "construct", "codebook", "encode", "dec_setup",
     "stream_decode", "rle_expand", "reconstruct", "mlp_predict", "mlp_grad", "mlp_update", "dec_status",
-    "dec_header"};
+    "dec_header", "batch_persistent"};
 
 int csz_kernel_count(void) { return K_COUNT; }
 

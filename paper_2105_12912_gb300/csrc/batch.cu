@@ -1,9 +1,10 @@
 // Batched compression: many fields of any shape and dimensionality go through one
-// launch per stage -- range, construction, books and record offsets, encoding --
-// each kernel walking a per-field table in device memory (the construction and
-// encoding kernels take codec blocks of all fields from one ticket).  The launch
-// sequence is captured once into a CUDA graph and replayed; results stay on the
-// device until the caller reads them.  An autotuner picks the construction kernel's
+// persistent launch (batch_persistent_kernel: range, construction, books and record
+// offsets, encoding as phases of every CTA, handed over per field) or, as the staged
+// plan, one launch per stage, each kernel walking a per-field table in device memory
+// (the construction and encoding kernels take codec blocks of all fields from one
+// ticket).  The plan is captured once into a CUDA graph and replayed; results stay on
+// the device until the caller reads them.  An autotuner picks the plan and its
 // persistent grid (resident CTAs per SM) by timing the candidates on the batch.
 #include <cmath>
 #include <cstdio>
@@ -36,6 +37,11 @@ struct csz_batch {
   int common_nd = 0;       // the fields' dimensionality when they all share it, else 0
   int tuned_grid = 0;
   double tuned_ms[4] = {0, 0, 0, 0};
+  // the one-launch plan: every stage in batch_persistent_kernel
+  PersistArgs pargs{};
+  int persistent = 0;      // the graph holds the persistent kernel (else the staged launches)
+  int persist_grid = 0;
+  double persist_ms[4] = {0, 0, 0, 0};
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -87,7 +93,7 @@ FieldLayout field_layout(const Geom& g) {
 // tables, then the fields' own regions.
 struct BatchLayout {
   uint64_t tickets, states, hists, lb, zero_end;
-  uint64_t ctasks, tile0, rtasks, cta0, btasks, etasks, fields_begin;
+  uint64_t ctasks, tile0, rtasks, cta0, btasks, etasks, len_books, fields_begin;
   std::vector<uint64_t> lb_at, field_at;
   uint64_t total;
 };
@@ -121,6 +127,8 @@ BatchLayout batch_layout(const std::vector<Geom>& gs) {
   o += a256(sizeof(BookArgs) * F);
   B.etasks = o;
   o += a256(sizeof(EncodeArgs) * F);
+  B.len_books = o;  // the persistent kernel's run-length book working memory
+  o += a256(persist_len_book_bytes() * F);
   B.fields_begin = o;
   B.field_at.resize(F);
   for (uint64_t f = 0; f < F; f++) {
@@ -161,6 +169,17 @@ cudaError_t enqueue(const csz_batch* b, int construct_grid, cudaStream_t s) {
     return e;
   if ((e = launch_codebook_batch(b->btasks, b->nfields, s)) != cudaSuccess) return e;
   return launch_encode_batch(b->etasks, b->tile0, b->nfields, b->ntiles, &b->tickets[1], s);
+}
+
+// The same batch as one launch of the persistent kernel.
+cudaError_t enqueue_persistent(const csz_batch* b, int grid, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, s);
+  if (e != cudaSuccess) return e;
+  return launch_batch_persistent(b->pargs, grid, b->common_nd, s);
+}
+
+cudaError_t enqueue_plan(const csz_batch* b, cudaStream_t s) {
+  return b->persistent ? enqueue_persistent(b, b->persist_grid, s) : enqueue(b, b->construct_grid, s);
 }
 
 }  // namespace
@@ -337,35 +356,78 @@ csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_opti
     return CSZ_E_CUDA;
   }
 
-  // autotune the construction grid: resident CTAs per SM 1..max, timed on the batch
+  // the persistent kernel's tables (its argument block, passed by value)
+  PersistArgs& P = b->pargs;
+  P.rtasks = b->rtasks;
+  P.cta0 = b->cta0;
+  P.nrange = b->nrange;
+  P.ctasks = b->ctasks;
+  P.tile0 = b->tile0;
+  P.ntiles = tiles;
+  P.btasks = b->btasks;
+  P.len_books = ws + B.len_books;
+  P.etasks = b->etasks;
+  P.nfields = nfields;
+  P.tickets = b->tickets;
+  P.spin_limit = kSpinLimit;
+
+  // The plan: one persistent launch (default) or the staged launches, and its grid.
+  // With CSZ_BATCH_AUTOTUNE every allowed candidate is timed on the batch (resident
+  // CTAs per SM 1..4 for either plan) and the fastest is kept; the archives do not
+  // depend on the choice.
+  const bool allow_staged = (autotune & CSZ_BATCH_STAGED) || !(autotune & CSZ_BATCH_PERSISTENT);
+  const int pmax = persist_grid_max();
+  const bool allow_persist = pmax > 0 && ((autotune & CSZ_BATCH_PERSISTENT) || !(autotune & CSZ_BATCH_STAGED));
   const int full = construct_grid(tiles);
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->tuned_grid = full;
-  if (autotune && sms > 0) {
+  b->construct_grid = full;
+  b->persist_grid = pmax;
+  b->persistent = allow_persist ? 1 : 0;
+  if ((autotune & CSZ_BATCH_AUTOTUNE) && sms > 0) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 0.0f;
-    for (int k = 1; k <= 4; k++) {
-      int grid = sms * k;
-      if (grid > full) grid = full;
-      float ms = 0.0f;
+    auto time_it = [&](bool persist, int grid, float& ms) {
       for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
         cudaEventRecord(e0, s);
-        e = enqueue(b, grid, s);
+        e = persist ? enqueue_persistent(b, grid, s) : enqueue(b, grid, s);
         cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
       }
+    };
+    for (int k = 1; k <= 4 && allow_staged && e == cudaSuccess; k++) {
+      int grid = sms * k;
+      if (grid > full) grid = full;
+      float ms = 0.0f;
+      time_it(false, grid, ms);
       if (e != cudaSuccess) break;
       b->tuned_ms[k - 1] = ms;
       if (best == 0.0f || ms < best) {
         best = ms;
         b->tuned_grid = grid;
+        b->construct_grid = grid;
+        b->persistent = 0;
       }
       if (grid == full) break;
+    }
+    for (int k = 1; k <= 4 && allow_persist && e == cudaSuccess; k++) {
+      int grid = sms * k;
+      if (grid > pmax) grid = pmax;
+      float ms = 0.0f;
+      time_it(true, grid, ms);
+      if (e != cudaSuccess) break;
+      b->persist_ms[k - 1] = ms;
+      if (best == 0.0f || ms < best) {
+        best = ms;
+        b->persist_grid = grid;
+        b->persistent = 1;
+      }
+      if (grid == pmax) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -374,7 +436,6 @@ csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_opti
       return CSZ_E_CUDA;
     }
   }
-  b->construct_grid = b->tuned_grid;
 
   // capture the launch sequence once, on a private stream (the caller's may be the
   // legacy default stream, which cannot be captured); replays go to any stream
@@ -388,7 +449,7 @@ csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_opti
     step = "begin capture";
   }
   if (e == cudaSuccess) {
-    const cudaError_t e2 = enqueue(b, b->construct_grid, cap);
+    const cudaError_t e2 = enqueue_plan(b, cap);
     e = cudaStreamEndCapture(cap, &graph);
     step = "end capture";
     if (e == cudaSuccess && e2 != cudaSuccess) {
@@ -418,13 +479,12 @@ csz_status csz_batch_compress(csz_batch* b, void* stream) {
   if (trace_on()) {
     // with tracing on, the graph's launches run one by one so that each gets its
     // events, and the call waits for them (tracing is a diagnostic mode)
-    if (enqueue(b, b->construct_grid, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
-      return CSZ_E_CUDA;
+    if (enqueue_plan(b, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return CSZ_E_CUDA;
     trace_fold();
     return CSZ_OK;
   }
   if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return CSZ_E_CUDA;
-  trace_count_batch();
+  trace_count_batch(b->persistent != 0);
   return CSZ_OK;
 }
 
@@ -452,6 +512,15 @@ csz_status csz_batch_info(const csz_batch* b, int* construct_grid, double* tuned
   if (construct_grid) *construct_grid = b->construct_grid;
   if (tuned_ms)
     for (int i = 0; i < 4; i++) tuned_ms[i] = b->tuned_ms[i];
+  return CSZ_OK;
+}
+
+csz_status csz_batch_plan(const csz_batch* b, int* persistent, int* grid, double* persist_ms) {
+  if (!b) return CSZ_E_ARG;
+  if (persistent) *persistent = b->persistent;
+  if (grid) *grid = b->persistent ? b->persist_grid : b->construct_grid;
+  if (persist_ms)
+    for (int i = 0; i < 4; i++) persist_ms[i] = b->persist_ms[i];
   return CSZ_OK;
 }
 

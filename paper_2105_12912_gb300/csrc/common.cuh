@@ -116,6 +116,11 @@ struct DevState {
   // double-precision fields: value range as order keys, quantization step and inverse
   unsigned long long range64_lo_inv, range64_hi;
   double step_d, rstep_d;
+  // batched persistent kernel: phase hand-overs of this field (released by the
+  // producer, acquired by the consumer)
+  uint32_t ready_range;    // 1 once the bound is derived
+  uint32_t tiles_flushed;  // tiles whose histograms, counts and codes are in place
+  uint32_t books_done;     // book-phase items finished (three books and the record offsets)
 };
 
 // ---------------------------------------------------------------------------------
@@ -915,6 +920,30 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+// Ends an mbarrier's life, so that its shared-memory words can hold other data.
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Sets the flag *p to 1 with release semantics at GPU scope: what the calling thread
+// wrote before is visible to a thread that reads the 1 with acquire semantics.
+__device__ __forceinline__ void release_flag(uint32_t* p) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(1u) : "memory");
+}
+
+// Bounded wait (one thread) until the counter *p reaches `target`, read with acquire
+// semantics at GPU scope, so that what the producers wrote before their release is
+// visible after it; false when `limit` polls (about 64 ns apart) pass first.
+__device__ __forceinline__ bool wait_ge_acquire(const uint32_t* p, uint32_t target, uint32_t limit) {
+  for (uint32_t i = 0;; i++) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    if (v >= target) return true;
+    if (i >= limit) return false;
+    __nanosleep(64);
+  }
 }
 
 // Bounded wait for phase `parity` of an mbarrier: at most `limit` tries, each

@@ -11,6 +11,7 @@
 //                                     look-back, payload
 //   (the block counted last)          header, padding, books
 #include "common.cuh"
+#include "construct_body.cuh"
 #include "kernels.h"
 
 namespace cszp {
@@ -142,8 +143,10 @@ __global__ __launch_bounds__(256) void range_d_kernel(const double* __restrict__
 
 // Grid-stride min/max with float4 loads; non-finite values are flagged.  The last CTA
 // to finish derives the error bound.
+// ready (batched persistent kernel only, else nullptr): released as 1 by the last CTA
+// once the bound is derived or found impossible.
 __device__ __forceinline__ void range_body(const float* __restrict__ x, uint64_t n, DevState* st, int mode, double eb,
-                           uint32_t cta, uint32_t nctas) {
+                           uint32_t cta, uint32_t nctas, uint32_t* ready = nullptr) {
   __shared__ uint32_t s_red[2][33];
   __shared__ bool s_last;
   uint32_t lo_inv = 0, hi = 0, bad = 0;
@@ -217,9 +220,10 @@ __device__ __forceinline__ void range_body(const float* __restrict__ x, uint64_t
     uint32_t b = atomicAdd(&st->range_hi, 0u);
     if (b == 0) {  // nothing finite was seen
       atomicOr(&st->status, ERR_NONFINITE);
-      return;
+    } else {
+      derive_eb(st, mode, eb, key_to_float(~a), key_to_float(b));
     }
-    derive_eb(st, mode, eb, key_to_float(~a), key_to_float(b));
+    if (ready) release_flag(ready);
   }
 }
 
@@ -300,7 +304,7 @@ __device__ void record_offsets_body(const BookArgs& a) {
   const int tid = threadIdx.x;
   const uint32_t nblk = a.nblk;
   uint64_t carry = 0;
-  for (uint32_t base = 0; base < nblk; base += kBookThreads * kPerThread) {
+  for (uint32_t base = 0; base < nblk; base += blockDim.x * kPerThread) {
     const uint32_t b0 = base + tid * kPerThread;
     uint32_t c[kPerThread];
     uint64_t mine = 0;
@@ -321,10 +325,17 @@ __device__ void record_offsets_body(const BookArgs& a) {
   }
 }
 
+// Working memory of one book over nsym symbols: len nsym B | sym 2 nsym | weight by
+// node 8 nsym | parent by node 4 nsym | region A 8 nsym (sort keys, live node list,
+// canonical scratch) | region B 8 nsym (sort scratch, new nodes, depth pass).
+__host__ __device__ constexpr uint32_t book_mem_bytes(int nsym) { return 31u * (uint32_t)nsym; }
+
 // One canonical book (role 0 code, 1 run value, 2 run length) or, role 3, the
-// record offsets of a field.
-__device__ void codebook_body(const BookArgs& a, int role) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// record offsets of a field, by a CTA of NT threads.  mem: book_mem_bytes(nsym) of
+// working memory, shared (the book kernels) or global (the batched persistent
+// kernel's run-length books).
+template <int NT>
+__device__ void codebook_core(const BookArgs& a, int role, unsigned char* mem) {
   if (role == 3) {
     record_offsets_body(a);
     return;
@@ -335,12 +346,12 @@ __device__ void codebook_body(const BookArgs& a, int role) {
   uint8_t* len_out = a.lens + (book == 0 ? 0 : (book == 1 ? kNsymCode : 2 * kNsymCode));
   uint64_t* code_out = a.codes + (book == 0 ? 0 : (book == 1 ? kNsymCode : 2 * kNsymCode));
 
-  uint8_t* s_len = smem;                                                       // 4096
-  uint16_t* s_sym = reinterpret_cast<uint16_t*>(smem + 4096);                  // 4096
-  uint32_t* s_wt = reinterpret_cast<uint32_t*>(smem + 12288);                  // 8192
-  uint16_t* s_par = reinterpret_cast<uint16_t*>(smem + 45056);                 // 8192
-  uint64_t* A = reinterpret_cast<uint64_t*>(smem + 61440);                     // 4096
-  uint64_t* B = reinterpret_cast<uint64_t*>(smem + 94208);                     // 4096
+  uint8_t* s_len = mem;
+  uint16_t* s_sym = reinterpret_cast<uint16_t*>(mem + nsym);
+  uint32_t* s_wt = reinterpret_cast<uint32_t*>(mem + 3 * nsym);
+  uint16_t* s_par = reinterpret_cast<uint16_t*>(mem + 11 * nsym);
+  uint64_t* A = reinterpret_cast<uint64_t*>(mem + 15 * nsym);
+  uint64_t* B = reinterpret_cast<uint64_t*>(mem + 23 * nsym);
   __shared__ uint32_t s_L;
   __shared__ int s_n, s_k, s_next;
   __shared__ CanonSmem cs;
@@ -408,8 +419,8 @@ __device__ void codebook_body(const BookArgs& a, int role) {
       }
       __syncthreads();
       const int nr = n - 2 * k;
-      uint64_t mine[4];
-      int dst[4], cnt = 0;
+      uint64_t mine[(kNsymLen + NT - 1) / NT];
+      int dst[(kNsymLen + NT - 1) / NT], cnt = 0;
       for (int i = tid; i < n - k; i += blockDim.x) {
         const bool from_rest = i < nr;
         const uint64_t x = from_rest ? A[2 * k + i] : B[i - nr];
@@ -479,7 +490,7 @@ __device__ void codebook_body(const BookArgs& a, int role) {
     __syncthreads();
     // depths by pointer jumping (region B)
     uint16_t* s_anc = reinterpret_cast<uint16_t*>(B);
-    uint16_t* s_dep = s_anc + 2 * kNsymLen;
+    uint16_t* s_dep = s_anc + 2 * nsym;
     for (int i = tid; i < nn; i += blockDim.x) {
       s_anc[i] = s_par[i];
       s_dep[i] = (i == nn - 1) ? 0 : 1;
@@ -487,7 +498,7 @@ __device__ void codebook_body(const BookArgs& a, int role) {
     __syncthreads();
     // (done once every node's ancestor is the root: the depths no longer change)
     for (int step = 1; step < nn; step <<= 1) {
-      uint16_t na[8], nd[8];
+      uint16_t na[(2 * kNsymLen + NT - 1) / NT], nd[(2 * kNsymLen + NT - 1) / NT];
       int c = 0;
       bool open = false;
       for (int i = tid; i < nn; i += blockDim.x) {
@@ -517,14 +528,18 @@ __device__ void codebook_body(const BookArgs& a, int role) {
   canonical_build(s_len, nsym, &cs, reinterpret_cast<uint16_t*>(A), code_out, nullptr);
 }
 
-__global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) { codebook_body(a, blockIdx.x); }
+__global__ __launch_bounds__(kBookThreads) void codebook_kernel(BookArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  codebook_core<kBookThreads>(a, blockIdx.x, smem);
+}
 
 // Batch: four CTAs per field (three books and the record offsets).
 __global__ __launch_bounds__(kBookThreads) void codebook_batch_kernel(const BookArgs* __restrict__ tasks) {
-  codebook_body(tasks[blockIdx.x >> 2], blockIdx.x & 3);
+  extern __shared__ __align__(16) unsigned char smem[];
+  codebook_core<kBookThreads>(tasks[blockIdx.x >> 2], blockIdx.x & 3, smem);
 }
 
-static size_t codebook_smem_bytes() { return 94208 + kNsymLen * 8; }
+static size_t codebook_smem_bytes() { return book_mem_bytes(kNsymLen); }
 
 // =================================================================================
 // per-block selection and encoding
@@ -696,8 +711,8 @@ __device__ __forceinline__ uint32_t units_from_partials(const uint32_t* part) {
 static_assert(kEncThreads % kMadoN == 0, "madogram distances by thread");
 
 // Selection and encoding of codec block b of one field (all threads of the CTA).
-__device__ void encode_body(const EncodeArgs& a, uint32_t b) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// smem: encode_smem_bytes() of dynamic shared memory.
+__device__ void encode_body(const EncodeArgs& a, uint32_t b, unsigned char* smem) {
   uint16_t* s_c = reinterpret_cast<uint16_t*>(smem);             // 4096 codes
   uint16_t* s_rv = s_c + kSlots;                                 // run values
   uint16_t* s_rl = s_rv + kSlots;                                // run lengths
@@ -1091,9 +1106,10 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b) {
 // blocks that CTAs already hold.
 __global__ __launch_bounds__(kEncThreads, 5) void encode_kernel(EncodeArgs a) {
   __shared__ uint32_t s_tile;
+  extern __shared__ __align__(16) unsigned char smem[];
   if (threadIdx.x == 0) s_tile = atomicAdd(&a.st->ticket_encode, 1u);
   __syncthreads();
-  encode_body(a, s_tile);
+  encode_body(a, s_tile, smem);
 }
 
 // Batch: one CTA per codec block of every field; the ticket runs over the blocks of
@@ -1115,11 +1131,156 @@ __global__ __launch_bounds__(kEncThreads, 5) void encode_batch_kernel(const Enco
     s_tile = t - tile0[lo];
   }
   __syncthreads();
-  encode_body(tasks[s_field], s_tile);
+  extern __shared__ __align__(16) unsigned char smem[];
+  encode_body(tasks[s_field], s_tile, smem);
 }
 
 static size_t encode_smem_bytes() {
   return kSlots * 2 * 3 + kBufBytes + (kSlots / 32) * 4 * 3 + 16 + 2 * kEncThreads * 4 + 34 * 4 + 33 * 8 + 16;
+}
+
+// =================================================================================
+// batched compression in one persistent launch
+// =================================================================================
+// Every CTA runs the four phases of the staged batch in order, so the work items of
+// each phase are taken (by ticket) only after those of the phases before it were all
+// taken: a waiting CTA waits on items that running CTAs hold, and those wait only on
+// earlier phases, so with every CTA resident the launch cannot deadlock.  The
+// hand-overs are per field (DevState ready_range, tiles_flushed, books_done: a
+// release by the producer, an acquire by thread 0 of the consumer, then a CTA
+// barrier), so one field's books and encoding start while other fields are still
+// being constructed.  Every wait is bounded (ERR_TIMEOUT in the field's status).
+// The output is the staged path's, byte for byte: the same bodies run on the same
+// items.
+constexpr int kPersistThreads = 256;
+static_assert(kPersistThreads == kEncThreads, "one CTA shape for every phase");
+
+__device__ __forceinline__ int field_of_prefix(const uint32_t* prefix, int nfields, uint32_t c) {
+  int lo = 0, hi = nfields - 1;  // last field with prefix[f] <= c
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// thread 0 draws the next item of a phase; every thread gets it (two barriers, so the
+// word is free for the next draw)
+__device__ __forceinline__ uint32_t draw_item(uint32_t* ticket, uint32_t* s_word) {
+  if (threadIdx.x == 0) *s_word = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const uint32_t v = *s_word;
+  __syncthreads();
+  return v;
+}
+
+// thread 0 waits for a field's hand-over counter, then the CTA proceeds together
+__device__ __forceinline__ void await_field(const uint32_t* counter, uint32_t target, DevState* st, uint32_t limit) {
+  if (threadIdx.x == 0 && !wait_ge_acquire(counter, target, limit)) atomicOr(&st->status, ERR_TIMEOUT);
+  __syncthreads();
+}
+
+template <int ND>
+__global__ __launch_bounds__(kPersistThreads, 4) void batch_persistent_kernel(const __grid_constant__ PersistArgs p) {
+  // the construction phase's swizzled TMA tiles want 1024-byte aligned buffers; the
+  // alignment is taken here (1 KB of slack in the dynamic size) rather than declared,
+  // which would pad the static shared memory of every kernel in this file
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  unsigned char* smem_raw = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+  __shared__ uint32_t s_word;
+  const int tid = threadIdx.x;
+  // ---- phase 1: value ranges and bounds ---------------------------------------------
+  while (true) {
+    const uint32_t c = draw_item(&p.tickets[2], &s_word);
+    if (c >= p.nrange) break;
+    const int f = field_of_prefix(p.cta0, p.nfields, c);
+    const RangeTask& t = p.rtasks[f];
+    if (t.mode == 0) {
+      if (tid == 0) {
+        derive_eb(t.st, 0, t.eb, 0.0f, 0.0f);
+        release_flag(&t.st->ready_range);
+      }
+    } else {
+      range_body(t.x, t.n, t.st, t.mode, t.eb, c - p.cta0[f], p.cta0[f + 1] - p.cta0[f], &t.st->ready_range);
+    }
+    __syncthreads();
+  }
+  // ---- phase 2: construction (waits for each field's bound) ---------------------------
+  cons::construct_loop<ND, float, false, true>(p.ctasks[0], p.ctasks, p.tile0, p.nfields, p.ntiles, &p.tickets[0],
+                                               p.spin_limit, smem_raw);
+  // ---- phase 3: books and record offsets (wait for each field's tiles) ---------------
+  while (true) {
+    const uint32_t j = draw_item(&p.tickets[3], &s_word);
+    if (j >= 4u * (uint32_t)p.nfields) break;
+    const int f = (int)(j >> 2), role = (int)(j & 3);
+    const BookArgs& ba = p.btasks[f];
+    await_field(&ba.st->tiles_flushed, p.tile0[f + 1] - p.tile0[f], ba.st, p.spin_limit);
+    unsigned char* mem = role == 2 ? p.len_books + (size_t)f * book_mem_bytes(kNsymLen) : smem_raw;
+    codebook_core<kPersistThreads>(ba, role, mem);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(&ba.st->books_done, 1u);
+    }
+  }
+  // ---- phase 4: encoding (waits for each field's books) -------------------------------
+  int ready_field = -1;
+  while (true) {
+    const uint32_t t = draw_item(&p.tickets[1], &s_word);
+    if (t >= p.ntiles) break;
+    const int f = field_of_prefix(p.tile0, p.nfields, t);
+    const EncodeArgs& ea = p.etasks[f];
+    if (f != ready_field) {
+      await_field(&ea.st->books_done, 4u, ea.st, p.spin_limit);
+      ready_field = f;
+    }
+    encode_body(ea, t - p.tile0[f], smem_raw);
+    __syncthreads();
+  }
+}
+
+static size_t persist_smem_bytes() {
+  size_t b = construct_smem_bytes();
+  if (encode_smem_bytes() > b) b = encode_smem_bytes();
+  if (book_mem_bytes(kNsymCode) > b) b = book_mem_bytes(kNsymCode);
+  return b + 1024;  // alignment slack
+}
+
+size_t persist_len_book_bytes() { return book_mem_bytes(kNsymLen); }
+
+template <int ND>
+static int persist_occupancy() {
+  static int occ = -1;
+  if (occ < 0) {
+    const int sm = (int)persist_smem_bytes();
+    if (cudaFuncSetAttribute(batch_persistent_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_persistent_kernel<ND>, kPersistThreads, sm) !=
+            cudaSuccess)
+      occ = 0;
+  }
+  return occ;
+}
+
+int persist_grid_max() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int occ = persist_occupancy<0>();
+  for (int o : {persist_occupancy<1>(), persist_occupancy<2>(), persist_occupancy<3>()})
+    if (o < occ) occ = o;
+  return occ * (sms > 0 ? sms : 0);
+}
+
+cudaError_t launch_batch_persistent(const PersistArgs& p, int grid, int nd, cudaStream_t s) {
+  auto k = nd == 1 ? batch_persistent_kernel<1>
+                   : (nd == 2 ? batch_persistent_kernel<2> : (nd == 3 ? batch_persistent_kernel<3> : batch_persistent_kernel<0>));
+  if (grid <= 0 || grid > persist_grid_max()) return cudaErrorInvalidConfiguration;
+  trace_begin(K_BATCH, s);
+  k<<<grid, kPersistThreads, persist_smem_bytes(), s>>>(p);
+  trace_end(K_BATCH, s);
+  return cudaGetLastError();
 }
 
 // =================================================================================

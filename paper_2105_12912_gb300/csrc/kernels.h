@@ -176,6 +176,7 @@ enum KernelId : int {
   K_MLP_UPDATE,
   K_DEC_STATUS,
   K_DEC_HEADER,
+  K_BATCH,  // the batched persistent compression kernel
   K_COUNT
 };
 void trace_begin(int id, cudaStream_t s);
@@ -184,7 +185,7 @@ bool trace_suspend();           // stop event tracing (stream capture); returns 
 bool trace_on();                // event tracing is enabled
 void trace_fold();              // fold the recorded events into the totals (after a synchronisation)
 void trace_resume(bool on);
-void trace_count_batch();       // one replay of a compression batch graph: count its launches
+void trace_count_batch(bool persistent);  // one replay of a compression batch graph: count its launches
 void trace_count_decode_batch();  // the same for a decompression batch graph
 
 // ---- launchers (return cudaGetLastError of the launch) ---------------------------
@@ -208,6 +209,30 @@ cudaError_t launch_range_batch(const RangeTask* d_tasks, const uint32_t* d_cta0,
 cudaError_t launch_codebook_batch(const BookArgs* d_tasks, int nfields, cudaStream_t s);
 cudaError_t launch_encode_batch(const EncodeArgs* d_tasks, const uint32_t* d_tile0, int nfields, uint32_t ntiles,
                                 uint32_t* ticket, cudaStream_t s);
+
+// Batched compression as one persistent kernel: every CTA goes through the same
+// four phases in order, taking work items from one ticket per phase -- value-range
+// CTAs (cta0 prefix), construction tiles, the four book-phase items of each field,
+// encoding blocks -- and waits (bounded) only on the hand-over counters of
+// DevState that an earlier phase releases, so the whole batch is one launch.
+struct PersistArgs {
+  const RangeTask* rtasks;
+  const uint32_t* cta0;  // nfields + 1
+  uint32_t nrange;
+  const ConstructTask* ctasks;
+  const uint32_t* tile0;  // nfields + 1
+  uint32_t ntiles;
+  const BookArgs* btasks;
+  unsigned char* len_books;  // nfields x persist_len_book_bytes(): working memory of the run-length books
+  const EncodeArgs* etasks;
+  int nfields;
+  uint32_t* tickets;  // [0] construction, [1] encoding, [2] value range, [3] books
+  uint32_t spin_limit;
+};
+size_t persist_len_book_bytes();
+int persist_grid_max();  // resident CTAs of the persistent kernel on this GPU (all SMs)
+// grid <= persist_grid_max(); nd: the fields' common dimensionality, 0 if mixed
+cudaError_t launch_batch_persistent(const PersistArgs& p, int grid, int nd, cudaStream_t s);
 
 cudaError_t launch_decode(const DecodeArgs& a, cudaStream_t s);
 // the decompression's csz_status into a device word (asynchronous decompression)

@@ -1,10 +1,11 @@
-"""Batched compression: one launch per stage for all fields, replayed as a CUDA graph.
+"""Batched compression, replayed as a CUDA graph: one persistent launch for all fields
+(plan "persistent") or one launch per stage (plan "staged").
 
 Every field's archive from the batch must be byte-identical to what the single-field
-call writes (and, for a sample, to the oracle's), across mixed dimensionalities,
-REL/ABS bounds, shapes whose rows TMA cannot describe (x extent not a multiple of 4,
-offset base pointers), fields with errors (which must not disturb the others), and
-repeated graph replays with new data in the same buffers.
+call writes (and, for a sample, to the oracle's), under both plans, across mixed
+dimensionalities, REL/ABS bounds, shapes whose rows TMA cannot describe (x extent not
+a multiple of 4, offset base pointers), fields with errors (which must not disturb the
+others), and repeated graph replays with new data in the same buffers.
 """
 import numpy as np
 import pytest
@@ -43,11 +44,17 @@ def _single(api, x, eb, mode, sel="exhaustive", weights=None):
     return st, ar[:nb].cpu().numpy() if st == 0 else None
 
 
+PLANS = ["persistent", "staged"]
+
+
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("sel", ["exhaustive", "heuristic", "huff", "rle_huff"])
-def test_batch_matches_single_field_calls(gpu, sel):
+def test_batch_matches_single_field_calls(gpu, sel, plan):
     fields = _mixed_fields(1)
     xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
-    bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields], select=sel)
+    bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields], select=sel, plan=plan,
+                             autotune=False)
+    assert bc.info()["persistent"] == (plan == "persistent")
     bc.run()
     sizes, stats = bc.results()
     for i, (x, eb, mode) in enumerate(fields):
@@ -79,14 +86,15 @@ def test_batch_matches_oracle_and_replays(gpu, orc):
             assert np.array_equal(y.cpu().numpy().ravel().view(np.uint32), yr.view(np.uint32))
 
 
-def test_batch_without_tma_layouts(gpu):
+@pytest.mark.parametrize("plan", PLANS)
+def test_batch_without_tma_layouts(gpu, plan):
     """Rows whose byte pitch is not a multiple of 16 and base pointers off 16 bytes
     take the thread-loaded path."""
     rng = np.random.default_rng(3)
     base = torch.from_numpy(rng.standard_normal(200000).astype(np.float32).cumsum()).cuda()
     xs = [base[1:1 + 150 * 203].view(150, 203), base[3:3 + 9 * 31 * 33].view(9, 31, 33), base[5:5 + 77777],
           base[:64 * 64].view(64, 64)]
-    bc = gpu.BatchCompressor(xs, 1e-3, "rel", autotune=False)
+    bc = gpu.BatchCompressor(xs, 1e-3, "rel", autotune=False, plan=plan)
     bc.run()
     sizes, stats = bc.results()
     for i, x in enumerate(xs):
@@ -95,7 +103,8 @@ def test_batch_without_tma_layouts(gpu):
         assert np.array_equal(bc.archives[i][:sizes[i]].cpu().numpy(), ref), i
 
 
-def test_batch_errors_stay_per_field(gpu):
+@pytest.mark.parametrize("plan", PLANS)
+def test_batch_errors_stay_per_field(gpu, plan):
     rng = np.random.default_rng(4)
     good = torch.from_numpy(rng.standard_normal((64, 70)).astype(np.float32).cumsum(1)).cuda()
     nan = good.clone()
@@ -103,7 +112,8 @@ def test_batch_errors_stay_per_field(gpu):
     const = torch.full((50, 50), 2.5, device="cuda")
     big = torch.tensor([0.0, 1e7, 0.0], device="cuda")
     xs = [good, nan, const, big, good.clone()]
-    bc = gpu.BatchCompressor(xs, [1e-3, 1e-3, 1e-3, 0.5, 1e-3], ["rel", "rel", "rel", "abs", "rel"])
+    bc = gpu.BatchCompressor(xs, [1e-3, 1e-3, 1e-3, 0.5, 1e-3], ["rel", "rel", "rel", "abs", "rel"], plan=plan,
+                             autotune=False)
     bc.run()
     sizes, stats = bc.results()
     assert stats == [0, 2, 1, 3, 0]
@@ -112,12 +122,14 @@ def test_batch_errors_stay_per_field(gpu):
     assert np.array_equal(bc.archives[4][:sizes[4]].cpu().numpy(), ref)
 
 
-def test_batch_learned_selector(gpu, orc):
+@pytest.mark.parametrize("plan", PLANS)
+def test_batch_learned_selector(gpu, orc, plan):
     from paper_2105_12912_gb300 import selector
     fields = _mixed_fields(5)
     xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
     w = selector.init_weights(2) * 2.0
-    bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields], select="learned", weights=w)
+    bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields], select="learned", weights=w,
+                             plan=plan, autotune=False)
     bc.run()
     sizes, stats = bc.results()
     for i, (x, eb, mode) in enumerate(fields):
@@ -128,11 +140,19 @@ def test_batch_learned_selector(gpu, orc):
 
 
 def test_batch_autotune_info(gpu):
+    """The autotuner times both plans and keeps one; the archives do not depend on it."""
     fields = _mixed_fields(6)
     xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
     bc = gpu.BatchCompressor(xs, 1e-3, "abs")
     info = bc.info()
-    assert info["construct_grid"] > 0 and info["tuned_ms"][0] > 0
+    assert info["construct_grid"] > 0 and info["tuned_ms"][0] > 0 and info["persist_ms"][0] > 0
+    assert info["grid"] > 0
+    bc.run()
+    sizes, stats = bc.results()
+    assert stats == [0] * len(xs)
+    for i, x in enumerate(xs):
+        st, ref = _single(gpu, x, 1e-3, "abs")
+        assert st == 0 and np.array_equal(bc.archives[i][:sizes[i]].cpu().numpy(), ref), i
 
 
 def test_batch_round_trip(gpu, orc):
@@ -235,12 +255,13 @@ def test_batch_decompress_bad_header_isolated(gpu):
         assert torch.equal(bd.outs[i].view(torch.int32), y.view(torch.int32))
 
 
-def test_batch_traced_launches_match_graph(gpu):
+@pytest.mark.parametrize("plan", PLANS)
+def test_batch_traced_launches_match_graph(gpu, plan):
     """With tracing on, batch calls launch their kernels one by one (each with CUDA
     events); archives and reconstructions must equal the graph replays'."""
     fields = _mixed_fields(9)[:8]
     xs = [torch.from_numpy(x).cuda() for x, _, _ in fields]
-    bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields], autotune=False)
+    bc = gpu.BatchCompressor(xs, [e for _, e, _ in fields], [m for _, _, m in fields], autotune=False, plan=plan)
     bd = gpu.BatchDecompressor(bc.archives, [tuple(x.shape) for x in xs])
     bc.run()
     bd.run()
@@ -262,13 +283,18 @@ def test_batch_traced_launches_match_graph(gpu):
     for i in range(len(xs)):
         assert torch.equal(bc.archives[i][:sizes[i]], ref_ar[i])
         assert torch.equal(bd.outs[i].view(torch.int32), ref_out[i].view(torch.int32))
-    for k in ("range", "construct", "codebook", "encode", "dec_header", "dec_setup", "stream_decode", "reconstruct"):
+    comp = ("batch_persistent",) if plan == "persistent" else ("range", "construct", "codebook", "encode")
+    for k in comp + ("dec_header", "dec_setup", "stream_decode", "reconstruct"):
         ms, cnt = tr[k]
         assert cnt == 1 and ms > 0, (k, tr[k])
+    other = ("range", "construct", "codebook", "encode") if plan == "persistent" else ("batch_persistent",)
+    for k in other:
+        assert tr[k][1] == 0, (k, tr[k])
 
 
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("nd", [1, 2, 3])
-def test_batch_of_one_dimensionality(gpu, nd):
+def test_batch_of_one_dimensionality(gpu, nd, plan):
     """A batch whose fields share their dimensionality runs the specialised
     construction kernel; archives must still equal the single-field calls'."""
     shapes = {1: [(5000,), (70001,), (4096,)], 2: [(70, 131), (64, 64), (300, 301)],
@@ -280,7 +306,7 @@ def test_batch_of_one_dimensionality(gpu, nd):
         for ax in range(len(sh)):
             x = np.cumsum(x, axis=ax).astype(np.float32)
         xs.append(torch.from_numpy(x).cuda())
-    bc = gpu.BatchCompressor(xs, 1e-3, "rel", autotune=False)
+    bc = gpu.BatchCompressor(xs, 1e-3, "rel", autotune=False, plan=plan)
     bc.run()
     sizes, stats = bc.results()
     for i, x in enumerate(xs):
@@ -291,24 +317,35 @@ def test_batch_of_one_dimensionality(gpu, nd):
 
 def test_batch256_matches_single_field_calls_and_oracle(gpu, orc):
     """The real mixed batch (256 fields, seeds 100-355, 2.65e9 elements, 10.6 GB): every
-    archive of the batched path equals the single-field call's byte for byte, and the
-    largest 1-D, 2-D and 3-D fields equal the oracle's archives, with reconstructions
-    bit-identical to the oracle's recurrence."""
+    archive of the batched path, under the one-launch plan and the staged plan alike,
+    equals the single-field call's byte for byte, and the largest 1-D, 2-D and 3-D
+    fields equal the oracle's archives, with reconstructions bit-identical to the
+    oracle's recurrence."""
     from paper_2105_12912_gb300 import synth
     specs = synth.workload_batch(256)
     xs = [synth.make_field(sp, "cuda") for sp in specs]
     caps = [min(gpu.max_archive_bytes(tuple(x.shape)), 6 * x.numel() + (1 << 20)) for x in xs]
-    bc = gpu.BatchCompressor(xs, [sp.eb for sp in specs], [sp.eb_mode for sp in specs], archive_caps=caps)
-    bc.run()
-    sizes, stats = bc.results()
-    assert all(s == 0 for s in stats), stats
+    runs = {}
+    for plan in PLANS:
+        bc = gpu.BatchCompressor(xs, [sp.eb for sp in specs], [sp.eb_mode for sp in specs], archive_caps=caps,
+                                 plan=plan, autotune=False)
+        assert bc.info()["persistent"] == (plan == "persistent")
+        bc.run()
+        sizes, stats = bc.results()
+        assert all(s == 0 for s in stats), (plan, stats)
+        runs[plan] = (bc.archives, sizes)
+        del bc.workspace
+    sizes = runs["persistent"][1]
+    assert runs["staged"][1] == sizes
     ws = gpu.Workspace(xs[0].device)
     arc = torch.empty(max(caps), dtype=torch.uint8, device="cuda")
     for i, (x, sp) in enumerate(zip(xs, specs)):
         ar, nb, _ = gpu.compress(x, sp.eb, sp.eb_mode, out=arc[:caps[i]], workspace=ws)
         assert nb == sizes[i], i
-        assert torch.equal(ar[:nb], bc.archives[i][:nb]), i
+        for plan in PLANS:
+            assert torch.equal(ar[:nb], runs[plan][0][i][:nb]), (plan, i)
     del arc, ws
+    archives = runs["persistent"][0]
     largest = {}
     for i, x in enumerate(xs):
         nd = x.dim()
@@ -319,7 +356,7 @@ def test_batch256_matches_single_field_calls_and_oracle(gpu, orc):
         sp = specs[i]
         st, ref = orc.compress(xh, orc.EB_REL, sp.eb)
         assert st == 0
-        assert ref.size == sizes[i] and np.array_equal(bc.archives[i][:sizes[i]].cpu().numpy(), ref), (nd, i)
-        y, _ = gpu.decompress(bc.archives[i], sizes[i])
+        assert ref.size == sizes[i] and np.array_equal(archives[i][:sizes[i]].cpu().numpy(), ref), (nd, i)
+        y, _ = gpu.decompress(archives[i], sizes[i])
         st, yr = orc.decompress(ref, xh.size)
         assert np.array_equal(y.cpu().numpy().ravel().view(np.uint32), yr.view(np.uint32)), (nd, i)
