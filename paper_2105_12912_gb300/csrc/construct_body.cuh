@@ -53,13 +53,18 @@ struct Chunk<3> {
 // ---- prequantization by element type (Sec. IV-A1; doubles: step 2eb (1 - 2^-24)) ---
 template <typename T>
 struct Pq;
+// The bound's words are read once per CTA and field (load_pq, thread 0, through L2:
+// in the batched persistent kernel another SM derived them during the same launch)
+// into the CTA's shared copy w, which every thread reads per tile.
 template <>
 struct Pq<float> {
   float eb_f, ebx2_f, ebx2_r;
-  // read through L2 (ld.global.cg): in the batched persistent kernel another SM
-  // derived the bound during the same launch
-  __device__ explicit Pq(const DevState* st)
-      : eb_f(__ldcg(&st->eb_f)), ebx2_f(__ldcg(&st->ebx2_f)), ebx2_r(__ldcg(&st->ebx2_r)) {}
+  __device__ explicit Pq(const float* w) : eb_f(w[0]), ebx2_f(w[1]), ebx2_r(w[2]) {}
+  __device__ static void load(const DevState* st, float* w) {
+    w[0] = __ldcg(&st->eb_f);
+    w[1] = __ldcg(&st->ebx2_f);
+    w[2] = __ldcg(&st->ebx2_r);
+  }
   __device__ __forceinline__ bool fast(float x, int32_t& k) const { return prequant_fast(x, eb_f, ebx2_f, ebx2_r, k); }
   __device__ __forceinline__ uint32_t full(float x, int32_t& k, bool& patch) const {
     return prequant(x, eb_f, ebx2_f, ebx2_r, k, patch);
@@ -68,8 +73,12 @@ struct Pq<float> {
 template <>
 struct Pq<double> {
   double eb_d, step, rstep;
-  __device__ explicit Pq(const DevState* st)
-      : eb_d(__ldcg(&st->eb_d)), step(__ldcg(&st->step_d)), rstep(__ldcg(&st->rstep_d)) {}
+  __device__ explicit Pq(const double* w) : eb_d(w[0]), step(w[1]), rstep(w[2]) {}
+  __device__ static void load(const DevState* st, double* w) {
+    w[0] = __ldcg(&st->eb_d);
+    w[1] = __ldcg(&st->step_d);
+    w[2] = __ldcg(&st->rstep_d);
+  }
   __device__ __forceinline__ bool fast(double x, int32_t& k) const { return prequant_fast_d(x, eb_d, step, rstep, k); }
   __device__ __forceinline__ uint32_t full(double x, int32_t& k, bool& patch) const {
     patch = false;
@@ -143,6 +152,7 @@ struct SmemT {
   unsigned long long scan[33];
   unsigned long long bar[2];    // mbarriers of the two buffers
   uint32_t box[2][6];           // origin and extent of each buffer's tile (thread 0 writes)
+  T pq[3];                      // the current field's bound (Pq<T>::load)
 };
 
 // One TMA tile copy (box at element coordinates c0 (x), c1, c2) into shared memory.
@@ -240,7 +250,7 @@ template <int ND, typename E>
 __device__ __noinline__ uint32_t edge_codes(const ConstructArgs& A, uint32_t b, SmemT<E>& S, E* in,
                                             const uint32_t* w, uint32_t m, int32_t* dglob) {
   const int tid = threadIdx.x, lane = tid & 31;
-  const Pq<E> pq(A.st);
+  const Pq<E> pq(S.pq);
   const int32_t r = (int32_t)A.radius;
   int32_t* s_k = reinterpret_cast<int32_t*>(in);
   uint32_t err = 0;
@@ -455,7 +465,7 @@ __device__ void process_tile(const ConstructArgs& A, uint32_t b, const uint32_t*
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t w[3] = {box[3], box[4], box[5]};
   const uint32_t m = w[0] * w[1] * w[2];
-  const Pq<E> pq(A.st);
+  const Pq<E> pq(S.pq);
   const int32_t r = (int32_t)A.radius;
   const Geom& g = A.g;
   const bool full = w[0] == g.blk[0] && w[1] == g.blk[1] && w[2] == g.blk[2];
@@ -725,7 +735,7 @@ __device__ void process_tile_global(const ConstructArgs& A, uint32_t b, const ui
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t w[3] = {box[3], box[4], box[5]};
   const uint32_t m = w[0] * w[1] * w[2];
-  const Pq<E> pq(A.st);
+  const Pq<E> pq(S.pq);
   const int32_t r = (int32_t)A.radius;
   int32_t* dglob = A.deltas + (uint64_t)b * kSlots;
   uint32_t err = 0;
@@ -914,10 +924,16 @@ __device__ __forceinline__ void construct_loop(const ConstructTask& one, const C
           ntile_acc = 0;
         }
         for (int i = tid; i < kNsymCode + kNsymCode + kHlShared; i += kThreads) S.hc[i] = 0;
-        if (P && tid == 0) await_bound(f);
+        if (tid == 0) {
+          if (P) await_bound(f);
+          Pq<E>::load(T->a.st, S.pq);
+        }
         __syncthreads();
-      } else if (P) {
-        if (tid == 0) await_bound(f);
+      } else {
+        if (tid == 0) {
+          if (P) await_bound(f);
+          Pq<E>::load(T->a.st, S.pq);
+        }
         __syncthreads();
       }
       field = f;
