@@ -30,7 +30,14 @@ constexpr uint32_t kMagic = 0x2B5A5343u;  // "CSZ+"
 constexpr uint32_t kVersion = 2;
 constexpr int kLanes = 32;  // interleave width of Huffman streams (header field)
 constexpr int kMaxLen = 64;
-constexpr int kLutBits = 12;
+// decode lookup tables: one 16-bit entry per kLutBits-bit prefix, (symbol << 4) | the
+// length of the code it starts with (0: a longer code)
+constexpr int kLutBits = 14;
+using LutEntry = uint16_t;
+__host__ __device__ constexpr uint32_t lut_entry(uint32_t sym, uint32_t len) { return (sym << 4) | len; }
+__host__ __device__ constexpr int lut_len(uint32_t e) { return (int)(e & 15u); }
+__host__ __device__ constexpr int lut_sym(uint32_t e) { return (int)(e >> 4); }
+static_assert(kLutBits <= 15 && kNsymLen <= 4096, "symbol and length fit a 16-bit entry");
 constexpr uint32_t kSpinLimit = 1u << 20;
 
 enum : int { CODEC_HUFF = 0, CODEC_RLE = 1, CODEC_RLE_HUFF = 2 };

@@ -270,17 +270,17 @@ __device__ void dec_tables_body(const DecodeArgs& a, int book) {
     t->maxlen = mx;
     t->present = 1;
   }
-  // lookup: for each 12-bit prefix, the shortest matching code of length <= 12
+  // lookup: for each kLutBits-bit prefix, the code of length <= kLutBits it starts with
   for (int v = tid; v < (1 << kLutBits); v += blockDim.x) {
     uint32_t e = 0;
     for (int l = 1; l <= kLutBits; l++) {
       const uint64_t c = (uint64_t)(v >> (kLutBits - l));
       if (cs.cnt[l] && c >= cs.first[l] && c - cs.first[l] < cs.cnt[l]) {
-        e = ((uint32_t)t->sorted[cs.off[l] + (uint32_t)(c - cs.first[l])] << 8) | (uint32_t)l;
+        e = lut_entry(t->sorted[cs.off[l] + (uint32_t)(c - cs.first[l])], (uint32_t)l);
         break;
       }
     }
-    t->lut[v] = e;
+    t->lut[v] = (LutEntry)e;
   }
 }
 
@@ -301,7 +301,7 @@ __global__ __launch_bounds__(1024) void dec_setup_kernel(DecodeArgs a, uint32_t 
 // interleaved Huffman streams: one warp decodes one stream (see common.cuh)
 // =================================================================================
 struct BookView {
-  const uint32_t* lut;  // 1 << kLutBits entries
+  const LutEntry* lut;  // 1 << kLutBits entries
   const unsigned long long* first;
   const unsigned long long* limit;
   const uint32_t* count;
@@ -373,8 +373,8 @@ struct IhsReader {
     const uint32_t lt = (1u << lane) - 1u;
     const bool live = active && !bad;
     uint32_t e = bk.lut[(uint32_t)(bb >> (64 - kLutBits))];
-    int l = (int)(e & 0xffu);
-    int sym = (int)(e >> 8);
+    int l = lut_len(e);
+    int sym = lut_sym(e);
     int ml = (live && (uint32_t)(l - 1) < (uint32_t)nb) ? l : 0;  // a table code within the bits
     bool lng = live && l == 0 && nb > kLutBits;
     if (__any_sync(~0u, lng)) {
@@ -402,10 +402,10 @@ struct IhsReader {
       }
       // only lanes that took a unit look again
       e = bk.lut[(uint32_t)(bb >> (64 - kLutBits))];
-      l = (int)(e & 0xffu);
+      l = lut_len(e);
       if (take && (uint32_t)(l - 1) < (uint32_t)nb) {
         ml = l;
-        sym = (int)(e >> 8);
+        sym = lut_sym(e);
       }
       lng = take && l == 0 && nb > kLutBits;
       if (__any_sync(~0u, lng)) {
@@ -692,7 +692,7 @@ constexpr int kRecTabWords = 288;  // per decoding warp of a fused stream: recor
 // CTA takes block b_begin + i if below b_end.
 template <int ND, typename E>
 __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32_t b_end) {
-  extern __shared__ __align__(16) uint32_t s_luts[];  // the present books' tables
+  extern __shared__ __align__(16) uint32_t s_dyn[];  // the present books' tables, then record tables
   __shared__ unsigned long long s_first[kMaxLen + 1], s_limit[kMaxLen + 1];
   __shared__ uint32_t s_off[kMaxLen + 1], s_count[kMaxLen + 1];
   __shared__ int s_go;
@@ -701,12 +701,14 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
   // that a corruption flagged by another CTA meanwhile cannot split this CTA
   if (threadIdx.x == 0) s_go = !(a.st->status & ERR_CORRUPT);
   const bool huff = (a.flags & 1u) != 0, rle = (a.flags & 2u) != 0;
-  uint32_t* lut_code = s_luts;
-  uint32_t* lut_val = s_luts + (huff ? (1 << kLutBits) : 0);
-  uint32_t* lut_len = lut_val + (1 << kLutBits);
+  LutEntry* s_luts = reinterpret_cast<LutEntry*>(s_dyn);
+  LutEntry* lut_code = s_luts;
+  LutEntry* lut_val = s_luts + (huff ? (1 << kLutBits) : 0);
+  LutEntry* lut_len = lut_val + (1 << kLutBits);
   // fused streams: after the tables, per warp a record table (32 words) and the 3-D
   // running sums (256 words); the launch sizes the dynamic shared memory for them
-  uint32_t* s_rectab = s_luts + (huff ? (1 << kLutBits) : 0) + (rle ? 2 * (1 << kLutBits) : 0);
+  uint32_t* s_rectab =
+      reinterpret_cast<uint32_t*>(s_luts + (huff ? (1 << kLutBits) : 0) + (rle ? 2 * (1 << kLutBits) : 0));
   // a chunk of blocks (batches) copies only the tables its own blocks use
   bool need_code = huff, need_runs = rle;
   if (b_end != 0) {
@@ -715,11 +717,12 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
     need_code = __syncthreads_or(huff && c == CODEC_HUFF) != 0;
     need_runs = __syncthreads_or(rle && c == CODEC_RLE_HUFF) != 0;
   }
-  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) {
-    if (need_code) lut_code[i] = a.tabs[0].lut[i];
+  constexpr int kLutVec = (1 << kLutBits) * (int)sizeof(LutEntry) / 16;  // 16-byte pieces per table
+  for (int i = threadIdx.x; i < kLutVec; i += blockDim.x) {
+    if (need_code) reinterpret_cast<uint4*>(lut_code)[i] = reinterpret_cast<const uint4*>(a.tabs[0].lut)[i];
     if (need_runs) {
-      lut_val[i] = a.tabs[1].lut[i];
-      lut_len[i] = a.tabs[2].lut[i];
+      reinterpret_cast<uint4*>(lut_val)[i] = reinterpret_cast<const uint4*>(a.tabs[1].lut)[i];
+      reinterpret_cast<uint4*>(lut_len)[i] = reinterpret_cast<const uint4*>(a.tabs[2].lut)[i];
     }
   }
   for (int i = threadIdx.x; i <= kMaxLen; i += blockDim.x) {
@@ -1565,7 +1568,7 @@ cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s) {
   trace_end(K_DEC_SETUP, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int warps = L.warps ? L.warps : kStreamWarps;
-  const size_t smem = 3 * (1u << kLutBits) * sizeof(uint32_t) + (L.nd ? (size_t)warps * kRecTabWords * 4 : 0);
+  const size_t smem = 3 * (1u << kLutBits) * sizeof(LutEntry) + (L.nd ? (size_t)warps * kRecTabWords * 4 : 0);
   auto k = L.nd == 1 ? stream_decode_batch_kernel<1>
                      : (L.nd == 2 ? stream_decode_batch_kernel<2>
                                   : (L.nd == 3 ? stream_decode_batch_kernel<3> : stream_decode_batch_kernel<0>));
@@ -1620,7 +1623,7 @@ cudaError_t launch_decode_stages(const DecodeArgs& a, cudaStream_t s) {
   const int nluts = ((a.flags & 1u) ? 1 : 0) + ((a.flags & 2u) ? 2 : 0);
   if (nluts) {
     const size_t lut_bytes =
-        (size_t)nluts * (1u << kLutBits) * sizeof(uint32_t) + (size_t)kStreamWarps * kRecTabWords * 4;
+        (size_t)nluts * (1u << kLutBits) * sizeof(LutEntry) + (size_t)kStreamWarps * kRecTabWords * 4;
     static int sms = 0, occ[4][4] = {};
     auto k = nd == 1 ? stream_decode_kernel<1, E> : (nd == 2 ? stream_decode_kernel<2, E> : stream_decode_kernel<3, E>);
     if (sms == 0) {
@@ -1629,7 +1632,7 @@ cudaError_t launch_decode_stages(const DecodeArgs& a, cudaStream_t s) {
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       for (auto kk : {stream_decode_kernel<1, E>, stream_decode_kernel<2, E>, stream_decode_kernel<3, E>})
         cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(3 * (1u << kLutBits) * sizeof(uint32_t) + kStreamWarps * kRecTabWords * 4));
+                             (int)(3 * (1u << kLutBits) * sizeof(LutEntry) + kStreamWarps * kRecTabWords * 4));
     }
     if (occ[nd][nluts] == 0) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[nd][nluts], k, 32 * kStreamWarps, lut_bytes);

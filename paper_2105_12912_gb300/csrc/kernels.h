@@ -125,7 +125,7 @@ struct DecTab {
   uint32_t present;
   uint32_t maxlen;
   uint16_t sorted[kNsymLen];
-  uint32_t lut[1 << kLutBits];  // (symbol << 8) | length, 0 = longer than kLutBits
+  alignas(16) LutEntry lut[1 << kLutBits];  // lut_entry(symbol, length), 0 = longer than kLutBits
 };
 
 struct DecodeArgs {
