@@ -706,7 +706,7 @@ struct IhsPlan {
 };
 
 constexpr uint32_t kLaneWords = 64;                       // words per lane string
-constexpr uint32_t kLaneBitsMax = 32 * (kLaneWords - 1);  // 2016: room for a 2-word read
+constexpr uint32_t kLaneBitsMax = 32 * (kLaneWords - 1);  // 2016 bits: a string and the word after it fit
 
 __device__ __forceinline__ uint32_t plan_len(const IhsPlan& P, int i) {
   // selects rather than an indexed load, so the plan stays in registers
@@ -774,22 +774,23 @@ __device__ inline IhsPlan2Out ihs_plan2(const uint16_t* sym, uint32_t m, const u
 
 // Pass 2; requires every lane total <= kLaneBitsMax.  out16[0] receives units_a,
 // stream A starts at out16[1], stream B at out16[1 + units_a].  lanebuf: 64 *
-// kLaneWords u32.  scratch: >= 8 u32.  Contains __syncthreads.
+// kLaneWords u32, all zero if `clean` (cleared before a block barrier the caller
+// passed), else cleared here.  scratch: >= 8 u32.  Contains __syncthreads.
 __device__ inline void ihs_emit2(const uint16_t* sym, uint32_t m, const uint64_t* __restrict__ codes,
                                  const IhsPlan& P, uint32_t units_a, uint32_t* lanebuf, uint16_t* out16,
-                                 uint32_t* scratch) {
+                                 uint32_t* scratch, bool clean) {
   const uint32_t tid = threadIdx.x, l = tid & 31, w = tid >> 5, sidx = w >> 2, wl = w & 3;
   const uint32_t h = huff_split(m);
   const uint16_t* ss = sym + (sidx ? h : 0);
   const uint32_t t0 = 16 * wl;
   uint32_t* mine = lanebuf + kLaneWords * (32 * sidx + l);
-  // each thread clears the words its bits land in, plus the next one (a unit read
-  // takes two words); together the threads of a lane clear every word that is read
-  {
+  // each thread clears the words its bits land in (and the one after them); together
+  // the threads of a lane clear every word that is read
+  if (!clean) {
     const uint32_t w0 = P.pre >> 5, w1 = min((P.pre + P.cum + 31) >> 5, kLaneWords - 1);
     for (uint32_t wi = w0; wi <= w1; wi++) mine[wi ^ l] = 0;
+    __syncthreads();
   }
-  __syncthreads();
   // codes gather in a 64-bit window (left-aligned, `fill` bits used, < 32 between
   // codes); each completed word is stored.  Only the thread's first and last words
   // can be shared with the neighbouring steps of the lane: those two are OR-ed in.
@@ -837,11 +838,9 @@ __device__ inline void ihs_emit2(const uint16_t* sym, uint32_t m, const uint64_t
   for (uint32_t v = 0; v < wl; v++) base += scratch[4 * sidx + v];
   if (tid == 0) out16[0] = (uint16_t)units_a;
   const uint32_t lt = (1u << l) - 1u;
-  auto unit_at = [&](uint32_t k) -> uint16_t {  // unit k of this lane's string
-    const uint32_t q = 16 * k, wi = q >> 5, off = q & 31;
-    const uint64_t two = ((uint64_t)mine[wi ^ l] << 32) | (uint64_t)mine[(wi + 1) ^ l];
-    return (uint16_t)(two >> (48 - off));
-  };
+  // unit k of this lane's string: units are 16-bit aligned, so unit k is the upper
+  // (k even) or lower (k odd) half of word k / 2
+  auto unit_at = [&](uint32_t k) -> uint16_t { return (uint16_t)(mine[(k >> 1) ^ l] >> ((~k & 1u) << 4)); };
   uint32_t c = P.pre, uprev = u_begin;
   // four steps at a time; a lane takes two or more units in one step only for a code
   // longer than 16 bits, so usually one ballot per step gives every position

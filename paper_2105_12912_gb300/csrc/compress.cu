@@ -744,6 +744,10 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b, unsigned char* smem
     const uint4* src = reinterpret_cast<const uint4*>(a.codes + (uint64_t)b * kSlots);
     uint4* dst = reinterpret_cast<uint4*>(s_c);
     for (int i = tid; i < kSlots / 8; i += kEncThreads) dst[i] = __ldcs(&src[i]);
+    // the Huffman emitter's lane strings (s_rv and s_rl, 16 KB) start cleared; run
+    // extraction overwrites them, and the emitter then clears what it uses itself
+    uint4* lanes = reinterpret_cast<uint4*>(s_rv);
+    for (int i = tid; i < 2 * kSlots * 2 / 16; i += kEncThreads) lanes[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   // the block statistics' code histogram (the first 1024 words of s_buf, which holds
   // no payload until assembly) starts at zero, and the learned selector's parameters
@@ -1044,7 +1048,8 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b, unsigned char* smem
     if (codec == CODEC_HUFF) {
       const uint32_t u = 1u + plan_out.units_a + plan_out.units_b;
       if (plan_out.max_lane_bits <= kLaneBitsMax) {
-        ihs_emit2(s_c, m, ccode, plan, plan_out.units_a, reinterpret_cast<uint32_t*>(s_rv), out16, s_part);
+        ihs_emit2(s_c, m, ccode, plan, plan_out.units_a, reinterpret_cast<uint32_t*>(s_rv), out16, s_part,
+                  !have_runs);
       } else {
         const uint32_t h = huff_split(m);
         if (tid == 0) out16[0] = (uint16_t)plan_out.units_a;
