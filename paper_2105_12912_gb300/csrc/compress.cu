@@ -2,14 +2,16 @@
 //
 // Pipeline (one stream, no host round trip until the end):
 //   range_kernel / abs_params_kernel  value range (REL) and the FP32 error bound
-//   construct_kernel (construct.cu)   prequant + chunk-local Lorenzo + postquant,
-//                                     record counts, bit words, residuals, histograms
+//   construct_kernel (construct.cu,   prequant + chunk-local Lorenzo + postquant,
+//     device code construct_body.cuh) record counts, bit words, residuals, histograms
 //   codebook_kernel                   three canonical Huffman books; a fourth CTA
 //                                     scans the blocks' record counts
 //   encode_kernel                     per block: its records, exact sizes or heuristic /
 //                                     MLP pick, payload placement by decoupled
 //                                     look-back, payload
 //   (the block counted last)          header, padding, books
+// Batches run the same bodies either as one launch per stage (the *_batch kernels)
+// or as the phases of one persistent kernel (batch_persistent_kernel).
 #include "common.cuh"
 #include "construct_body.cuh"
 #include "kernels.h"
