@@ -1,7 +1,7 @@
 // Decompression kernels of cszp (sm_103a).
 //
 //   dec_setup_kernel       codec / block-size validation and payload offsets (scan),
-//                          decode tables + 12-bit lookup table per book, record
+//                          decode tables + 14-bit lookup table per book, record
 //                          validation and each block's first record
 //   stream_decode_kernel   one warp per interleaved 32-lane stream (Huffman code
 //                          streams, RLE+Huffman value and length streams)
@@ -191,7 +191,7 @@ __device__ void dec_records_body(const DecodeArgs& a, uint32_t cta, uint32_t nct
 }
 
 // One CTA per book: lengths from the archive, Kraft check, canonical tables and a
-// 12-bit lookup table.
+// 14-bit lookup table (16-bit entries).
 __device__ void dec_tables_body(const DecodeArgs& a, int book) {
   if (a.dead) return;
   __shared__ uint8_t s_len[kNsymLen];
@@ -312,8 +312,8 @@ struct BookView {
 };
 
 // Matching the next codeword among the nb valid top bits of bb.  A table code of
-// length l <= nb found among the zero-padded top 12 bits is the next codeword (no
-// codeword is a prefix of another).  A table miss with more than 12 bits at hand is
+// length l <= nb found among the zero-padded top kLutBits bits is the next codeword (no
+// codeword is a prefix of another).  A table miss with more than kLutBits bits at hand is
 // a longer code: its length is the smallest one whose left-justified codes end above
 // bb (a binary search over the canonical limits), the true length whenever it is <= nb
 // (zero bits below nb cannot complete a shorter codeword), checked to be a codeword.
