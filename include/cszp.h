@@ -349,7 +349,9 @@ csz_status csz_selector_train(float* d_weights, const float* d_feat, const float
  * Failure-path self-test (a test aid).  Runs one bounded wait that nothing
  * satisfies, with the same code the pipeline uses: which = 0, the decoupled
  * look-back of a tile whose predecessor never publishes; which = 1, an mbarrier
- * phase that no copy or arrival completes.  The wait gives up after spin_limit
+ * phase that no copy or arrival completes; which = 2, a field hand-over of the
+ * batched persistent kernel (a counter no earlier phase releases, read with
+ * acquire semantics).  The wait gives up after spin_limit
  * tries, the kernel sets the timeout bit and returns, and the call reports
  * CSZ_E_TIMEOUT.  The context stays usable.  d_scratch: device memory, at least
  * 512 bytes, overwritten.  Synchronises `stream`.

@@ -169,7 +169,7 @@ csz_status csz_trace_read(double* ms, uint64_t* launches, int reset) {
 
 csz_status csz_wait_selftest(int which, uint32_t spin_limit, void* d_scratch, size_t scratch_bytes,
                               void* stream) {
-  if (!d_scratch || scratch_bytes < 512 || which < 0 || which > 1 || spin_limit == 0) return CSZ_E_ARG;
+  if (!d_scratch || scratch_bytes < 512 || which < 0 || which > 2 || spin_limit == 0) return CSZ_E_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DevState* st = static_cast<DevState*>(d_scratch);
   uint64_t* lb = reinterpret_cast<uint64_t*>(static_cast<unsigned char*>(d_scratch) + 256);

@@ -1593,6 +1593,9 @@ __global__ void wait_selftest_kernel(int which, uint32_t spin_limit, uint64_t* l
   __shared__ unsigned long long s_bar;
   if (which == 0) {
     if (threadIdx.x < 32) lookback_warp(lb, 1, 5, &st->status, spin_limit);
+  } else if (which == 2) {
+    // a field hand-over of the batched persistent kernel that no producer releases
+    if (threadIdx.x == 0 && !wait_ge_acquire(&st->tiles_flushed, 1u, spin_limit)) atomicOr(&st->status, ERR_TIMEOUT);
   } else if (threadIdx.x == 0) {
     mbar_init(&s_bar);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

@@ -101,7 +101,7 @@ def test_async_and_selftest_argument_checks_need_no_device(L, orc):
     assert L.csz_decompress_async(fake, ar.size, hdr, fake, 4999, fake, 1 << 20, status, None) == 5
     assert L.csz_decompress_async(fake, ar.size, hdr, fake, 5000, fake, 16, status, None) == 5
     # the self-test's argument checks
-    assert L.csz_wait_selftest(2, 100, fake, 512, None) == 1
+    assert L.csz_wait_selftest(3, 100, fake, 512, None) == 1
     assert L.csz_wait_selftest(0, 0, fake, 512, None) == 1
     assert L.csz_wait_selftest(0, 100, fake, 64, None) == 1
     assert L.csz_wait_selftest(0, 100, None, 512, None) == 1

@@ -1,7 +1,8 @@
 """Failure path on the GPU without a fault: a bounded wait that nothing satisfies
 (the look-back of a tile whose predecessor never publishes; an mbarrier phase no
-copy completes) gives up, leaves the timeout status, and the kernel returns; the
-context stays usable for the next compression."""
+copy completes; a field hand-over of the batched persistent kernel that no phase
+releases) gives up, leaves the timeout status, and the kernel returns; the context
+stays usable for the next compression."""
 import numpy as np
 import pytest
 import torch
@@ -17,7 +18,7 @@ def gpu():
     return api
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_wait_reports_timeout(gpu, which):
     assert gpu.wait_selftest(which, spin_limit=500) == 7  # CSZ_E_TIMEOUT
     # the context is intact: an ordinary round trip still works
@@ -30,5 +31,5 @@ def test_bounded_wait_reports_timeout(gpu, which):
 
 
 def test_selftest_rejects_bad_arguments(gpu):
-    assert gpu.wait_selftest(2) == 1  # CSZ_E_ARG
+    assert gpu.wait_selftest(3) == 1  # CSZ_E_ARG
     assert gpu.wait_selftest(0, spin_limit=0) == 1
