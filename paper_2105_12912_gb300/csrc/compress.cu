@@ -860,16 +860,21 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b, unsigned char* smem
     __syncthreads();
   };
   uint64_t size_h = ~0ull, size_r = ~0ull, size_rh = ~0ull;
-  auto exact_sizes = [&](bool h, bool rl, bool rh) {
-    if (h && size_h == ~0ull) size_h = (2ull * huff_units() + 3) & ~3ull;
+  // for_pick: the sizes only decide an exhaustive pick, so the Huffman size is left
+  // unknown (~0) when a run codec is already smaller than any Huffman payload can be:
+  // every code takes at least one bit, so a Huffman block of m codes holds at least
+  // m / 16 units plus its unit count, 2 + m / 8 bytes.  The pick is the same.
+  auto exact_sizes = [&](bool h, bool rl, bool rh, bool for_pick) {
     if (rl) size_r = 4ull * nr;
     if (rh && eligible && size_rh == ~0ull) {
       rlehuff_units();
       size_rh = (8ull + 2ull * (s_units[1] + s_units[2]) + 3) & ~3ull;
     }
+    const bool beaten = for_pick && min(size_r, size_rh) < 2ull + m / 8;
+    if (h && size_h == ~0ull && !beaten) size_h = (2ull * huff_units() + 3) & ~3ull;
   };
   exact_sizes(analyze || sel == SEL_HUFF || sel == SEL_EXHAUSTIVE, analyze || sel == SEL_RLE || sel == SEL_EXHAUSTIVE,
-              analyze || sel == SEL_RLE_HUFF || sel == SEL_EXHAUSTIVE);
+              analyze || sel == SEL_RLE_HUFF || sel == SEL_EXHAUSTIVE, sel == SEL_EXHAUSTIVE && !analyze);
 
   // selection
   const bool statistics = analyze || ((sel == SEL_HEURISTIC || sel == SEL_LEARNED) && eligible);
@@ -1018,7 +1023,7 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b, unsigned char* smem
       }
       if (s_fallback) {
         // the network is unsure: exact sizes decide
-        exact_sizes(true, true, true);
+        exact_sizes(true, true, true, true);
         if (tid == 0) s_codec = (uint32_t)exhaustive_pick(size_h, size_r, size_rh);
       }
     }
@@ -1029,7 +1034,7 @@ __device__ void encode_body(const EncodeArgs& a, uint32_t b, unsigned char* smem
   __syncthreads();
   const int codec = (int)s_codec;
   if (codec == CODEC_RLE || codec == CODEC_RLE_HUFF) extract_runs();
-  exact_sizes(codec == CODEC_HUFF, codec == CODEC_RLE, codec == CODEC_RLE_HUFF);
+  exact_sizes(codec == CODEC_HUFF, codec == CODEC_RLE, codec == CODEC_RLE_HUFF, false);
   const uint64_t size = codec == CODEC_HUFF ? size_h : (codec == CODEC_RLE ? 4ull * nr : size_rh);
   // The block's codec and size are counted, then the block counts itself done with
   // release semantics: the block that takes the last count (acquire) writes the
