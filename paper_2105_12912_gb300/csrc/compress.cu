@@ -1156,8 +1156,9 @@ static size_t encode_smem_bytes() {
 // =================================================================================
 // Every CTA runs the four phases of the staged batch in order, so the work items of
 // each phase are taken (by ticket) only after those of the phases before it were all
-// taken: a waiting CTA waits on items that running CTAs hold, and those wait only on
-// earlier phases, so with every CTA resident the launch cannot deadlock.  The
+// taken: a waiting CTA waits on items that running CTAs hold (only a running CTA takes
+// an item), and those wait only on earlier phases, so the launch cannot deadlock even
+// when not all of its CTAs are resident at once.  The
 // hand-overs are per field (DevState ready_range, tiles_flushed, books_done: a
 // release by the producer, an acquire by thread 0 of the consumer, then a CTA
 // barrier), so one field's books and encoding start while other fields are still
