@@ -204,8 +204,7 @@ csz_status csz_decompress_static(const uint8_t* d_archive, size_t bytes, float* 
  * a few times, and keeps the fastest; CSZ_BATCH_PERSISTENT or CSZ_BATCH_STAGED alone
  * restricts the candidates to one plan; with neither flag and no tuning the plan is
  * the persistent launch on every resident CTA), and captures it into a CUDA graph.
- * Each
- * csz_batch_compress replays the graph on `stream` without synchronising; the
+ * Each csz_batch_compress replays the graph on `stream` without synchronising; the
  * archives then hold exactly what csz_compress would write for each field with the
  * same options.  csz_batch_results synchronises and reads every field's archive
  * size and status.
@@ -231,7 +230,8 @@ typedef struct csz_batch csz_batch;
 #define CSZ_BATCH_STAGED 2     /* candidates: the staged launches */
 #define CSZ_BATCH_PERSISTENT 4 /* candidates: the single persistent launch */
 
-/* Workspace for a batch (0 if any field is invalid). */
+/* Workspace for a batch (0 if any field is invalid); it includes 124 KB per field of
+   working memory for the persistent plan's run-length books. */
 size_t csz_batch_workspace_bytes(int nfields, const csz_field* fields);
 csz_status csz_batch_create(int nfields, const csz_field* fields, const csz_options* opt,
                             void* d_workspace, size_t workspace_bytes, int autotune,
