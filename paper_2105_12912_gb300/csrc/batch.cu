@@ -530,7 +530,7 @@ csz_status csz_batch_plan(const csz_batch* b, int* persistent, int* grid, double
 }  // extern "C"
 
 // Stream-decode CTA shapes the batch's tuner chooses among (warps per CTA; a CTA
-// decodes warps / 2 codec blocks).  None changes the output.
+// decodes kDecChunkRounds * warps / 2 codec blocks).  None changes the output.
 constexpr int kDecShapes[3] = {8, 16, 32};
 
 struct csz_batch_dec {
@@ -697,7 +697,7 @@ csz_status csz_batch_dec_create(int nfields, const csz_dfield* fields, void* d_w
     if (rec_ctas > 256) rec_ctas = 256;
     nsetup += prep_chunks(g) + 3 + (uint32_t)rec_ctas;
     for (int v = 0; v < 3; v++) {
-      const uint32_t per = (uint32_t)kDecShapes[v] / 2;
+      const uint32_t per = kDecChunkRounds * ((uint32_t)kDecShapes[v] / 2);
       chunk0s[v][f] = nchunks_v[v];
       nchunks_v[v] += (g.nblk + per - 1) / per;
     }

@@ -688,8 +688,9 @@ constexpr int kRecTabWords = 288;  // per decoding warp of a fused stream: recor
 // (ND != 0 and a.fuse), a stream of a full Huffman block is reconstructed by the
 // warp as it is decoded (fused_decode_reconstruct); other Huffman streams leave
 // their codes in the workspace for the reconstruction kernel.
-// Blocks come from the field's ticket (b_end == 0) or, in batches, warp i of the
-// CTA takes block b_begin + i if below b_end.
+// Streams come from the field's ticket (b_end == 0) or, in batches, from the CTA's
+// chunk of blocks [b_begin, b_end): each warp draws the chunk's next stream from a
+// shared counter until none is left.
 template <int ND, typename E>
 __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32_t b_end) {
   extern __shared__ __align__(16) uint32_t s_dyn[];  // the present books' tables, then record tables
@@ -699,7 +700,11 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
   if (a.dead) return;
   // the status is read once, by thread 0, and acted on after the staging barrier, so
   // that a corruption flagged by another CTA meanwhile cannot split this CTA
-  if (threadIdx.x == 0) s_go = !(a.st->status & ERR_CORRUPT);
+  __shared__ uint32_t s_next;  // batches: the chunk's next stream slot
+  if (threadIdx.x == 0) {
+    s_go = !(a.st->status & ERR_CORRUPT);
+    s_next = 0;
+  }
   const bool huff = (a.flags & 1u) != 0, rle = (a.flags & 2u) != 0;
   LutEntry* s_luts = reinterpret_cast<LutEntry*>(s_dyn);
   LutEntry* lut_code = s_luts;
@@ -737,15 +742,17 @@ __device__ void stream_decode_body(const DecodeArgs& a, uint32_t b_begin, uint32
   const bool ticketed = b_end == 0;
   // work items are (block, stream) slots: a Huffman block's streams A and B, an
   // RLE+Huffman block's value and length streams
-  for (uint32_t round = 0;; round++) {
+  for (;;) {
     uint32_t slot = 0;
     if (ticketed) {
       if (lane0) slot = atomicAdd(&a.st->ticket_decode, 1u);
       slot = __shfl_sync(~0u, slot, 0);
       if (slot >= 2 * a.g.nblk) break;
     } else {
-      slot = 2 * b_begin + (threadIdx.x >> 5);
-      if (round > 0 || slot >= 2 * b_end) break;
+      // the chunk's streams, drawn one at a time by whichever warp is free
+      if (lane0) slot = atomicAdd(&s_next, 1u);
+      slot = 2 * b_begin + __shfl_sync(~0u, slot, 0);
+      if (slot >= 2 * b_end) break;
     }
     const uint32_t b = slot >> 1, which = slot & 1;
     const int codec = a.ar[a.off_codec + b];
@@ -1516,7 +1523,7 @@ __global__ __launch_bounds__(1024) void stream_decode_batch_kernel(const DecodeA
                                                                    const uint32_t* __restrict__ chunk0, int nfields) {
   const int f = field_of(chunk0, nfields, blockIdx.x);
   const DecodeArgs& a = tasks[f];
-  const uint32_t per = blockDim.x / 64;  // blocks per CTA: two streams each
+  const uint32_t per = kDecChunkRounds * (blockDim.x / 64);  // blocks per CTA: two streams each
   const uint32_t b0 = (blockIdx.x - chunk0[f]) * per;
   const uint32_t b1 = min(a.g.nblk, b0 + per);
   stream_decode_body<ND, float>(a, b0, b1);

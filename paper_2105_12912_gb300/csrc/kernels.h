@@ -255,6 +255,10 @@ struct DecodeBatchLaunch {
   int warps;               // stream-decode warps per CTA (8, 16 or 32; 0 = 16)
 };
 constexpr int kStreamWarpsPerCta = 16;
+// batched decoding: a decoding CTA of w warps takes kDecChunkRounds * w / 2 codec
+// blocks (its decode tables staged once for them), its warps drawing the blocks'
+// streams one at a time
+constexpr uint32_t kDecChunkRounds = 4;
 cudaError_t launch_decode_batch(const DecodeBatchLaunch& L, cudaStream_t s);
 
 }  // namespace cszp
